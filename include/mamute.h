@@ -1,0 +1,187 @@
+/*
+ * mamute.h - C ABI of the GB300-native Mamute hot path.
+ *
+ * The library computes, on one sm_103a GPU, the three steps the paper builds
+ * its modelling and FWI on:
+ *   - the 3-D acoustic finite-difference propagator of Eq. 1 (second order in
+ *     time, eighth order in space, optional variable-density term), with the
+ *     damping absorbing boundary, source injection and receiver sampling
+ *     (Sec. 2.1; Table 1: ModelingStep, ReadReceiver; Algorithm 1);
+ *   - the adjoint wavefield driven by data residuals and the zero-lag
+ *     cross-correlation imaging condition, summed over shots into the
+ *     gradient of the misfit (Algorithm 3; Sec. 2.1, adjoint-state method);
+ *   - optimal checkpointing of the forward wavefield (Sec. 2.1, third
+ *     wavefield-management mode; check_mem of Table 4).
+ *
+ * Conventions shared by every call
+ *   Grid       Model arrays are [nz][ny][nx] float32, x fastest (Sec. 2.2.2,
+ *              "z x y x x").  A sponge of `border` cells is added outside the
+ *              model on all six faces; the model is edge-replicated into it.
+ *              Spacing is isotropic (h).  The wavefield is zero outside the
+ *              padded grid.
+ *   Sources    One wavelet w[nt] shared by all shots (Sec. 2.2.2, source.bin),
+ *              injected at the nearest node: u^{n+1}(x_s) += dt^2 w[n] /
+ *              (h^3 sqrt(rho(x_s))).
+ *   Receivers  Shot s owns receivers rec_offset[s] .. rec_offset[s+1]-1,
+ *              coordinates (x, y, z) in metres from (ox, oy, oz), nearest
+ *              node; sample n records p = sqrt(rho) u^{n+1} (Sec. 2.2.2:
+ *              traces are [n_rec][ns], trace-major).
+ *   Memory     Arrays named "device" are device pointers owned by the caller
+ *              (e.g. torch tensors) on the context's device; arrays named
+ *              "host" are host pointers.  The library owns only its context
+ *              scratch (wavefields, checkpoints, tables), grown on demand and
+ *              freed by mamute_ctx_destroy.  Nothing is retained from caller
+ *              buffers after a call returns.
+ *   Streams    Work is issued on the stream given to mamute_ctx_create; every
+ *              compute call synchronises that stream before returning, so its
+ *              outputs are ready when it returns.
+ *   Errors     Every int-returning call returns MAMUTE_OK (0) or a negative
+ *              MAMUTE_E* code; no exception or abort crosses the ABI.
+ *              mamute_last_error() gives a one-line description of the last
+ *              failure on a context.  A context is used by one host thread at
+ *              a time.
+ */
+#ifndef MAMUTE_H
+#define MAMUTE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MAMUTE_OK 0
+#define MAMUTE_EINVAL (-1)   /* bad dimensions, null pointer, point outside the model */
+#define MAMUTE_ECFL (-2)     /* max(c) dt / h above the stability bound 0.4529 */
+#define MAMUTE_ENOMEM (-3)   /* device allocation failed */
+#define MAMUTE_ECUDA (-4)    /* a CUDA runtime or driver call failed */
+#define MAMUTE_ETIMEOUT (-5) /* a bounded device-side wait ran out */
+#define MAMUTE_EARCH (-6)    /* the device is not compute capability 10.3 */
+
+typedef struct mamute_ctx mamute_ctx;
+
+/* Grid and time axis (Table 2: nx, ny, nz, dx=dy=dz, border, ox, oy, oz, ns,
+ * dt).  cerjan is the Cerjan damping constant alpha of the sponge profile
+ * g(d) = exp(-(alpha d)^2), d = depth into the sponge in cells (Sec. 2.1,
+ * damping boundary); 0 disables damping.  free_surface must be 0. */
+typedef struct {
+  int nx, ny, nz;
+  int border;
+  float h;
+  float dt;
+  int nt;
+  float ox, oy, oz;
+  float cerjan;
+  int free_surface;
+} mamute_grid;
+
+/* Options (Table 4 check_mem; Sec. 3 zeroes_nplanes_gradient).
+ *   check_mem       fraction (0,1] of free device memory that checkpoint
+ *                   slots may use when n_snapshots == 0 (default 0.8).
+ *   n_snapshots     0: as many revolve slots as check_mem allows;
+ *                   >0: exactly that many slots; -1: keep the imaging term of
+ *                   every step (no recomputation).
+ *   zero_top_planes ZeroesNearSurface: gradient planes z < this are zeroed.
+ *   aperture        host [n_src][4] or NULL: shot s propagates only over the
+ *                   model columns x in [a0, a1), y in [a2, a3) plus the sponge
+ *                   around them (cells of the global padded grid, so the
+ *                   sponge of an interior aperture sees the true model); a0
+ *                   must be a multiple of 4.  NULL: every shot uses the whole
+ *                   grid.
+ *   phess           device [nz][ny][nx] or NULL: receives the pseudo-Hessian
+ *                   sum_s sum_n (g (lap - m2) u_s^n)^2 of the forward pass
+ *                   (overwritten).
+ * A NULL options pointer means all defaults. */
+typedef struct {
+  float check_mem;
+  int n_snapshots;
+  int zero_top_planes;
+  const int* aperture;
+  float* phess;
+} mamute_opts;
+
+/* Creates a context on `device` issuing work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Returns MAMUTE_EARCH unless the device
+ * is sm_103.  *ctx is NULL on failure. */
+int mamute_ctx_create(mamute_ctx** ctx, int device, void* cuda_stream);
+
+/* Frees the context and all of its device scratch.  NULL is allowed. */
+void mamute_ctx_destroy(mamute_ctx* ctx);
+
+/* Static description of an error code. */
+const char* mamute_strerror(int code);
+
+/* Description of the last failure on ctx (empty string if none). */
+const char* mamute_last_error(const mamute_ctx* ctx);
+
+/* Seismic modelling (Algorithm 1; Table 1 ModelingStep and ReadReceiver).
+ *   vel       device [nz][ny][nx] P-wave velocity (m/s)
+ *   rho       device [nz][ny][nx] density, or NULL for constant density
+ *             (Eq. 1 right / left)
+ *   src_xyz   host [n_src][3] source positions (m)
+ *   wavelet   host [nt] source signature
+ *   rec_offset host [n_src+1], rec_offset[0] = 0, non-decreasing
+ *   rec_xyz   host [rec_offset[n_src]][3] receiver positions (m)
+ *   opts      may be NULL (aperture and phess are honoured)
+ *   seis      device [rec_offset[n_src]][nt] output, overwritten
+ * Errors: EINVAL (dimensions, nulls, a point outside the model, misaligned
+ * aperture), ECFL (ValidConditions, Table 1), ENOMEM, ECUDA, ETIMEOUT. */
+int mamute_model(mamute_ctx* ctx, const mamute_grid* grid, const float* vel, const float* rho,
+                 int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+                 const float* rec_xyz, const mamute_opts* opts, float* seis);
+
+/* Misfit and gradient (Algorithm 3): forward propagation with wavefield
+ * checkpointing, J = 1/2 sum (d - d_obs)^2 (SeismicData::Misfit), adjoint
+ * propagation driven by the residuals with cross-correlation imaging, the
+ * sum over shots, MultiplyAdjoint (dJ/dc = 2 c dt^2 dJ/dA, A = c^2 dt^2) and
+ * ZeroesNearSurface.
+ *   d_obs   device [rec_offset[n_src]][nt] observed data
+ *   misfit  host, receives J (accumulated in FP64)
+ *   grad    device [nz][ny][nx], receives dJ/dc, overwritten
+ * Other arguments and errors as mamute_model. */
+int mamute_gradient(mamute_ctx* ctx, const mamute_grid* grid, const float* vel, const float* rho,
+                    int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+                    const float* rec_xyz, const float* d_obs, const mamute_opts* opts,
+                    double* misfit, float* grad);
+
+/* Transposed Jacobian applied to a data-space vector (the backward pass of
+ * modelling): grad = d<seis(c), d_res>/dc, i.e. the adjoint wavefield is
+ * driven by d_res instead of the residual.  Used by the autograd binding.
+ *   d_res  device [rec_offset[n_src]][nt]
+ *   grad   device [nz][ny][nx], overwritten
+ * Other arguments and errors as mamute_gradient. */
+int mamute_adjoint(mamute_ctx* ctx, const mamute_grid* grid, const float* vel, const float* rho,
+                   int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+                   const float* rec_xyz, const float* d_res, const mamute_opts* opts, float* grad);
+
+/* As mamute_model and mamute_gradient, but vel, rho, seis, d_obs, grad and
+ * opts->phess are HOST pointers; the call stages them through context
+ * buffers (host->device before, device->host after). */
+int mamute_model_host(mamute_ctx* ctx, const mamute_grid* grid, const float* vel,
+                      const float* rho, int n_src, const float* src_xyz, const float* wavelet,
+                      const int* rec_offset, const float* rec_xyz, const mamute_opts* opts,
+                      float* seis);
+int mamute_gradient_host(mamute_ctx* ctx, const mamute_grid* grid, const float* vel,
+                         const float* rho, int n_src, const float* src_xyz,
+                         const float* wavelet, const int* rec_offset, const float* rec_xyz,
+                         const float* d_obs, const mamute_opts* opts, double* misfit,
+                         float* grad);
+
+/* Checkpoint schedule (host only, no device work; Sec. 2.1 optimal
+ * checkpointing after Griewank and Walther).  Plans the reversal of nt steps
+ * from the zero initial state with n_slots checkpoint slots.  Writes the
+ * number of forward steps the plan takes (the first sweep included) to
+ * *n_forward and the number of actions to *n_actions; if `actions` is not
+ * NULL it must hold 3 * (*n_actions) ints from a previous sizing call and
+ * receives triples (kind, a, b): kind 0 = advance from step a to step b,
+ * 1 = store the current state in slot a, 2 = restore slot a (state of step
+ * b; slot -1 is the zero initial state), 3 = reverse step a.
+ * Errors: EINVAL for nt < 1 or n_slots < 0. */
+int mamute_revolve_plan(int nt, int n_slots, long long* n_forward, int* n_actions, int* actions);
+
+/* Stability bound used by the CFL check (max(c) dt / h must not exceed it). */
+double mamute_cfl_limit(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAMUTE_H */

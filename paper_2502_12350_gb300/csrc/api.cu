@@ -1,0 +1,835 @@
+// C ABI of libmamute: context, validation, planning and the modelling /
+// gradient drivers (Algorithm 1 and Algorithm 3 of the paper).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mamute.h"
+#include "aux.h"
+#include "common.cuh"
+#include "revolve.h"
+#include "stencil.h"
+
+using namespace mamute;
+
+namespace {
+
+// Stability bound of the 3-D eighth-order leapfrog scheme:
+// (c dt / h)^2 * 3 * max_theta(-c0 - 2 sum c_j cos j theta) <= 4.
+double cfl_bound() {
+  const double c[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+  double mx = 0.0;
+  for (int i = 0; i <= 100000; ++i) {
+    const double th = M_PI * i / 100000.0;
+    double s = -c[0];
+    for (int j = 1; j <= 4; ++j) s -= 2.0 * c[j] * std::cos(j * th);
+    mx = std::max(mx, s);
+  }
+  return 2.0 / std::sqrt(3.0 * mx);
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+struct Plan {
+  int nx, ny, nz, b, Nx, Ny, Nz, pitchG, nt;
+  double h, dt;
+  bool dens;
+  int tx, ty;             // forward tile
+  int atx, aty;           // adjoint tile
+  std::vector<VolDesc> vols;
+  std::vector<WorkItem> items, aitems;
+  std::vector<int> rec_ptr, arec_ptr;
+  std::vector<RecEntry> rec, arec;
+  std::vector<long long> rec_cell, arec_cell;
+  std::vector<float> rec_g, arec_g;
+  std::vector<int> colmap, acolmap;
+  std::vector<long long> src_cell;
+  std::vector<float> gx, gy, gz;
+  long long pool_elems = 0, term_elems = 0;
+  int ncol = 0;
+};
+
+}  // namespace
+
+struct mamute_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  // scratch (grow-only)
+  DevBuf coefA, coefM, pool[2], psi[2], acc, slots, tstore, dint, rint, dtmp, partial, misfit;
+  DevBuf items, vols, maps, cmaps, recptr, rec, colmap, gx, gy, gz, cells, gvals, srccell,
+      aitems, arecptr, arec, acolmap, acells, agvals;
+  DevBuf hvel, hrho, hseis, hobs, hgrad, hphess;  // staging for the *_host calls
+  int* status = nullptr;
+  unsigned int* maxbits = nullptr;
+};
+
+namespace {
+
+int fail(mamute_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? MAMUTE_ENOMEM : MAMUTE_ECUDA, \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+  if (bytes <= b.bytes && b.p) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  return e;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+template <typename T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
+  cudaError_t e = ensure(b, sizeof(T) * std::max<size_t>(v.size(), 1));
+  if (e != cudaSuccess || v.empty()) return e;
+  e = cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);  // host vectors are released after the call
+}
+
+std::vector<float> sponge(int N, int b, double alpha) {
+  std::vector<float> p(N);
+  for (int i = 0; i < N; ++i) {
+    int d = 0;
+    if (i < b) d = b - i;
+    else if (i > N - 1 - b) d = i - (N - 1 - b);
+    const double a = alpha * d;
+    p[i] = (float)std::exp(-a * a);
+  }
+  return p;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v ? atoi(v) : dflt;
+}
+
+// Receiver tables for one tile configuration.
+void build_receivers(Plan& P, int TX, int TY, const std::vector<std::vector<int>>& recnode,
+                     const std::vector<int>& item_base, const std::vector<int>& tiles_x,
+                     std::vector<WorkItem>& items, std::vector<int>& rec_ptr,
+                     std::vector<RecEntry>& rec, std::vector<long long>& cells,
+                     std::vector<float>& gvals, std::vector<int>& colmap, int n_rec_total,
+                     const std::vector<long long>& rcell_all, const std::vector<int>& rshot) {
+  struct Tmp {
+    int item, z, lxy, r;
+  };
+  std::vector<Tmp> t;
+  t.reserve(n_rec_total);
+  for (int r = 0; r < n_rec_total; ++r) {
+    const int s = rshot[r];
+    const int lx = recnode[r][0], ly = recnode[r][1], lz = recnode[r][2];
+    const int ti = lx / TX, tj = ly / TY;
+    const int item = item_base[s] + tj * tiles_x[s] + ti;
+    t.push_back(Tmp{item, lz, (lx - ti * TX) + TX * (ly - tj * TY), r});
+  }
+  std::sort(t.begin(), t.end(), [](const Tmp& a, const Tmp& b) {
+    if (a.item != b.item) return a.item < b.item;
+    if (a.z != b.z) return a.z < b.z;
+    if (a.lxy != b.lxy) return a.lxy < b.lxy;
+    return a.r < b.r;
+  });
+  rec.assign(t.size(), RecEntry{});
+  cells.assign(t.size(), 0);
+  gvals.assign(t.size(), 0.f);
+  colmap.assign(t.size(), 0);
+  rec_ptr.clear();
+  for (auto& it : items) it.rec_tab = -1;
+  size_t e = 0;
+  while (e < t.size()) {
+    const int item = t[e].item;
+    size_t f = e;
+    while (f < t.size() && t[f].item == item) ++f;
+    WorkItem& W = items[item];
+    W.rec_tab = (int)rec_ptr.size();
+    const int npl = W.ze - W.zb;
+    size_t k = e;
+    for (int j = 0; j <= npl; ++j) {
+      while (k < f && t[k].z < W.zb + j) ++k;
+      rec_ptr.push_back((int)k);
+    }
+    e = f;
+  }
+  for (size_t i = 0; i < t.size(); ++i) {
+    RecEntry& R = rec[i];
+    R.lxy = t[i].lxy;
+    R.col = (int)i;
+    R.group = 0;
+    colmap[i] = t[i].r;
+    cells[i] = rcell_all[t[i].r];
+    const int s = rshot[t[i].r];
+    const VolDesc& V = P.vols[s];
+    const int lx = recnode[t[i].r][0], ly = recnode[t[i].r][1], lz = recnode[t[i].r][2];
+    gvals[i] = P.gx[V.gx_off + lx] * P.gy[V.gy_off + ly] * P.gz[lz];
+  }
+  for (size_t i = 0; i < t.size();) {
+    size_t j = i;
+    while (j < t.size() && t[j].item == t[i].item && t[j].z == t[i].z && t[j].lxy == t[i].lxy) ++j;
+    rec[i].group = (int)(j - i);
+    i = j;
+  }
+}
+
+int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, const float* src_xyz,
+               const int* rec_offset, const float* rec_xyz, const int* aperture, Plan& P) {
+  if (!g) return fail(ctx, MAMUTE_EINVAL, "grid is NULL");
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->border < 0 || g->nt < 1)
+    return fail(ctx, MAMUTE_EINVAL, "bad grid dimensions");
+  if (!(g->h > 0.f) || !(g->dt > 0.f)) return fail(ctx, MAMUTE_EINVAL, "h and dt must be > 0");
+  if (g->free_surface != 0) return fail(ctx, MAMUTE_EINVAL, "free_surface is not supported");
+  if (!(g->cerjan >= 0.f)) return fail(ctx, MAMUTE_EINVAL, "cerjan must be >= 0");
+  if (n_src < 1 || !src_xyz || !rec_offset) return fail(ctx, MAMUTE_EINVAL, "no shots");
+  if (rec_offset[0] != 0) return fail(ctx, MAMUTE_EINVAL, "rec_offset[0] must be 0");
+  for (int s = 0; s < n_src; ++s)
+    if (rec_offset[s + 1] < rec_offset[s]) return fail(ctx, MAMUTE_EINVAL, "rec_offset decreasing");
+  const int n_rec = rec_offset[n_src];
+  if (n_rec > 0 && !rec_xyz) return fail(ctx, MAMUTE_EINVAL, "rec_xyz is NULL");
+  P.nx = g->nx; P.ny = g->ny; P.nz = g->nz; P.b = g->border; P.nt = g->nt;
+  P.h = g->h; P.dt = g->dt; P.dens = dens;
+  P.Nx = P.nx + 2 * P.b; P.Ny = P.ny + 2 * P.b; P.Nz = P.nz + 2 * P.b;
+  P.pitchG = (int)round_up(P.Nx, 8);
+  const long long nmax = 1LL << 31;
+  if ((long long)P.Nz * P.Ny * P.pitchG >= nmax * 4)
+    return fail(ctx, MAMUTE_EINVAL, "grid too large");
+  P.tx = env_int("MAMUTE_TX", 64); P.ty = env_int("MAMUTE_TY", 16);
+  P.atx = env_int("MAMUTE_ADJ_TX", 64); P.aty = env_int("MAMUTE_ADJ_TY", 8);
+  if (!tile_supported(P.tx, P.ty) || !tile_supported(P.atx, P.aty))
+    return fail(ctx, MAMUTE_EINVAL, "unsupported tile shape");
+  P.gz = sponge(P.Nz, P.b, g->cerjan);
+  auto node = [&](const float* xyz, int& i, int& j, int& k) {
+    i = (int)std::floor(((double)xyz[0] - g->ox) / g->h + 0.5);
+    j = (int)std::floor(((double)xyz[1] - g->oy) / g->h + 0.5);
+    k = (int)std::floor(((double)xyz[2] - g->oz) / g->h + 0.5);
+    return i >= 0 && i < P.nx && j >= 0 && j < P.ny && k >= 0 && k < P.nz;
+  };
+  std::vector<std::vector<int>> recnode(n_rec, std::vector<int>(3));
+  std::vector<long long> rcell(n_rec);
+  std::vector<int> rshot(n_rec);
+  long long off = 0, toff = 0;
+  for (int s = 0; s < n_src; ++s) {
+    int a0 = 0, a1 = P.nx, a2 = 0, a3 = P.ny;
+    if (aperture) {
+      a0 = aperture[4 * s]; a1 = aperture[4 * s + 1]; a2 = aperture[4 * s + 2]; a3 = aperture[4 * s + 3];
+      if (a0 < 0 || a1 > P.nx || a0 >= a1 || a2 < 0 || a3 > P.ny || a2 >= a3)
+        return fail(ctx, MAMUTE_EINVAL, "aperture of shot %d outside the model", s);
+      if (a0 % 4) return fail(ctx, MAMUTE_EINVAL, "aperture x start of shot %d not a multiple of 4", s);
+    }
+    VolDesc V{};
+    V.cx0 = a0; V.cy0 = a2;
+    V.Nx = (a1 - a0) + 2 * P.b; V.Ny = (a3 - a2) + 2 * P.b; V.Nz = P.Nz;
+    V.pitch = (int)round_up(V.Nx, 8);
+    V.border = P.b; V.nxi = a1 - a0; V.nyi = a3 - a2; V.nzi = P.nz;
+    V.slab = round_up((long long)V.Nz * V.Ny * V.pitch, 64);
+    V.off = off; off += V.slab;
+    V.toff = toff; toff += (long long)V.nxi * V.nyi * V.nzi;
+    V.gx_off = (int)P.gx.size(); V.gy_off = (int)P.gy.size();
+    std::vector<float> px = sponge(V.Nx, P.b, g->cerjan), py = sponge(V.Ny, P.b, g->cerjan);
+    P.gx.insert(P.gx.end(), px.begin(), px.end());
+    P.gy.insert(P.gy.end(), py.begin(), py.end());
+    int i, j, k;
+    if (!node(src_xyz + 3 * s, i, j, k)) return fail(ctx, MAMUTE_EINVAL, "source %d outside the model", s);
+    if (i < a0 || i >= a1 || j < a2 || j >= a3)
+      return fail(ctx, MAMUTE_EINVAL, "source %d outside its aperture", s);
+    V.src_x = i + P.b - a0; V.src_y = j + P.b - a2; V.src_z = k + P.b;
+    P.src_cell.push_back(((long long)k * P.ny + j) * P.nx + i);
+    for (int r = rec_offset[s]; r < rec_offset[s + 1]; ++r) {
+      if (!node(rec_xyz + 3 * (long long)r, i, j, k))
+        return fail(ctx, MAMUTE_EINVAL, "receiver %d outside the model", r);
+      if (i < a0 || i >= a1 || j < a2 || j >= a3)
+        return fail(ctx, MAMUTE_EINVAL, "receiver %d outside the aperture of its shot", r);
+      recnode[r] = {i + P.b - a0, j + P.b - a2, k + P.b};
+      rcell[r] = ((long long)k * P.ny + j) * P.nx + i;
+      rshot[r] = s;
+    }
+    P.vols.push_back(V);
+  }
+  P.pool_elems = off;
+  P.term_elems = toff;
+  P.ncol = n_rec;
+  // Work items: one per tile, all planes (forward and adjoint tiles).
+  auto make_items = [&](int TX, int TY, std::vector<WorkItem>& items, std::vector<int>& base,
+                        std::vector<int>& tiles_x) {
+    items.clear();
+    base.clear();
+    tiles_x.clear();
+    for (int s = 0; s < n_src; ++s) {
+      const VolDesc& V = P.vols[s];
+      const int ntx = (V.Nx + TX - 1) / TX, nty = (V.Ny + TY - 1) / TY;
+      base.push_back((int)items.size());
+      tiles_x.push_back(ntx);
+      for (int tj = 0; tj < nty; ++tj)
+        for (int ti = 0; ti < ntx; ++ti) items.push_back(WorkItem{s, ti, tj, 0, V.Nz, -1, 0, 0});
+    }
+  };
+  std::vector<int> base, tiles_x;
+  make_items(P.tx, P.ty, P.items, base, tiles_x);
+  build_receivers(P, P.tx, P.ty, recnode, base, tiles_x, P.items, P.rec_ptr, P.rec, P.rec_cell,
+                  P.rec_g, P.colmap, n_rec, rcell, rshot);
+  make_items(P.atx, P.aty, P.aitems, base, tiles_x);
+  build_receivers(P, P.atx, P.aty, recnode, base, tiles_x, P.aitems, P.arec_ptr, P.arec,
+                  P.arec_cell, P.arec_g, P.acolmap, n_rec, rcell, rshot);
+  return MAMUTE_OK;
+}
+
+CUresult encode3d(mamute_ctx* ctx, CUtensorMap* m, const float* base, int Nx, int Ny, int Nz,
+                  int pitch, int bx, int by) {
+  cuuint64_t dims[3] = {(cuuint64_t)Nx, (cuuint64_t)Ny, (cuuint64_t)Nz};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * Ny * 4};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return ctx->encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+// Device-resident problem: coefficients, tables and maps for one call.
+struct Run {
+  Plan P;
+  bool adj_maps = false;
+};
+
+int check_cfl(mamute_ctx* ctx, const Plan& P, const float* vel) {
+  CK(cudaMemsetAsync(ctx->maxbits, 0, sizeof(unsigned int), ctx->stream));
+  CK(launch_max(vel, (long long)P.nx * P.ny * P.nz, ctx->maxbits, ctx->stream));
+  unsigned int bits = 0;
+  CK(cudaMemcpyAsync(&bits, ctx->maxbits, sizeof bits, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  float vmax;
+  std::memcpy(&vmax, &bits, sizeof vmax);
+  const double courant = (double)vmax * P.dt / P.h;
+  if (!(courant <= cfl_bound()))
+    return fail(ctx, MAMUTE_ECFL, "max(c) dt / h = %.5f exceeds the stability bound %.5f", courant,
+                cfl_bound());
+  return MAMUTE_OK;
+}
+
+// Coefficients, geometry tables, pools and maps.
+int setup(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho, bool need_psi,
+          bool need_acc) {
+  const size_t nG = (size_t)P.Nz * P.Ny * P.pitchG;
+  CK(ensure(ctx->coefA, nG * 4));
+  if (P.dens) CK(ensure(ctx->coefM, nG * 4));
+  CoefPrepArgs ca{vel, rho, P.nx, P.ny, P.nz, P.b, P.Nx, P.Ny, P.Nz, P.pitchG, P.h, P.dt,
+                  (float*)ctx->coefA.p, P.dens ? (float*)ctx->coefM.p : nullptr};
+  CK(launch_prep_coef(ca, ctx->stream));
+  const size_t pool = (size_t)P.pool_elems * 4;
+  for (int i = 0; i < 2; ++i) CK(ensure(ctx->pool[i], pool));
+  if (need_psi)
+    for (int i = 0; i < 2; ++i) CK(ensure(ctx->psi[i], pool));
+  if (need_acc) CK(ensure(ctx->acc, pool));
+  CK(upload(ctx->vols, P.vols, ctx->stream));
+  CK(upload(ctx->items, P.items, ctx->stream));
+  CK(upload(ctx->recptr, P.rec_ptr, ctx->stream));
+  CK(upload(ctx->rec, P.rec, ctx->stream));
+  CK(upload(ctx->colmap, P.colmap, ctx->stream));
+  CK(upload(ctx->cells, P.rec_cell, ctx->stream));
+  CK(upload(ctx->gvals, P.rec_g, ctx->stream));
+  CK(upload(ctx->aitems, P.aitems, ctx->stream));
+  CK(upload(ctx->arecptr, P.arec_ptr, ctx->stream));
+  CK(upload(ctx->arec, P.arec, ctx->stream));
+  CK(upload(ctx->acolmap, P.acolmap, ctx->stream));
+  CK(upload(ctx->acells, P.arec_cell, ctx->stream));
+  CK(upload(ctx->agvals, P.arec_g, ctx->stream));
+  CK(upload(ctx->srccell, P.src_cell, ctx->stream));
+  CK(upload(ctx->gx, P.gx, ctx->stream));
+  CK(upload(ctx->gy, P.gy, ctx->stream));
+  CK(upload(ctx->gz, P.gz, ctx->stream));
+  // Scales at receivers (both tables) and sources.
+  GeomArgs ga{vel, rho, (int)P.rec.size(), (int)P.vols.size(), (const long long*)ctx->cells.p,
+              (const float*)ctx->gvals.p, (RecEntry*)ctx->rec.p, (const long long*)ctx->srccell.p,
+              (VolDesc*)ctx->vols.p, P.h, P.dt};
+  CK(launch_geometry(ga, ctx->stream));
+  GeomArgs gb{vel, rho, (int)P.arec.size(), 0, (const long long*)ctx->acells.p,
+              (const float*)ctx->agvals.p, (RecEntry*)ctx->arec.p, nullptr, nullptr, P.h, P.dt};
+  CK(launch_geometry(gb, ctx->stream));
+  // Tensor maps (layout in ShotMaps).
+  std::vector<ShotMaps> maps(P.vols.size());
+  for (size_t s = 0; s < P.vols.size(); ++s) {
+    const VolDesc& V = P.vols[s];
+    auto enc = [&](int slot, const void* base, int bx, int by) {
+      return encode3d(ctx, &maps[s].m[slot], (const float*)base + V.off, V.Nx, V.Ny, V.Nz, V.pitch,
+                      bx, by) == CUDA_SUCCESS;
+    };
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+      ok = ok && enc(2 * b + 0, ctx->pool[b].p, P.tx + 8, P.ty + 8);
+      ok = ok && enc(2 * b + 1, ctx->pool[b].p, P.tx, P.ty);
+      if (need_psi) {
+        ok = ok && enc(4 + 2 * b + 0, ctx->psi[b].p, P.atx + 8, P.aty + 8);
+        ok = ok && enc(4 + 2 * b + 1, ctx->psi[b].p, P.atx, P.aty);
+        ok = ok && enc(9 + b, ctx->pool[b].p, P.atx + 8, P.aty + 8);
+      }
+    }
+    if (need_acc) {
+      ok = ok && enc(8, ctx->acc.p, P.tx, P.ty);
+      ok = ok && enc(11, ctx->acc.p, P.atx, P.aty);
+    }
+    if (!ok) return fail(ctx, MAMUTE_ECUDA, "cuTensorMapEncodeTiled failed (shot %d)", (int)s);
+  }
+  CK(upload(ctx->maps, maps, ctx->stream));
+  std::vector<CoefMaps> cm(2);  // [0]: forward tile boxes, [1]: adjoint tile boxes
+  for (int v = 0; v < 2; ++v) {
+    const int bx = v ? P.atx : P.tx, by = v ? P.aty : P.ty;
+    if (encode3d(ctx, &cm[v].m[0], (const float*)ctx->coefA.p, P.Nx, P.Ny, P.Nz, P.pitchG, bx, by))
+      return fail(ctx, MAMUTE_ECUDA, "cuTensorMapEncodeTiled failed (A)");
+    if (P.dens &&
+        encode3d(ctx, &cm[v].m[1], (const float*)ctx->coefM.p, P.Nx, P.Ny, P.Nz, P.pitchG, bx, by))
+      return fail(ctx, MAMUTE_ECUDA, "cuTensorMapEncodeTiled failed (M)");
+  }
+  CK(upload(ctx->cmaps, cm, ctx->stream));
+  return MAMUTE_OK;
+}
+
+StepArgs fwd_args(mamute_ctx* ctx, const Plan& P, int n, const float* wavelet, float* dout,
+                  int mode) {
+  StepArgs a{};
+  a.items = (const WorkItem*)ctx->items.p;
+  a.vols = (const VolDesc*)ctx->vols.p;
+  a.maps = (const ShotMaps*)ctx->maps.p;
+  a.cmaps = (const CoefMaps*)ctx->cmaps.p;
+  a.gx = (const float*)ctx->gx.p;
+  a.gy = (const float*)ctx->gy.p;
+  a.gz = (const float*)ctx->gz.p;
+  a.fcur = n & 1;
+  a.ucur = 0;
+  a.wn = wavelet[n];
+  a.fout = (float*)ctx->pool[(n + 1) & 1].p;
+  a.acc = (float*)ctx->acc.p;
+  a.tstore = (mode == MODE_FWD_STORE) ? (float*)ctx->tstore.p + (size_t)n * P.term_elems : nullptr;
+  a.rec_ptr = (const int*)ctx->recptr.p;
+  a.rec = (const RecEntry*)ctx->rec.p;
+  a.dout = dout;
+  a.rin = nullptr;
+  a.status = ctx->status;
+  return a;
+}
+
+int finish(mamute_ctx* ctx) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st & kErrTimeout) return fail(ctx, MAMUTE_ETIMEOUT, "a device-side wait ran out");
+  return MAMUTE_OK;
+}
+
+int check_common(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* wavelet) {
+  if (!ctx) return MAMUTE_EINVAL;
+  ctx->err.clear();
+  if (!vel || !wavelet || !g) return fail(ctx, MAMUTE_EINVAL, "NULL vel, wavelet or grid");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  return MAMUTE_OK;
+}
+
+#define TRY(x)               \
+  do {                       \
+    int rc_ = (x);           \
+    if (rc_ != MAMUTE_OK) return rc_; \
+  } while (0)
+
+int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* rho,
+              int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+              const float* rec_xyz, const mamute_opts* opts, float* seis) {
+  TRY(check_common(ctx, g, vel, wavelet));
+  Plan P;
+  TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz,
+                 opts ? opts->aperture : nullptr, P));
+  if (P.ncol > 0 && !seis) return fail(ctx, MAMUTE_EINVAL, "seis is NULL");
+  TRY(check_cfl(ctx, P, vel));
+  const bool ph = opts && opts->phess;
+  TRY(setup(ctx, P, vel, rho, false, ph));
+  const size_t pool = (size_t)P.pool_elems * 4;
+  CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
+  if (ph) CK(cudaMemsetAsync(ctx->acc.p, 0, pool, ctx->stream));
+  CK(ensure(ctx->dint, (size_t)P.nt * std::max(P.ncol, 1) * 4));
+  const int mode = ph ? MODE_FWD_PH : MODE_FWD;
+  for (int n = 0; n < P.nt; ++n) {
+    StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
+    CK(launch_step(a, (int)P.items.size(), P.tx, P.ty, P.dens, mode, ctx->stream));
+  }
+  CK(launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol, seis,
+                     ctx->stream));
+  if (ph) {
+    FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
+                    P.nx, P.ny, P.nz, P.b, P.dt, 1, 0, opts->phess};
+    CK(launch_finalize(fa, ctx->stream));
+  }
+  return finish(ctx);
+}
+
+// Gradient (residual mode, d_in = d_obs) or transposed Jacobian (d_in = d_res).
+int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* rho,
+                 int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+                 const float* rec_xyz, const float* d_in, bool residual_mode,
+                 const mamute_opts* opts, double* misfit, float* grad) {
+  TRY(check_common(ctx, g, vel, wavelet));
+  if (!grad) return fail(ctx, MAMUTE_EINVAL, "grad is NULL");
+  Plan P;
+  TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz,
+                 opts ? opts->aperture : nullptr, P));
+  if (P.ncol > 0 && !d_in) return fail(ctx, MAMUTE_EINVAL, "data is NULL");
+  TRY(check_cfl(ctx, P, vel));
+  const bool ph = opts && opts->phess;
+  TRY(setup(ctx, P, vel, rho, true, true));
+  const size_t pool = (size_t)P.pool_elems * 4;
+  const size_t ncol = std::max(P.ncol, 1);
+  CK(ensure(ctx->dint, (size_t)P.nt * ncol * 4));
+  CK(ensure(ctx->rint, (size_t)P.nt * ncol * 4));
+  CK(ensure(ctx->partial, (size_t)std::max(data_in_blocks(P.nt, P.ncol), 1) * 8));
+  for (int i = 0; i < 2; ++i) {
+    CK(cudaMemsetAsync(ctx->pool[i].p, 0, pool, ctx->stream));
+    CK(cudaMemsetAsync(ctx->psi[i].p, 0, pool, ctx->stream));
+  }
+  CK(cudaMemsetAsync(ctx->acc.p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->misfit.p, 0, 8, ctx->stream));
+  // Storage mode.
+  const int nsnap = opts ? opts->n_snapshots : 0;
+  const bool all_mode = nsnap < 0;
+  int slots = 0;
+  if (all_mode) {
+    CK(ensure(ctx->tstore, (size_t)P.nt * P.term_elems * 4));
+  } else if (nsnap > 0) {
+    slots = std::min(nsnap, P.nt);
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    const double frac = (opts && opts->check_mem > 0.f) ? opts->check_mem : 0.8;
+    const double per = 2.0 * (double)pool;
+    slots = (int)std::min<double>(std::floor(frac * (double)fr / per), (double)P.nt);
+    if (slots < 0) slots = 0;
+  }
+  if (!all_mode && slots > 0) CK(ensure(ctx->slots, (size_t)slots * 2 * pool));
+  const int fmode_first = all_mode ? MODE_FWD_STORE : (ph ? MODE_FWD_PH : MODE_FWD);
+  if (all_mode && ph) return fail(ctx, MAMUTE_EINVAL, "phess is not available with n_snapshots = -1");
+  int recorded = 0;  // steps whose data sample is recorded
+  auto fwd_step = [&](int n, bool first_sweep) -> int {
+    const bool rec = first_sweep && n >= recorded;
+    const int mode = rec ? fmode_first : MODE_FWD;
+    StepArgs a = fwd_args(ctx, P, n, wavelet,
+                          (rec && residual_mode) ? (float*)ctx->dint.p + (size_t)n * P.ncol : nullptr,
+                          mode);
+    CK(launch_step(a, (int)P.items.size(), P.tx, P.ty, P.dens, mode, ctx->stream));
+    if (rec) recorded = n + 1;
+    return MAMUTE_OK;
+  };
+  // Residual in the adjoint tile's column order: r = d - d_obs (or r = d_res).
+  // The forward data are recorded in the forward tile's column order, so they
+  // go through the user layout: seis (scratch) = data_out(d_int), then
+  // r_int = data_in(seis - d_obs) in the adjoint order.
+  auto make_residual = [&]() -> int {
+    if (residual_mode) {
+      CK(ensure(ctx->dtmp, (size_t)P.nt * ncol * 4));
+      CK(launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol,
+                         (float*)ctx->dtmp.p, ctx->stream));
+      // r = seis - d_obs: first r_int = -(-seis) then subtract d_obs.
+      CK(launch_data_in((const float*)ctx->dtmp.p, (const int*)ctx->acolmap.p, P.nt, P.ncol,
+                        nullptr, -1.0f, (float*)ctx->dint.p, nullptr, nullptr, ctx->stream));
+      CK(launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, (const float*)ctx->dint.p,
+                        1.0f, (float*)ctx->rint.p, (double*)ctx->partial.p, (double*)ctx->misfit.p,
+                        ctx->stream));
+    } else {
+      CK(launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, nullptr, -1.0f,
+                        (float*)ctx->rint.p, nullptr, nullptr, ctx->stream));
+    }
+    return MAMUTE_OK;
+  };
+  auto adj_step = [&](int i) -> int {  // adjoint index k = i + 1, imaging against u^i
+    const int k = i + 1;
+    StepArgs a{};
+    a.items = (const WorkItem*)ctx->aitems.p;
+    a.vols = (const VolDesc*)ctx->vols.p;
+    a.maps = (const ShotMaps*)ctx->maps.p;
+    a.cmaps = (const CoefMaps*)ctx->cmaps.p + 1;
+    a.gx = (const float*)ctx->gx.p;
+    a.gy = (const float*)ctx->gy.p;
+    a.gz = (const float*)ctx->gz.p;
+    a.fcur = (k + 1) & 1;
+    a.ucur = i & 1;
+    a.wn = 0.f;
+    a.fout = (float*)ctx->psi[k & 1].p;
+    a.acc = (float*)ctx->acc.p;
+    a.tstore = all_mode ? (float*)ctx->tstore.p + (size_t)i * P.term_elems : nullptr;
+    a.rec_ptr = (const int*)ctx->arecptr.p;
+    a.rec = (const RecEntry*)ctx->arec.p;
+    a.dout = nullptr;
+    a.rin = (const float*)ctx->rint.p + (size_t)i * P.ncol;
+    a.status = ctx->status;
+    CK(launch_step(a, (int)P.aitems.size(), P.atx, P.aty, P.dens,
+                   all_mode ? MODE_ADJ_STORED : MODE_ADJ, ctx->stream));
+    return MAMUTE_OK;
+  };
+  auto begin_adjoint = [&]() -> int {
+    TRY(make_residual());
+    if (ph) {
+      FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(),
+                      vel, P.nx, P.ny, P.nz, P.b, P.dt, 1, 0, opts->phess};
+      CK(launch_finalize(fa, ctx->stream));
+      CK(cudaMemsetAsync(ctx->acc.p, 0, pool, ctx->stream));
+    }
+    return MAMUTE_OK;
+  };
+  if (all_mode) {
+    for (int n = 0; n < P.nt; ++n) TRY(fwd_step(n, true));
+    TRY(begin_adjoint());
+    for (int i = P.nt - 1; i >= 0; --i) TRY(adj_step(i));
+  } else {
+    std::vector<RevAction> acts;
+    long long nf = 0;
+    revolve_plan(P.nt, slots, acts, nf);
+    bool first_reverse = true;
+    for (const RevAction& A : acts) {
+      switch (A.kind) {
+        case REV_ADVANCE:
+          for (int n = A.a; n < A.b; ++n) TRY(fwd_step(n, first_reverse));
+          break;
+        case REV_STORE: {
+          char* dst = (char*)ctx->slots.p + (size_t)A.a * 2 * pool;
+          CK(cudaMemcpyAsync(dst, ctx->pool[0].p, pool, cudaMemcpyDeviceToDevice, ctx->stream));
+          CK(cudaMemcpyAsync(dst + pool, ctx->pool[1].p, pool, cudaMemcpyDeviceToDevice, ctx->stream));
+          break;
+        }
+        case REV_RESTORE:
+          if (A.a < 0) {
+            CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
+            CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
+          } else {
+            const char* src = (const char*)ctx->slots.p + (size_t)A.a * 2 * pool;
+            CK(cudaMemcpyAsync(ctx->pool[0].p, src, pool, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->pool[1].p, src + pool, pool, cudaMemcpyDeviceToDevice, ctx->stream));
+          }
+          break;
+        case REV_REVERSE:
+          if (first_reverse) {
+            // The last forward step yields the final data sample; it
+            // overwrites u^{nt-2}, which no reversal needs.
+            if (recorded < P.nt) TRY(fwd_step(P.nt - 1, true));
+            TRY(begin_adjoint());
+            first_reverse = false;
+          }
+          TRY(adj_step(A.a));
+          break;
+      }
+    }
+  }
+  FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
+                  P.nx, P.ny, P.nz, P.b, P.dt, 0, opts ? opts->zero_top_planes : 0, grad};
+  CK(launch_finalize(fa, ctx->stream));
+  if (misfit) {
+    double J = 0.0;
+    CK(cudaMemcpyAsync(&J, ctx->misfit.p, sizeof J, cudaMemcpyDeviceToHost, ctx->stream));
+    TRY(finish(ctx));
+    *misfit = J;
+    return MAMUTE_OK;
+  }
+  return finish(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mamute_strerror(int code) {
+  switch (code) {
+    case MAMUTE_OK: return "ok";
+    case MAMUTE_EINVAL: return "invalid argument";
+    case MAMUTE_ECFL: return "CFL stability condition violated";
+    case MAMUTE_ENOMEM: return "out of device memory";
+    case MAMUTE_ECUDA: return "CUDA error";
+    case MAMUTE_ETIMEOUT: return "device-side wait timed out";
+    case MAMUTE_EARCH: return "device is not sm_103";
+  }
+  return "unknown error";
+}
+
+const char* mamute_last_error(const mamute_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+double mamute_cfl_limit(void) { return cfl_bound(); }
+
+int mamute_ctx_create(mamute_ctx** out, int device, void* stream) {
+  if (!out) return MAMUTE_EINVAL;
+  *out = nullptr;
+  int cc_major = 0, cc_minor = 0;
+  if (cudaSetDevice(device) != cudaSuccess) return MAMUTE_ECUDA;
+  if (cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, device) != cudaSuccess)
+    return MAMUTE_ECUDA;
+  if (cc_major != 10 || cc_minor != 3) return MAMUTE_EARCH;
+  mamute_ctx* ctx = new mamute_ctx();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    delete ctx;
+    return MAMUTE_ECUDA;
+  }
+  ctx->encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  if (cudaMalloc(&ctx->status, 256) != cudaSuccess || cudaMalloc(&ctx->maxbits, 256) != cudaSuccess ||
+      ensure(ctx->misfit, 256) != cudaSuccess) {
+    mamute_ctx_destroy(ctx);
+    return MAMUTE_ENOMEM;
+  }
+  *out = ctx;
+  return MAMUTE_OK;
+}
+
+void mamute_ctx_destroy(mamute_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  DevBuf* all[] = {&ctx->coefA, &ctx->coefM, &ctx->pool[0], &ctx->pool[1], &ctx->psi[0],
+                   &ctx->psi[1], &ctx->acc, &ctx->slots, &ctx->tstore, &ctx->dint, &ctx->rint, &ctx->dtmp,
+                   &ctx->partial, &ctx->misfit, &ctx->items, &ctx->vols, &ctx->maps, &ctx->cmaps,
+                   &ctx->recptr, &ctx->rec, &ctx->colmap, &ctx->gx, &ctx->gy, &ctx->gz,
+                   &ctx->cells, &ctx->gvals, &ctx->srccell, &ctx->aitems, &ctx->arecptr,
+                   &ctx->arec, &ctx->acolmap, &ctx->acells, &ctx->agvals, &ctx->hvel,
+                   &ctx->hrho, &ctx->hseis, &ctx->hobs, &ctx->hgrad, &ctx->hphess};
+  for (DevBuf* b : all) release(*b);
+  if (ctx->status) cudaFree(ctx->status);
+  if (ctx->maxbits) cudaFree(ctx->maxbits);
+  delete ctx;
+}
+
+int mamute_model(mamute_ctx* ctx, const mamute_grid* grid, const float* vel, const float* rho,
+                 int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+                 const float* rec_xyz, const mamute_opts* opts, float* seis) {
+  return run_model(ctx, grid, vel, rho, n_src, src_xyz, wavelet, rec_offset, rec_xyz, opts, seis);
+}
+
+int mamute_gradient(mamute_ctx* ctx, const mamute_grid* grid, const float* vel, const float* rho,
+                    int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+                    const float* rec_xyz, const float* d_obs, const mamute_opts* opts,
+                    double* misfit, float* grad) {
+  return run_gradient(ctx, grid, vel, rho, n_src, src_xyz, wavelet, rec_offset, rec_xyz, d_obs,
+                      true, opts, misfit, grad);
+}
+
+int mamute_adjoint(mamute_ctx* ctx, const mamute_grid* grid, const float* vel, const float* rho,
+                   int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+                   const float* rec_xyz, const float* d_res, const mamute_opts* opts, float* grad) {
+  return run_gradient(ctx, grid, vel, rho, n_src, src_xyz, wavelet, rec_offset, rec_xyz, d_res,
+                      false, opts, nullptr, grad);
+}
+
+int mamute_model_host(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* rho,
+                      int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
+                      const float* rec_xyz, const mamute_opts* opts, float* seis) {
+  if (!ctx || !g || !vel || !rec_offset || n_src < 1) return MAMUTE_EINVAL;
+  TRY(check_common(ctx, g, vel, wavelet));
+  const size_t nm = (size_t)g->nx * g->ny * g->nz * 4;
+  const size_t ns = (size_t)rec_offset[n_src] * g->nt * 4;
+  CK(ensure(ctx->hvel, nm));
+  CK(cudaMemcpyAsync(ctx->hvel.p, vel, nm, cudaMemcpyHostToDevice, ctx->stream));
+  if (rho) {
+    CK(ensure(ctx->hrho, nm));
+    CK(cudaMemcpyAsync(ctx->hrho.p, rho, nm, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  CK(ensure(ctx->hseis, ns));
+  mamute_opts o{};
+  if (opts) o = *opts;
+  if (opts && opts->phess) {
+    CK(ensure(ctx->hphess, nm));
+    o.phess = (float*)ctx->hphess.p;
+  }
+  TRY(run_model(ctx, g, (const float*)ctx->hvel.p, rho ? (const float*)ctx->hrho.p : nullptr, n_src,
+                src_xyz, wavelet, rec_offset, rec_xyz, opts ? &o : nullptr, (float*)ctx->hseis.p));
+  if (seis && ns) CK(cudaMemcpyAsync(seis, ctx->hseis.p, ns, cudaMemcpyDeviceToHost, ctx->stream));
+  if (opts && opts->phess)
+    CK(cudaMemcpyAsync(opts->phess, ctx->hphess.p, nm, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MAMUTE_OK;
+}
+
+int mamute_gradient_host(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* rho,
+                         int n_src, const float* src_xyz, const float* wavelet,
+                         const int* rec_offset, const float* rec_xyz, const float* d_obs,
+                         const mamute_opts* opts, double* misfit, float* grad) {
+  if (!ctx || !g || !vel || !rec_offset || n_src < 1 || !grad) return MAMUTE_EINVAL;
+  TRY(check_common(ctx, g, vel, wavelet));
+  const size_t nm = (size_t)g->nx * g->ny * g->nz * 4;
+  const size_t ns = (size_t)rec_offset[n_src] * g->nt * 4;
+  CK(ensure(ctx->hvel, nm));
+  CK(cudaMemcpyAsync(ctx->hvel.p, vel, nm, cudaMemcpyHostToDevice, ctx->stream));
+  if (rho) {
+    CK(ensure(ctx->hrho, nm));
+    CK(cudaMemcpyAsync(ctx->hrho.p, rho, nm, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  CK(ensure(ctx->hobs, ns));
+  if (ns) CK(cudaMemcpyAsync(ctx->hobs.p, d_obs, ns, cudaMemcpyHostToDevice, ctx->stream));
+  CK(ensure(ctx->hgrad, nm));
+  mamute_opts o{};
+  if (opts) o = *opts;
+  if (opts && opts->phess) {
+    CK(ensure(ctx->hphess, nm));
+    o.phess = (float*)ctx->hphess.p;
+  }
+  TRY(run_gradient(ctx, g, (const float*)ctx->hvel.p, rho ? (const float*)ctx->hrho.p : nullptr,
+                   n_src, src_xyz, wavelet, rec_offset, rec_xyz, (const float*)ctx->hobs.p, true,
+                   opts ? &o : nullptr, misfit, (float*)ctx->hgrad.p));
+  CK(cudaMemcpyAsync(grad, ctx->hgrad.p, nm, cudaMemcpyDeviceToHost, ctx->stream));
+  if (opts && opts->phess)
+    CK(cudaMemcpyAsync(opts->phess, ctx->hphess.p, nm, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MAMUTE_OK;
+}
+
+int mamute_revolve_plan(int nt, int n_slots, long long* n_forward, int* n_actions, int* actions) {
+  if (nt < 1 || n_slots < 0 || !n_forward || !n_actions) return MAMUTE_EINVAL;
+  std::vector<RevAction> acts;
+  long long nf = 0;
+  if (revolve_plan(nt, n_slots, acts, nf)) return MAMUTE_EINVAL;
+  *n_forward = nf;
+  if (actions) {
+    const int cap = *n_actions;
+    for (int i = 0; i < (int)acts.size() && i < cap; ++i) {
+      actions[3 * i] = acts[i].kind;
+      actions[3 * i + 1] = acts[i].a;
+      actions[3 * i + 2] = acts[i].b;
+    }
+  }
+  *n_actions = (int)acts.size();
+  return MAMUTE_OK;
+}
+
+}  // extern "C"

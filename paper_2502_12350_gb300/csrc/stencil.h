@@ -1,0 +1,44 @@
+// Launch interface of the time-step kernels (internal to libmamute).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mamute {
+
+enum StepMode {
+  MODE_FWD = 0,
+  MODE_FWD_PH = 1,
+  MODE_FWD_STORE = 2,
+  MODE_ADJ = 3,
+  MODE_ADJ_STORED = 4,
+};
+
+struct StepArgs {
+  const WorkItem* items;
+  const VolDesc* vols;
+  const ShotMaps* maps;
+  const CoefMaps* cmaps;
+  const float* gx;        // x profiles of all shots
+  const float* gy;        // y profiles of all shots
+  const float* gz;        // z profile (shared)
+  int fcur;               // buffer holding the current level of the propagated field
+  int ucur;               // buffer holding u^{k-1} (adjoint imaging)
+  float wn;               // wavelet sample of this step (forward)
+  float* fout;            // pool receiving the new level (buffer fcur ^ 1)
+  float* acc;             // accumulator pool (pseudo-Hessian or imaging)
+  float* tstore;          // imaging-term store for this step (all-states mode)
+  const int* rec_ptr;     // per-item per-plane receiver offsets
+  const RecEntry* rec;    // receiver entries
+  float* dout;            // forward: data row of this step (internal columns), may be null
+  const float* rin;       // adjoint: residual row injected at this step
+  int* status;            // error flags
+};
+
+bool tile_supported(int tx, int ty);
+size_t step_smem_bytes(int tx, int ty, bool dens, int mode);
+cudaError_t launch_step(const StepArgs& a, int n_items, int tx, int ty, bool dens, int mode,
+                        cudaStream_t s);
+
+}  // namespace mamute

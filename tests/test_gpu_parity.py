@@ -1,0 +1,203 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: seismogram relative L2 <= 1e-4 against the FP64 oracle and
+<= 1e-5 against the oracle's FP32 mode; gradient cosine >= 0.9999 and
+misfit within 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+from paper_2502_12350_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEIS_TOL_64 = 1e-4
+SEIS_TOL_32 = 1e-5
+GRAD_COS = 0.9999
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_12350_gb300 import build, mamute
+    build.build()
+    c = mamute.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def cosine(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+
+
+def gpu_model(ctx, w, **opts):
+    from paper_2502_12350_gb300 import mamute
+    dev = torch.device("cuda:0")
+    vel = torch.from_numpy(np.ascontiguousarray(w.vel)).to(dev)
+    rho = None if w.rho is None else torch.from_numpy(np.ascontiguousarray(w.rho)).to(dev)
+    seis = torch.full((int(w.rec_offset[-1]), w.nt), float("nan"), device=dev)
+    ctx.model(mamute.grid_of(w), vel, rho, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, seis,
+              aperture=w.aperture, **opts)
+    return seis.cpu().numpy()
+
+
+def gpu_gradient(ctx, w, dobs, **opts):
+    from paper_2502_12350_gb300 import mamute
+    dev = torch.device("cuda:0")
+    vel = torch.from_numpy(np.ascontiguousarray(w.vel)).to(dev)
+    rho = None if w.rho is None else torch.from_numpy(np.ascontiguousarray(w.rho)).to(dev)
+    d = torch.from_numpy(np.ascontiguousarray(dobs, np.float32)).to(dev)
+    grad = torch.full_like(vel, float("nan"))
+    J = ctx.gradient(mamute.grid_of(w), vel, rho, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                     d, grad, aperture=w.aperture, **opts)
+    return J, grad.cpu().numpy()
+
+
+def ogrid(oracle, w):
+    return oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
+
+
+CASES = [
+    dict(seed=0, nx=24, ny=20, nz=18, border=8, nt=60, density=True),
+    dict(seed=1, nx=37, ny=29, nz=21, border=6, nt=70, density=False, n_src=3),
+    dict(seed=2, nx=70, ny=19, nz=33, border=5, nt=50, density=True, n_src=1, n_rec=40),
+    dict(seed=3, nx=9, ny=5, nz=6, border=3, nt=30, density=True),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_model_matches_oracle(ctx, oracle, case):
+    w = synth.small_case(**case)
+    got = gpu_model(ctx, w)
+    og = ogrid(oracle, w)
+    ref64 = oracle.model(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho)
+    ref32 = oracle.model(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho,
+                         precision=32)
+    assert np.isfinite(got).all()
+    assert rel(got, ref64) <= SEIS_TOL_64
+    assert rel(got, ref32) <= SEIS_TOL_32
+
+
+def test_model_forward_64cube_const_density(ctx, oracle):
+    """The 64^3 two-layer workload (500 steps, 16-cell sponge, 64 receivers)."""
+    w = synth.forward_small()
+    got = gpu_model(ctx, w)
+    ref = oracle.model(ogrid(oracle, w), w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz)
+    assert rel(got, ref) <= SEIS_TOL_64
+
+
+@pytest.mark.parametrize("tile", [(64, 16), (64, 8), (32, 16), (32, 8), (128, 8)])
+def test_tiles_bitwise_identical(ctx, monkeypatch, tile):
+    """The arithmetic per point does not depend on the tile shape."""
+    w = synth.small_case(seed=4, nx=45, ny=33, nz=20, border=6, nt=40)
+    ref = gpu_model(ctx, w)
+    monkeypatch.setenv("MAMUTE_TX", str(tile[0]))
+    monkeypatch.setenv("MAMUTE_TY", str(tile[1]))
+    got = gpu_model(ctx, w)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_host_entry_point_matches_device(ctx):
+    from paper_2502_12350_gb300 import mamute
+    w = synth.small_case(seed=5)
+    dev_out = gpu_model(ctx, w)
+    host_out = np.zeros_like(dev_out, dtype=np.float32)
+    ctx.model_host(mamute.grid_of(w), np.ascontiguousarray(w.vel), np.ascontiguousarray(w.rho),
+                   w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, host_out)
+    np.testing.assert_array_equal(host_out, dev_out)
+
+
+def test_pseudo_hessian_matches_oracle(ctx, oracle):
+    w = synth.small_case(seed=6, nt=40)
+    ph = torch.zeros(w.vel.shape, device="cuda:0")
+    gpu_model(ctx, w, phess=ph)
+    _, ref = oracle.model(ogrid(oracle, w), w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                          rho=w.rho, phess=True)
+    assert rel(ph.cpu().numpy(), ref) <= 1e-4
+
+
+def _grad_case(density, seed=7, nt=50):
+    return synth.small_case(seed=seed, nx=26, ny=22, nz=20, border=6, nt=nt, density=density,
+                            n_src=2, n_rec=9)
+
+
+@pytest.mark.parametrize("density", [False, True])
+def test_gradient_matches_oracle(ctx, oracle, density):
+    w = _grad_case(density)
+    og = ogrid(oracle, w)
+    rng = np.random.default_rng(3)
+    vtrue = (w.vel * (1 + 0.05 * rng.standard_normal(w.vel.shape))).astype(np.float32)
+    dobs = oracle.model(og, vtrue, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho)
+    dobs32 = dobs.astype(np.float32)
+    Jr, gr = oracle.gradient(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs32,
+                             rho=w.rho)
+    J, g = gpu_gradient(ctx, w, dobs32, n_snapshots=5)
+    assert np.isfinite(g).all()
+    assert cosine(g, gr) >= GRAD_COS
+    assert abs(J - Jr) <= 1e-4 * Jr
+    assert rel(g, gr) <= 1e-3
+
+
+def test_gradient_bitwise_identical_across_snapshot_modes(ctx):
+    w = _grad_case(True, seed=8, nt=33)
+    dobs = np.zeros((int(w.rec_offset[-1]), w.nt), np.float32)
+    J0, g0 = gpu_gradient(ctx, w, dobs, n_snapshots=-1)
+    for ns in (1, 2, 5, 32, 0):
+        J, g = gpu_gradient(ctx, w, dobs, n_snapshots=ns)
+        assert J == J0
+        np.testing.assert_array_equal(g, g0)
+
+
+def test_adjoint_is_transpose_applied_to_data(ctx, oracle):
+    """mamute_adjoint(d_res) equals the oracle gradient whose residual is d_res."""
+    from paper_2502_12350_gb300 import mamute
+    w = _grad_case(True, seed=9, nt=40)
+    og = ogrid(oracle, w)
+    rng = np.random.default_rng(4)
+    dres = rng.standard_normal((int(w.rec_offset[-1]), w.nt)).astype(np.float32)
+    d = oracle.model(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho)
+    _, gr = oracle.gradient(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                            d - dres.astype(np.float64), rho=w.rho)
+    dev = torch.device("cuda:0")
+    vel = torch.from_numpy(w.vel).to(dev)
+    rho = torch.from_numpy(w.rho).to(dev)
+    grad = torch.zeros_like(vel)
+    ctx.adjoint(mamute.grid_of(w), vel, rho, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                torch.from_numpy(dres).to(dev), grad, n_snapshots=3)
+    assert cosine(grad.cpu().numpy(), gr) >= GRAD_COS
+
+
+def test_zero_top_planes(ctx):
+    w = _grad_case(False, seed=10, nt=30)
+    dobs = np.zeros((int(w.rec_offset[-1]), w.nt), np.float32)
+    _, g0 = gpu_gradient(ctx, w, dobs, n_snapshots=4)
+    _, g3 = gpu_gradient(ctx, w, dobs, n_snapshots=4, zero_top_planes=3)
+    assert np.all(g3[:3] == 0)
+    np.testing.assert_array_equal(g3[3:], g0[3:])
+
+
+def test_errors_are_reported(ctx):
+    from paper_2502_12350_gb300 import mamute
+    w = synth.small_case(seed=12)
+    w.vel = w.vel * 3.0  # c dt / h above 0.4529
+    with pytest.raises(mamute.MamuteError) as e:
+        gpu_model(ctx, w)
+    assert e.value.code == mamute.ECFL
+    w = synth.small_case(seed=12)
+    w.rec_xyz = w.rec_xyz.copy()
+    w.rec_xyz[0, 0] = -50.0
+    with pytest.raises(mamute.MamuteError) as e:
+        gpu_model(ctx, w)
+    assert e.value.code == mamute.EINVAL
+    w = synth.small_case(seed=12)
+    w.aperture = np.array([[1, 10, 0, 10]] * w.n_src, np.int32)
+    with pytest.raises(mamute.MamuteError) as e:
+        gpu_model(ctx, w)
+    assert e.value.code == mamute.EINVAL
