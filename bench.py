@@ -1,0 +1,291 @@
+"""Benchmark of the modelling hot path: Gpt-updates/s and HBM roofline fraction.
+
+Workload: forward modelling with density on a 512x512x256 model
+(576x576x320 padded, 32-cell sponge, h = 12.5 m, dt = 1 ms, 4000 steps),
+seeded layered velocity with Gaussian anomalies, Gardner density, one
+Ricker 10 Hz shot and 256x256 receivers (every 2 cells at z = 4).  One
+benchmark step is one mamute_model call: coefficient preparation, the 4000
+fused time steps (stencil, sponge, source injection, receiver sampling) and
+the seismogram transpose.  Inputs are resident in HBM before the timed
+region and every array is larger than L2.
+
+Prints one JSON line.  --impl reference times the FP64 oracle on the host
+cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpt-updates/s"
+UNIT = "Gpt/s"
+BYTES_PER_PT = 20  # read u^n, u^{n-1}, A, A m2; write u^{n+1}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        loaded = [s for s in sm if mx and s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(nt=None):
+    from paper_2502_12350_gb300 import synth
+    return synth.forward_density() if nt is None else synth.forward_density(nt=nt)
+
+
+def cpu_oracle_rate(w, steps_lo=2, steps_hi=6):
+    """Oracle Gpt/s on the host cores: full grid, the difference of two runs
+    (steps_hi and steps_lo time steps) so that set-up cancels."""
+    from oracle import oracle
+    og = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, steps_hi)
+    wav = w.wavelet[:steps_hi].astype(np.float64)
+    t = []
+    for ns in (steps_lo, steps_hi):
+        og.nt = ns
+        t0 = time.perf_counter()
+        oracle.model(og, w.vel, w.src_xyz, wav[:ns], w.rec_offset, w.rec_xyz, rho=w.rho)
+        t.append(time.perf_counter() - t0)
+    dt = max(t[1] - t[0], 1e-9)
+    rate = w.n_padded * (steps_hi - steps_lo) / dt / 1e9
+    cores = os.cpu_count()
+    sample = (f"{steps_hi - steps_lo} time steps of the full {w.padded[2]}x{w.padded[1]}x"
+              f"{w.padded[0]} padded grid (difference of a {steps_hi}-step and a {steps_lo}-step "
+              f"FP64 oracle run), OpenMP over z planes")
+    return rate, cores, sample, sum(t)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(nt=8)
+    rates = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, 1, 2)
+    for _ in range(args.steps):
+        r, cores, sample, _ = cpu_oracle_rate(w, 1, 3)
+        rates.append(r)
+    v = statistics.median(rates)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "forward_512x512x256_density_4000steps",
+                       "padded": [576, 576, 320], "nt": 4000},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--nt", type=int, default=None, help="time steps (default: the workload's 4000)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2502_12350_gb300 import build, mamute
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    w = workload(args.nt)
+    nt = w.nt
+    g = mamute.grid_of(w)
+    stream = torch.cuda.current_stream(dev)
+    ctx = mamute.Context(local, stream.cuda_stream)
+    lib = mamute.load()
+    import ctypes
+    lib.mamute_ctx_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mamute_ctx_last_timing.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_longlong)]
+    lib.mamute_ctx_set_timing(ctx._h, 1)
+    vel = torch.from_numpy(w.vel).to(dev)
+    rho = torch.from_numpy(w.rho).to(dev)
+    n_rec = int(w.rec_offset[-1])
+    seis = torch.empty((n_rec, nt), device=dev)
+
+    def step():
+        ctx.model(g, vel, rho, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, seis)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    loop_ms, launches, step_launches = [], 0, 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            ms = ctypes.c_double()
+            sl, tl = ctypes.c_longlong(), ctypes.c_longlong()
+            lib.mamute_ctx_last_timing(ctx._h, ctypes.byref(ms), ctypes.byref(sl), ctypes.byref(tl))
+            loop_ms.append(ms.value)
+            launches += tl.value
+            step_launches = sl.value
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pts = w.n_padded * nt
+    value = world * pts * args.steps / (total_ms / 1e3) / 1e9
+
+    # End to end through the host-buffer entry point (pinned host memory).
+    vel_h = torch.from_numpy(w.vel).pin_memory()
+    rho_h = torch.from_numpy(w.rho).pin_memory()
+    seis_h = torch.empty((n_rec, nt), pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def host_step():
+        ctx.model_host(g, vel_h.numpy(), rho_h.numpy(), w.src_xyz, w.wavelet, w.rec_offset,
+                       w.rec_xyz, seis_h.numpy())
+
+    host_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        host_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = world * pts / e2e_s / 1e9
+
+    peak, peak_kind = _peaks()
+    kernel_ms = statistics.median(loop_ms) / max(step_launches, 1)
+    achieved = BYTES_PER_PT * w.n_padded / (kernel_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                traffic = json.load(f).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"forward_512x512x256_density_{nt}steps",
+                   "padded": list(w.padded)[::-1], "nt": nt, "shots": 1, "receivers": n_rec,
+                   "l2": "every array (425 MB) is larger than L2", "tile": [64, 16],
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(vel_h.numel() * 4 + rho_h.numel() * 4),
+                "d2h_bytes_per_step": int(seis_h.numel() * 4)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "step_kernel<64,16,density,forward>",
+                     "bytes_per_point": BYTES_PER_PT, "kernel_ms": kernel_ms},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        r, cores, sample, _ = cpu_oracle_rate(w)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

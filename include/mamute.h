@@ -177,6 +177,17 @@ int mamute_gradient_host(mamute_ctx* ctx, const mamute_grid* grid, const float* 
  * Errors: EINVAL for nt < 1 or n_slots < 0. */
 int mamute_revolve_plan(int nt, int n_slots, long long* n_forward, int* n_actions, int* actions);
 
+/* Timing of the time loop, for benchmarks.  When enabled, each compute call
+ * records CUDA events on the context's stream immediately before the first
+ * and after the last time-step kernel it launches, and counts its kernel
+ * launches.  mamute_ctx_last_timing reports, for the last completed call,
+ * the elapsed milliseconds between the two events, the number of time-step
+ * kernel launches and the number of all kernel launches (NULL outputs are
+ * skipped).  Errors: EINVAL for a NULL context; ECUDA if an event fails. */
+int mamute_ctx_set_timing(mamute_ctx* ctx, int enable);
+int mamute_ctx_last_timing(const mamute_ctx* ctx, double* loop_ms, long long* step_launches,
+                           long long* total_launches);
+
 /* Stability bound used by the CFL check (max(c) dt / h must not exceed it). */
 double mamute_cfl_limit(void);
 

@@ -127,6 +127,7 @@ Medium build_medium(const Grid& gr, const double* vel, const double* rho) {
   M.g.assign(n, 1.0);
   M.srho.assign(n, 1.0);
   const int b = gr.border;
+#pragma omp parallel for schedule(static)
   for (long k = 0; k < d.Nz; ++k)
     for (long j = 0; j < d.Ny; ++j)
       for (long i = 0; i < d.Nx; ++i) {
@@ -145,6 +146,7 @@ Medium build_medium(const Grid& gr, const double* vel, const double* rho) {
     auto val = [&](long i, long j, long k) {
       return s[d.at(clampl(i, 0, d.Nx - 1), clampl(j, 0, d.Ny - 1), clampl(k, 0, d.Nz - 1))];
     };
+#pragma omp parallel for schedule(static)
     for (long k = 0; k < d.Nz; ++k)
       for (long j = 0; j < d.Ny; ++j)
         for (long i = 0; i < d.Nx; ++i)
@@ -153,6 +155,7 @@ Medium build_medium(const Grid& gr, const double* vel, const double* rho) {
   std::vector<double> gx = sponge_profile(d.Nx, b, gr.cerjan);
   std::vector<double> gy = sponge_profile(d.Ny, b, gr.cerjan);
   std::vector<double> gz = sponge_profile(d.Nz, b, gr.cerjan);
+#pragma omp parallel for schedule(static)
   for (long k = 0; k < d.Nz; ++k)
     for (long j = 0; j < d.Ny; ++j)
       for (long i = 0; i < d.Nx; ++i) M.g[d.at(i, j, k)] = gx[i] * gy[j] * gz[k];
@@ -198,6 +201,7 @@ Coef<T> coef_of(const Medium& M, const Grid& gr) {
   Coef<T> c;
   const long n = M.d.n();
   c.A.resize(n); c.B.resize(n); c.m2.resize(n); c.g.resize(n);
+#pragma omp parallel for schedule(static)
   for (long p = 0; p < n; ++p) {
     c.A[p] = (T)M.A[p];
     c.m2[p] = (T)M.m2[p];

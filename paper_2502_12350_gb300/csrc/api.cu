@@ -76,6 +76,12 @@ struct mamute_ctx {
   DevBuf hvel, hrho, hseis, hobs, hgrad, hphess;  // staging for the *_host calls
   int* status = nullptr;
   unsigned int* maxbits = nullptr;
+  // timing hook
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool ev0_set = false;
+  double loop_ms = 0.0;
+  long long step_launches = 0, launches = 0;
 };
 
 namespace {
@@ -325,9 +331,14 @@ struct Run {
   bool adj_maps = false;
 };
 
+cudaError_t aux_count(mamute_ctx* ctx, cudaError_t e) {
+  ++ctx->launches;
+  return e;
+}
+
 int check_cfl(mamute_ctx* ctx, const Plan& P, const float* vel) {
   CK(cudaMemsetAsync(ctx->maxbits, 0, sizeof(unsigned int), ctx->stream));
-  CK(launch_max(vel, (long long)P.nx * P.ny * P.nz, ctx->maxbits, ctx->stream));
+  CK(aux_count(ctx, launch_max(vel, (long long)P.nx * P.ny * P.nz, ctx->maxbits, ctx->stream)));
   unsigned int bits = 0;
   CK(cudaMemcpyAsync(&bits, ctx->maxbits, sizeof bits, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -348,7 +359,7 @@ int setup(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho, bool nee
   if (P.dens) CK(ensure(ctx->coefM, nG * 4));
   CoefPrepArgs ca{vel, rho, P.nx, P.ny, P.nz, P.b, P.Nx, P.Ny, P.Nz, P.pitchG, P.h, P.dt,
                   (float*)ctx->coefA.p, P.dens ? (float*)ctx->coefM.p : nullptr};
-  CK(launch_prep_coef(ca, ctx->stream));
+  CK(aux_count(ctx, launch_prep_coef(ca, ctx->stream)));
   const size_t pool = (size_t)P.pool_elems * 4;
   for (int i = 0; i < 2; ++i) CK(ensure(ctx->pool[i], pool));
   if (need_psi)
@@ -375,10 +386,10 @@ int setup(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho, bool nee
   GeomArgs ga{vel, rho, (int)P.rec.size(), (int)P.vols.size(), (const long long*)ctx->cells.p,
               (const float*)ctx->gvals.p, (RecEntry*)ctx->rec.p, (const long long*)ctx->srccell.p,
               (VolDesc*)ctx->vols.p, P.h, P.dt};
-  CK(launch_geometry(ga, ctx->stream));
+  CK(aux_count(ctx, launch_geometry(ga, ctx->stream)));
   GeomArgs gb{vel, rho, (int)P.arec.size(), 0, (const long long*)ctx->acells.p,
               (const float*)ctx->agvals.p, (RecEntry*)ctx->arec.p, nullptr, nullptr, P.h, P.dt};
-  CK(launch_geometry(gb, ctx->stream));
+  CK(aux_count(ctx, launch_geometry(gb, ctx->stream)));
   // Tensor maps (layout in ShotMaps).
   std::vector<ShotMaps> maps(P.vols.size());
   for (size_t s = 0; s < P.vols.size(); ++s) {
@@ -417,6 +428,21 @@ int setup(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho, bool nee
   return MAMUTE_OK;
 }
 
+// Launch accounting and the timing events around the time loop.
+cudaError_t step_launch(mamute_ctx* ctx, const StepArgs& a, int n_items, int tx, int ty, bool dens,
+                        int mode) {
+  if (ctx->timing && !ctx->ev0_set) {
+    cudaError_t e = cudaEventRecord(ctx->ev0, ctx->stream);
+    if (e != cudaSuccess) return e;
+    ctx->ev0_set = true;
+  }
+  ++ctx->step_launches;
+  ++ctx->launches;
+  cudaError_t e = launch_step(a, n_items, tx, ty, dens, mode, ctx->stream);
+  if (e == cudaSuccess && ctx->timing) e = cudaEventRecord(ctx->ev1, ctx->stream);
+  return e;
+}
+
 StepArgs fwd_args(mamute_ctx* ctx, const Plan& P, int n, const float* wavelet, float* dout,
                   int mode) {
   StepArgs a{};
@@ -445,6 +471,11 @@ int finish(mamute_ctx* ctx) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->timing && ctx->ev0_set) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    ctx->loop_ms = ms;
+  }
   if (st & kErrTimeout) return fail(ctx, MAMUTE_ETIMEOUT, "a device-side wait ran out");
   return MAMUTE_OK;
 }
@@ -452,6 +483,10 @@ int finish(mamute_ctx* ctx) {
 int check_common(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* wavelet) {
   if (!ctx) return MAMUTE_EINVAL;
   ctx->err.clear();
+  ctx->ev0_set = false;
+  ctx->loop_ms = 0.0;
+  ctx->step_launches = 0;
+  ctx->launches = 0;
   if (!vel || !wavelet || !g) return fail(ctx, MAMUTE_EINVAL, "NULL vel, wavelet or grid");
   CK(cudaSetDevice(ctx->device));
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
@@ -483,14 +518,14 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   const int mode = ph ? MODE_FWD_PH : MODE_FWD;
   for (int n = 0; n < P.nt; ++n) {
     StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
-    CK(launch_step(a, (int)P.items.size(), P.tx, P.ty, P.dens, mode, ctx->stream));
+    CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
   }
-  CK(launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol, seis,
-                     ctx->stream));
+  CK(aux_count(ctx, launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol, seis,
+                     ctx->stream)));
   if (ph) {
     FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
                     P.nx, P.ny, P.nz, P.b, P.dt, 1, 0, opts->phess};
-    CK(launch_finalize(fa, ctx->stream));
+    CK(aux_count(ctx, launch_finalize(fa, ctx->stream)));
   }
   return finish(ctx);
 }
@@ -546,7 +581,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     StepArgs a = fwd_args(ctx, P, n, wavelet,
                           (rec && residual_mode) ? (float*)ctx->dint.p + (size_t)n * P.ncol : nullptr,
                           mode);
-    CK(launch_step(a, (int)P.items.size(), P.tx, P.ty, P.dens, mode, ctx->stream));
+    CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
     if (rec) recorded = n + 1;
     return MAMUTE_OK;
   };
@@ -557,17 +592,17 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   auto make_residual = [&]() -> int {
     if (residual_mode) {
       CK(ensure(ctx->dtmp, (size_t)P.nt * ncol * 4));
-      CK(launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol,
-                         (float*)ctx->dtmp.p, ctx->stream));
+      CK(aux_count(ctx, launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol,
+                         (float*)ctx->dtmp.p, ctx->stream)));
       // r = seis - d_obs: first r_int = -(-seis) then subtract d_obs.
-      CK(launch_data_in((const float*)ctx->dtmp.p, (const int*)ctx->acolmap.p, P.nt, P.ncol,
-                        nullptr, -1.0f, (float*)ctx->dint.p, nullptr, nullptr, ctx->stream));
-      CK(launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, (const float*)ctx->dint.p,
+      CK(aux_count(ctx, launch_data_in((const float*)ctx->dtmp.p, (const int*)ctx->acolmap.p, P.nt, P.ncol,
+                        nullptr, -1.0f, (float*)ctx->dint.p, nullptr, nullptr, ctx->stream)));
+      CK(aux_count(ctx, launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, (const float*)ctx->dint.p,
                         1.0f, (float*)ctx->rint.p, (double*)ctx->partial.p, (double*)ctx->misfit.p,
-                        ctx->stream));
+                        ctx->stream)));
     } else {
-      CK(launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, nullptr, -1.0f,
-                        (float*)ctx->rint.p, nullptr, nullptr, ctx->stream));
+      CK(aux_count(ctx, launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, nullptr, -1.0f,
+                        (float*)ctx->rint.p, nullptr, nullptr, ctx->stream)));
     }
     return MAMUTE_OK;
   };
@@ -592,8 +627,8 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     a.dout = nullptr;
     a.rin = (const float*)ctx->rint.p + (size_t)i * P.ncol;
     a.status = ctx->status;
-    CK(launch_step(a, (int)P.aitems.size(), P.atx, P.aty, P.dens,
-                   all_mode ? MODE_ADJ_STORED : MODE_ADJ, ctx->stream));
+    CK(step_launch(ctx, a, (int)P.aitems.size(), P.atx, P.aty, P.dens,
+                   all_mode ? MODE_ADJ_STORED : MODE_ADJ));
     return MAMUTE_OK;
   };
   auto begin_adjoint = [&]() -> int {
@@ -601,7 +636,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     if (ph) {
       FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(),
                       vel, P.nx, P.ny, P.nz, P.b, P.dt, 1, 0, opts->phess};
-      CK(launch_finalize(fa, ctx->stream));
+      CK(aux_count(ctx, launch_finalize(fa, ctx->stream)));
       CK(cudaMemsetAsync(ctx->acc.p, 0, pool, ctx->stream));
     }
     return MAMUTE_OK;
@@ -651,7 +686,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   }
   FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
                   P.nx, P.ny, P.nz, P.b, P.dt, 0, opts ? opts->zero_top_planes : 0, grad};
-  CK(launch_finalize(fa, ctx->stream));
+  CK(aux_count(ctx, launch_finalize(fa, ctx->stream)));
   if (misfit) {
     double J = 0.0;
     CK(cudaMemcpyAsync(&J, ctx->misfit.p, sizeof J, cudaMemcpyDeviceToHost, ctx->stream));
@@ -682,6 +717,26 @@ const char* mamute_strerror(int code) {
 const char* mamute_last_error(const mamute_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
 
 double mamute_cfl_limit(void) { return cfl_bound(); }
+
+int mamute_ctx_set_timing(mamute_ctx* ctx, int enable) {
+  if (!ctx) return MAMUTE_EINVAL;
+  if (enable && !ctx->ev0) {
+    cudaSetDevice(ctx->device);
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess)
+      return fail(ctx, MAMUTE_ECUDA, "cudaEventCreate failed");
+  }
+  ctx->timing = enable != 0;
+  return MAMUTE_OK;
+}
+
+int mamute_ctx_last_timing(const mamute_ctx* ctx, double* loop_ms, long long* step_launches,
+                           long long* total_launches) {
+  if (!ctx) return MAMUTE_EINVAL;
+  if (loop_ms) *loop_ms = ctx->loop_ms;
+  if (step_launches) *step_launches = ctx->step_launches;
+  if (total_launches) *total_launches = ctx->launches;
+  return MAMUTE_OK;
+}
 
 int mamute_ctx_create(mamute_ctx** out, int device, void* stream) {
   if (!out) return MAMUTE_EINVAL;
@@ -728,6 +783,8 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   delete ctx;
 }
 
