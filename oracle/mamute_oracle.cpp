@@ -250,6 +250,34 @@ void adjoint_step(const Dims& d, const Coef<double>& c, double* lam2, const doub
   std::memcpy(lam2, out.data(), sizeof(double) * n);
 }
 
+// Shot domain for an aperture [a0, a1) x [a2, a3) of model columns: the
+// window [a0, a1 + 2 border) x [a2, a3 + 2 border) x [0, Nz) of the global
+// padded grid, with its own sponge profiles at the window faces (the sponge
+// of an interior aperture sees the true model around it).
+Medium window(const Medium& G, const Grid& gr, int a0, int a1, int a2, int a3) {
+  Medium W;
+  const int b = gr.border;
+  W.d.Nx = (a1 - a0) + 2L * b;
+  W.d.Ny = (a3 - a2) + 2L * b;
+  W.d.Nz = G.d.Nz;
+  const long n = W.d.n();
+  W.c.resize(n); W.A.resize(n); W.m2.resize(n); W.g.resize(n); W.srho.resize(n);
+  std::vector<double> gx = sponge_profile(W.d.Nx, b, gr.cerjan);
+  std::vector<double> gy = sponge_profile(W.d.Ny, b, gr.cerjan);
+  std::vector<double> gz = sponge_profile(W.d.Nz, b, gr.cerjan);
+  for (long k = 0; k < W.d.Nz; ++k)
+    for (long j = 0; j < W.d.Ny; ++j)
+      for (long i = 0; i < W.d.Nx; ++i) {
+        long p = W.d.at(i, j, k), q = G.d.at(i + a0, j + a2, k);
+        W.c[p] = G.c[q];
+        W.A[p] = G.A[q];
+        W.m2[p] = G.m2[q];
+        W.srho[p] = G.srho[q];
+        W.g[p] = gx[i] * gy[j] * gz[k];
+      }
+  return W;
+}
+
 struct Shot {
   long src;                 // padded node of the source
   double src_scale;         // dt^2 / (dx dy dz sqrt(rho))
@@ -257,21 +285,55 @@ struct Shot {
   std::vector<double> rsc;  // sqrt(rho) at the receivers
 };
 
-int make_shots(const Grid& gr, const Medium& M, int n_src, const double* src_xyz,
-               const int* rec_offset, const double* rec_xyz, std::vector<Shot>& shots) {
-  shots.clear();
-  for (int s = 0; s < n_src; ++s) {
-    Shot sh;
-    sh.src = node_of(gr, M.d, src_xyz + 3 * s);
-    if (sh.src < 0) return -1;
-    sh.src_scale = gr.dt * gr.dt / (gr.dx * gr.dy * gr.dz * M.srho[sh.src]);
-    for (int r = rec_offset[s]; r < rec_offset[s + 1]; ++r) {
-      long p = node_of(gr, M.d, rec_xyz + 3 * (long)r);
-      if (p < 0) return -1;
-      sh.rec.push_back(p);
-      sh.rsc.push_back(M.srho[p]);
-    }
-    shots.push_back(sh);
+// Node of a coordinate in a shot window; -1 outside the model or aperture.
+long node_in(const Grid& gr, const Dims& d, const double* xyz, const int* ap) {
+  long i = (long)std::floor((xyz[0] - gr.ox) / gr.dx + 0.5);
+  long j = (long)std::floor((xyz[1] - gr.oy) / gr.dy + 0.5);
+  long k = (long)std::floor((xyz[2] - gr.oz) / gr.dz + 0.5);
+  if (i < 0 || i >= gr.nx || j < 0 || j >= gr.ny || k < 0 || k >= gr.nz) return -1;
+  long a0 = 0, a2 = 0;
+  if (ap) {
+    if (i < ap[0] || i >= ap[1] || j < ap[2] || j >= ap[3]) return -1;
+    a0 = ap[0];
+    a2 = ap[2];
+  }
+  return d.at(i + gr.border - a0, j + gr.border - a2, k + gr.border);
+}
+
+// Shot s with its medium (the global one, or its aperture window).
+struct ShotSetup {
+  Medium local;   // used only with an aperture
+  const Medium* M;
+  Shot sh;
+  int a0, a2;
+};
+
+int make_shot(const Grid& gr, const Medium& G, int s, const double* src_xyz, const int* rec_offset,
+              const double* rec_xyz, const int* aperture, ShotSetup& S) {
+  const int* ap = aperture ? aperture + 4 * s : nullptr;
+  if (ap) {
+    if (ap[0] < 0 || ap[1] > gr.nx || ap[0] >= ap[1] || ap[2] < 0 || ap[3] > gr.ny || ap[2] >= ap[3])
+      return -1;
+    S.local = window(G, gr, ap[0], ap[1], ap[2], ap[3]);
+    S.M = &S.local;
+    S.a0 = ap[0];
+    S.a2 = ap[2];
+  } else {
+    S.M = &G;
+    S.a0 = S.a2 = 0;
+  }
+  const Medium& M = *S.M;
+  Shot& sh = S.sh;
+  sh.rec.clear();
+  sh.rsc.clear();
+  sh.src = node_in(gr, M.d, src_xyz + 3 * s, ap);
+  if (sh.src < 0) return -1;
+  sh.src_scale = gr.dt * gr.dt / (gr.dx * gr.dy * gr.dz * M.srho[sh.src]);
+  for (int r = rec_offset[s]; r < rec_offset[s + 1]; ++r) {
+    long p = node_in(gr, M.d, rec_xyz + 3 * (long)r, ap);
+    if (p < 0) return -1;
+    sh.rec.push_back(p);
+    sh.rsc.push_back(M.srho[p]);
   }
   return 0;
 }
@@ -355,33 +417,46 @@ int oracle_advance(const oracle_grid* gr, const double* vel, const double* rho, 
   return 0;
 }
 
+// Adds a shot-window array into the global padded array.
+void scatter_add(const Dims& G, const Dims& W, int a0, int a2, const std::vector<double>& loc,
+                 std::vector<double>& glob) {
+  for (long k = 0; k < W.Nz; ++k)
+    for (long j = 0; j < W.Ny; ++j)
+      for (long i = 0; i < W.Nx; ++i) glob[G.at(i + a0, j + a2, k)] += loc[W.at(i, j, k)];
+}
+
 // Seismic modelling (Algorithm 1): seis[total_rec][nt].  precision 64 or 32.
 // phess (nullable): pseudo-Hessian summed over shots, [nz][ny][nx] interior.
+// aperture (nullable): [n_src][4] model columns per shot (see window()).
 int oracle_model(const oracle_grid* gr, const double* vel, const double* rho, int n_src,
                  const double* src_xyz, const double* wavelet, const int* rec_offset,
-                 const double* rec_xyz, int precision, double* seis, double* phess) {
-  Medium M = build_medium(*gr, vel, rho);
-  std::vector<Shot> shots;
-  if (make_shots(*gr, M, n_src, src_xyz, rec_offset, rec_xyz, shots)) return -1;
+                 const double* rec_xyz, int precision, double* seis, double* phess,
+                 const int* aperture) {
+  Medium G = build_medium(*gr, vel, rho);
   std::vector<double> ph;
-  if (phess) ph.assign(M.d.n(), 0.0);
-  if (precision == 32) {
-    Coef<float> c = coef_of<float>(M, *gr);
-    for (int s = 0; s < n_src; ++s)
-      forward_shot<float>(*gr, M.d, c, shots[s], wavelet, seis + (long)rec_offset[s] * gr->nt,
-                          phess ? ph.data() : nullptr);
-  } else {
-    Coef<double> c = coef_of<double>(M, *gr);
-    for (int s = 0; s < n_src; ++s)
-      forward_shot<double>(*gr, M.d, c, shots[s], wavelet, seis + (long)rec_offset[s] * gr->nt,
-                           phess ? ph.data() : nullptr);
+  if (phess) ph.assign(G.d.n(), 0.0);
+  for (int s = 0; s < n_src; ++s) {
+    ShotSetup S;
+    if (make_shot(*gr, G, s, src_xyz, rec_offset, rec_xyz, aperture, S)) return -1;
+    const Medium& M = *S.M;
+    std::vector<double> phl;
+    if (phess) phl.assign(M.d.n(), 0.0);
+    double* out = seis + (long)rec_offset[s] * gr->nt;
+    if (precision == 32) {
+      Coef<float> c = coef_of<float>(M, *gr);
+      forward_shot<float>(*gr, M.d, c, S.sh, wavelet, out, phess ? phl.data() : nullptr);
+    } else {
+      Coef<double> c = coef_of<double>(M, *gr);
+      forward_shot<double>(*gr, M.d, c, S.sh, wavelet, out, phess ? phl.data() : nullptr);
+    }
+    if (phess) scatter_add(G.d, M.d, S.a0, S.a2, phl, ph);
   }
   if (phess) {
     const int b = gr->border;
     for (long k = 0; k < gr->nz; ++k)
       for (long j = 0; j < gr->ny; ++j)
         for (long i = 0; i < gr->nx; ++i)
-          phess[(k * gr->ny + j) * gr->nx + i] = ph[M.d.at(i + b, j + b, k + b)];
+          phess[(k * gr->ny + j) * gr->nx + i] = ph[G.d.at(i + b, j + b, k + b)];
   }
   return 0;
 }
@@ -395,20 +470,22 @@ int oracle_model(const oracle_grid* gr, const double* vel, const double* rho, in
 int oracle_gradient(const oracle_grid* gr, const double* vel, const double* rho, int n_src,
                     const double* src_xyz, const double* wavelet, const int* rec_offset,
                     const double* rec_xyz, const double* dobs, int snap_every, double* misfit,
-                    double* grad, double* seis_out, double* dwav) {
-  Medium M = build_medium(*gr, vel, rho);
-  std::vector<Shot> shots;
-  if (make_shots(*gr, M, n_src, src_xyz, rec_offset, rec_xyz, shots)) return -1;
-  const Dims& d = M.d;
-  const long n = d.n();
+                    double* grad, double* seis_out, double* dwav, const int* aperture) {
+  Medium G = build_medium(*gr, vel, rho);
   const int nt = gr->nt;
-  Coef<double> c = coef_of<double>(M, *gr);
-  std::vector<double> gA(n, 0.0);
+  std::vector<double> gA_global(G.d.n(), 0.0);
   if (dwav) std::memset(dwav, 0, sizeof(double) * nt);
   double J = 0.0;
   const int seg = snap_every > 0 ? snap_every : nt;
   for (int s = 0; s < n_src; ++s) {
-    const Shot& sh = shots[s];
+    ShotSetup S;
+    if (make_shot(*gr, G, s, src_xyz, rec_offset, rec_xyz, aperture, S)) return -1;
+    const Medium& M = *S.M;
+    const Dims& d = M.d;
+    const long n = d.n();
+    Coef<double> c = coef_of<double>(M, *gr);
+    std::vector<double> gA(n, 0.0);
+    const Shot& sh = S.sh;
     const long nr = (long)sh.rec.size();
     const long roff = rec_offset[s];
     // Forward propagation, with the state pair (u^{m-1}, u^m) saved at every
@@ -469,6 +546,7 @@ int oracle_gradient(const oracle_grid* gr, const double* vel, const double* rho,
             }
       }
     }
+    scatter_add(G.d, d, S.a0, S.a2, gA, gA_global);
   }
   if (misfit) *misfit = J;
   // MultiplyAdjoint: dJ/dc = 2 c dt^2 dJ/dA on the interior.
@@ -476,8 +554,8 @@ int oracle_gradient(const oracle_grid* gr, const double* vel, const double* rho,
   for (long k = 0; k < gr->nz; ++k)
     for (long j = 0; j < gr->ny; ++j)
       for (long i = 0; i < gr->nx; ++i) {
-        long p = d.at(i + b, j + b, k + b);
-        grad[(k * gr->ny + j) * gr->nx + i] = 2.0 * M.c[p] * gr->dt * gr->dt * gA[p];
+        long p = G.d.at(i + b, j + b, k + b);
+        grad[(k * gr->ny + j) * gr->nx + i] = 2.0 * G.c[p] * gr->dt * gr->dt * gA_global[p];
       }
   return 0;
 }

@@ -107,24 +107,29 @@ def _acq(src_xyz, rec_offset, rec_xyz):
     return src_xyz, rec_offset, rec_xyz
 
 
+def _ap(aperture):
+    return None if aperture is None else np.ascontiguousarray(aperture, dtype=np.int32)
+
+
 def model(g: OGrid, vel, src_xyz, wavelet, rec_offset, rec_xyz, rho=None, precision=64,
-          phess=False):
+          phess=False, aperture=None):
     """Seismograms [total_rec][nt] (FP64 array); with phess=True also the
     pseudo-Hessian [nz][ny][nx]."""
     src_xyz, rec_offset, rec_xyz = _acq(src_xyz, rec_offset, rec_xyz)
     vel, rho, wavelet = _f64(vel), _f64(rho), _f64(wavelet)
     seis = np.zeros((int(rec_offset[-1]), g.nt))
     ph = np.zeros((g.nz, g.ny, g.nx)) if phess else None
+    ap = _ap(aperture)
     rc = _load().oracle_model(ctypes.byref(g), _p(vel), _p(rho), ctypes.c_int(len(src_xyz)),
                               _p(src_xyz), _p(wavelet), _p(rec_offset), _p(rec_xyz),
-                              ctypes.c_int(precision), _p(seis), _p(ph))
+                              ctypes.c_int(precision), _p(seis), _p(ph), _p(ap))
     if rc != 0:
         raise ValueError("oracle_model: source or receiver outside the model")
     return (seis, ph) if phess else seis
 
 
 def gradient(g: OGrid, vel, src_xyz, wavelet, rec_offset, rec_xyz, dobs, rho=None,
-             snap_every=0, return_seis=False, return_dwav=False):
+             snap_every=0, return_seis=False, return_dwav=False, aperture=None):
     """(misfit, dJ/dc [nz][ny][nx]) in FP64; optionally also the modelled
     seismograms and dJ/dw (the wavelet sensitivity)."""
     src_xyz, rec_offset, rec_xyz = _acq(src_xyz, rec_offset, rec_xyz)
@@ -133,10 +138,11 @@ def gradient(g: OGrid, vel, src_xyz, wavelet, rec_offset, rec_xyz, dobs, rho=Non
     seis = np.zeros((int(rec_offset[-1]), g.nt)) if return_seis else None
     dwav = np.zeros(g.nt) if return_dwav else None
     J = ctypes.c_double(0.0)
+    ap = _ap(aperture)
     rc = _load().oracle_gradient(ctypes.byref(g), _p(vel), _p(rho), ctypes.c_int(len(src_xyz)),
                                  _p(src_xyz), _p(wavelet), _p(rec_offset), _p(rec_xyz), _p(dobs),
                                  ctypes.c_int(snap_every), ctypes.byref(J), _p(grad), _p(seis),
-                                 _p(dwav))
+                                 _p(dwav), _p(ap))
     if rc != 0:
         raise ValueError("oracle_gradient: source or receiver outside the model")
     out = (J.value, grad)

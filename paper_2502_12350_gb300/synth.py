@@ -192,6 +192,7 @@ def batched_shots(nt: int = 2500, nx=600, ny=600, nz=200, n_side=8, rec_side=96,
             sy = int(round((j + 0.5) * ny / n_side))
             lx, ly = (int(v) for v in rng.integers(ap_min, ap_max + 1, 2))
             x0 = max(0, min(nx - lx, sx - lx // 2)) if lx < nx else 0
+            x0 -= x0 % 4  # window x origin on a 16-byte boundary
             y0 = max(0, min(ny - ly, sy - ly // 2)) if ly < ny else 0
             x1, y1 = min(nx, x0 + lx), min(ny, y0 + ly)
             aps.append((x0, x1, y0, y1))
