@@ -188,6 +188,30 @@ int mamute_ctx_set_timing(mamute_ctx* ctx, int enable);
 int mamute_ctx_last_timing(const mamute_ctx* ctx, double* loop_ms, long long* step_launches,
                            long long* total_launches);
 
+/* Misfit J = 1/2 sum_i (d[i] - d_obs[i])^2 (FP64 sums of FP32 residuals)
+ * for callers that cannot allocate device memory, e.g. because a host
+ * framework's caching allocator already holds the device's memory, or because
+ * a latency-sensitive loop must not pay for cudaMalloc's implicit
+ * synchronisation of the device.  The paper has no counterpart: this is the
+ * reduction that mamute_gradient uses for its misfit, with its per-block
+ * partial sums kept in a fixed file-scope device array (128 KiB on every
+ * device that loads the library, held until the process exits) instead of
+ * context scratch.  No context is needed and nothing is allocated or freed.
+ *   d, d_obs   device [n] float32 (any layout, the same for both)
+ *   n          number of samples, 0 <= n <= MAMUTE_MISFIT_NOALLOC_MAX_SAMPLES
+ *   cuda_stream stream to run on (NULL = legacy default stream); the call
+ *              synchronises it before returning
+ *   misfit     host, receives J
+ * The first call on a device looks up the scratch array's device address
+ * with that device current; later calls on that device reuse it.  All calls
+ * on a device share the one array, so calls that overlap on the GPU (from
+ * several host threads or streams) race and must be serialised by the caller.
+ * Errors: EINVAL for a NULL pointer, n < 0 or n above the limit (nothing is
+ * launched); ECUDA if a launch or the copy of the result fails. */
+#define MAMUTE_MISFIT_NOALLOC_MAX_SAMPLES (16384LL * 16384LL)
+int mamute_misfit_noalloc(const float* d, const float* d_obs, long long n, void* cuda_stream,
+                          double* misfit);
+
 /* Stability bound used by the CFL check (max(c) dt / h must not exceed it). */
 double mamute_cfl_limit(void);
 
