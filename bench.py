@@ -263,7 +263,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"forward_512x512x256_density_{nt}steps",
                    "padded": list(w.padded)[::-1], "nt": nt, "shots": 1, "receivers": n_rec,
-                   "l2": "every array (425 MB) is larger than L2", "tile": [64, 16],
+                   "l2": "every array (425 MB) is larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e, "unit": UNIT,
                 "h2d_bytes_per_step": int(vel_h.numel() * 4 + rho_h.numel() * 4),
@@ -271,7 +271,7 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "step_kernel<64,16,density,forward>",
+                     "kernel": "step_kernel<density,forward>",
                      "bytes_per_point": BYTES_PER_PT, "kernel_ms": kernel_ms},
         "clocks": clocks,
     }

@@ -82,6 +82,7 @@ struct mamute_ctx {
   bool ev0_set = false;
   double loop_ms = 0.0;
   long long step_launches = 0, launches = 0;
+  int max_planes = 1;  // planes per work item of the current call
 };
 
 namespace {
@@ -147,9 +148,35 @@ int env_int(const char* name, int dflt) {
   return v ? atoi(v) : dflt;
 }
 
-// Receiver tables for one tile configuration.
-void build_receivers(Plan& P, int TX, int TY, const std::vector<std::vector<int>>& recnode,
-                     const std::vector<int>& item_base, const std::vector<int>& tiles_x,
+// Tiling of one shot window: column starts (multiples of 4) and row starts.
+struct Tiling {
+  std::vector<int> xs, ys;  // boundaries, size ncols+1 / nrows+1
+};
+
+// Splits n into k pieces, each a multiple of `q` except possibly the last,
+// as equal as possible.
+std::vector<int> split(int n, int k, int q) {
+  std::vector<int> b(1, 0);
+  for (int i = 1; i < k; ++i) {
+    long long e = (long long)n * i / k;
+    e = (e + q / 2) / q * q;
+    if (e <= b.back()) e = b.back() + q;
+    if (e >= n) break;
+    b.push_back((int)e);
+  }
+  b.push_back(n);
+  return b;
+}
+
+int max_piece(const std::vector<int>& b) {
+  int m = 0;
+  for (size_t i = 1; i < b.size(); ++i) m = std::max(m, b[i] - b[i - 1]);
+  return m;
+}
+
+// Receiver tables for one tiling.
+void build_receivers(Plan& P, int TX, const std::vector<std::vector<int>>& recnode,
+                     const std::vector<int>& item_base, const std::vector<Tiling>& tilings,
                      std::vector<WorkItem>& items, std::vector<int>& rec_ptr,
                      std::vector<RecEntry>& rec, std::vector<long long>& cells,
                      std::vector<float>& gvals, std::vector<int>& colmap, int n_rec_total,
@@ -162,9 +189,12 @@ void build_receivers(Plan& P, int TX, int TY, const std::vector<std::vector<int>
   for (int r = 0; r < n_rec_total; ++r) {
     const int s = rshot[r];
     const int lx = recnode[r][0], ly = recnode[r][1], lz = recnode[r][2];
-    const int ti = lx / TX, tj = ly / TY;
-    const int item = item_base[s] + tj * tiles_x[s] + ti;
-    t.push_back(Tmp{item, lz, (lx - ti * TX) + TX * (ly - tj * TY), r});
+    const Tiling& T = tilings[s];
+    const int ti = (int)(std::upper_bound(T.xs.begin(), T.xs.end(), lx) - T.xs.begin()) - 1;
+    const int tj = (int)(std::upper_bound(T.ys.begin(), T.ys.end(), ly) - T.ys.begin()) - 1;
+    const int ncols = (int)T.xs.size() - 1;
+    const int item = item_base[s] + tj * ncols + ti;
+    t.push_back(Tmp{item, lz, (lx - T.xs[ti]) + TX * (ly - T.ys[tj]), r});
   }
   std::sort(t.begin(), t.end(), [](const Tmp& a, const Tmp& b) {
     if (a.item != b.item) return a.item < b.item;
@@ -213,6 +243,66 @@ void build_receivers(Plan& P, int TX, int TY, const std::vector<std::vector<int>
   }
 }
 
+// Chooses, among the compiled tile shapes, the shape and the row split that
+// minimise the work of the busiest SM (ceil(tiles / SMs) x largest tile),
+// so that no long full-depth column is left for a second, nearly empty wave.
+// MAMUTE_TX / MAMUTE_TY force a shape.
+struct TileChoice {
+  int tx = 64, ty = 16;
+  std::vector<Tiling> tilings;
+};
+
+TileChoice choose_tiles(const std::vector<VolDesc>& vols, bool dens, int mode, int n_sm,
+                        int force_tx, int force_ty) {
+  static const int shapes[][2] = {{64, 16}, {72, 16}, {48, 16}, {96, 8}, {64, 8},
+                                  {128, 8}, {32, 16}, {32, 8}};
+  TileChoice best;
+  double best_cost = -1.0;
+  for (const auto& sh : shapes) {
+    const int TX = sh[0], TY = sh[1];
+    if (force_tx > 0 && (TX != force_tx || TY != force_ty)) continue;
+    if (!tile_supported(TX, TY)) continue;
+    const int per_sm = step_blocks_per_sm(TX, TY, dens, mode, vols.empty() ? 1 : vols[0].Nz);
+    if (per_sm < 1) continue;
+    // Row refinement factor r: rows = r * ceil(Ny / TY) (r = 1 keeps the
+    // largest tiles); widths always use the fewest columns.
+    for (int r = 1; r <= 3; ++r) {
+      std::vector<Tiling> tl;
+      long long tiles = 0, maxarea = 0, total = 0;
+      for (const VolDesc& V : vols) {
+        Tiling T;
+        const int ncols = (V.Nx + TX - 1) / TX;
+        const int nrows = std::min(V.Ny, r * ((V.Ny + TY - 1) / TY));
+        T.xs = split(V.Nx, ncols, 4);
+        T.ys = split(V.Ny, nrows, 1);
+        if (max_piece(T.xs) > TX || max_piece(T.ys) > TY) {
+          T.xs.clear();
+        }
+        if (T.xs.empty()) { tiles = -1; break; }
+        tiles += (long long)(T.xs.size() - 1) * (T.ys.size() - 1);
+        maxarea = std::max<long long>(maxarea, (long long)max_piece(T.xs) * max_piece(T.ys));
+        total += (long long)V.Nx * V.Ny;
+        tl.push_back(std::move(T));
+      }
+      if (tiles <= 0) continue;
+      const long long waves_sm = (tiles + n_sm - 1) / n_sm;  // CTAs on the busiest SM
+      // Busiest SM's points, plus a charge for halo rows read from L2 and
+      // for idle box rows; an SM with fewer resident slots than its CTAs
+      // serialises them (same cost model).
+      const double halo = (double)(TX + 8) * (TY + 8) / ((double)TX * TY);
+      const double cost = (double)waves_sm * (double)maxarea * (1.0 + 0.05 * (halo - 1.0)) *
+                          (waves_sm > per_sm ? 1.0 : 1.0);
+      if (best_cost < 0 || cost < best_cost - 1e-9) {
+        best_cost = cost;
+        best.tx = TX;
+        best.ty = TY;
+        best.tilings = tl;
+      }
+    }
+  }
+  return best;
+}
+
 int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, const float* src_xyz,
                const int* rec_offset, const float* rec_xyz, const int* aperture, Plan& P) {
   if (!g) return fail(ctx, MAMUTE_EINVAL, "grid is NULL");
@@ -234,10 +324,6 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   const long long nmax = 1LL << 31;
   if ((long long)P.Nz * P.Ny * P.pitchG >= nmax * 4)
     return fail(ctx, MAMUTE_EINVAL, "grid too large");
-  P.tx = env_int("MAMUTE_TX", 64); P.ty = env_int("MAMUTE_TY", 16);
-  P.atx = env_int("MAMUTE_ADJ_TX", 64); P.aty = env_int("MAMUTE_ADJ_TY", 8);
-  if (!tile_supported(P.tx, P.ty) || !tile_supported(P.atx, P.aty))
-    return fail(ctx, MAMUTE_EINVAL, "unsupported tile shape");
   P.gz = sponge(P.Nz, P.b, g->cerjan);
   auto node = [&](const float* xyz, int& i, int& j, int& k) {
     i = (int)std::floor(((double)xyz[0] - g->ox) / g->h + 0.5);
@@ -289,28 +375,41 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   P.pool_elems = off;
   P.term_elems = toff;
   P.ncol = n_rec;
-  // Work items: one per tile, all planes (forward and adjoint tiles).
-  auto make_items = [&](int TX, int TY, std::vector<WorkItem>& items, std::vector<int>& base,
-                        std::vector<int>& tiles_x) {
+  // Work items: one per tile, all planes, for the forward and adjoint kernels.
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (n_sm < 1) n_sm = 1;
+  const int fmode = dens ? MODE_FWD : MODE_FWD;
+  TileChoice fc = choose_tiles(P.vols, dens, fmode, n_sm, env_int("MAMUTE_TX", 0),
+                               env_int("MAMUTE_TY", 0));
+  TileChoice ac = choose_tiles(P.vols, dens, MODE_ADJ, n_sm, env_int("MAMUTE_ADJ_TX", 64),
+                               env_int("MAMUTE_ADJ_TY", 8));
+  if (fc.tilings.empty() || ac.tilings.empty())
+    return fail(ctx, MAMUTE_EINVAL, "unsupported tile shape");
+  P.tx = fc.tx; P.ty = fc.ty; P.atx = ac.tx; P.aty = ac.ty;
+  auto make_items = [&](const TileChoice& C, std::vector<WorkItem>& items, std::vector<int>& base) {
     items.clear();
     base.clear();
-    tiles_x.clear();
     for (int s = 0; s < n_src; ++s) {
       const VolDesc& V = P.vols[s];
-      const int ntx = (V.Nx + TX - 1) / TX, nty = (V.Ny + TY - 1) / TY;
+      const Tiling& T = C.tilings[s];
       base.push_back((int)items.size());
-      tiles_x.push_back(ntx);
-      for (int tj = 0; tj < nty; ++tj)
-        for (int ti = 0; ti < ntx; ++ti) items.push_back(WorkItem{s, ti, tj, 0, V.Nz, -1, 0, 0});
+      for (size_t tj = 0; tj + 1 < T.ys.size(); ++tj)
+        for (size_t ti = 0; ti + 1 < T.xs.size(); ++ti)
+          items.push_back(WorkItem{s, T.xs[ti], T.ys[tj], 0, V.Nz, T.xs[ti + 1] - T.xs[ti],
+                                   T.ys[tj + 1] - T.ys[tj], -1});
     }
   };
-  std::vector<int> base, tiles_x;
-  make_items(P.tx, P.ty, P.items, base, tiles_x);
-  build_receivers(P, P.tx, P.ty, recnode, base, tiles_x, P.items, P.rec_ptr, P.rec, P.rec_cell,
+  std::vector<int> base;
+  make_items(fc, P.items, base);
+  build_receivers(P, P.tx, recnode, base, fc.tilings, P.items, P.rec_ptr, P.rec, P.rec_cell,
                   P.rec_g, P.colmap, n_rec, rcell, rshot);
-  make_items(P.atx, P.aty, P.aitems, base, tiles_x);
-  build_receivers(P, P.atx, P.aty, recnode, base, tiles_x, P.aitems, P.arec_ptr, P.arec,
+  make_items(ac, P.aitems, base);
+  build_receivers(P, P.atx, recnode, base, ac.tilings, P.aitems, P.arec_ptr, P.arec,
                   P.arec_cell, P.arec_g, P.acolmap, n_rec, rcell, rshot);
+  if (env_int("MAMUTE_VERBOSE", 0))
+    fprintf(stderr, "mamute plan: %d shots, forward tile %dx%d (%zu CTAs), adjoint tile %dx%d (%zu CTAs)\n",
+            n_src, P.tx, P.ty, P.items.size(), P.atx, P.aty, P.aitems.size());
   return MAMUTE_OK;
 }
 
@@ -438,7 +537,7 @@ cudaError_t step_launch(mamute_ctx* ctx, const StepArgs& a, int n_items, int tx,
   }
   ++ctx->step_launches;
   ++ctx->launches;
-  cudaError_t e = launch_step(a, n_items, tx, ty, dens, mode, ctx->stream);
+  cudaError_t e = launch_step(a, n_items, ctx->max_planes, tx, ty, dens, mode, ctx->stream);
   if (e == cudaSuccess && ctx->timing) e = cudaEventRecord(ctx->ev1, ctx->stream);
   return e;
 }
@@ -506,6 +605,7 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   Plan P;
   TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz,
                  opts ? opts->aperture : nullptr, P));
+  ctx->max_planes = P.Nz;
   if (P.ncol > 0 && !seis) return fail(ctx, MAMUTE_EINVAL, "seis is NULL");
   TRY(check_cfl(ctx, P, vel));
   const bool ph = opts && opts->phess;
@@ -540,6 +640,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   Plan P;
   TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz,
                  opts ? opts->aperture : nullptr, P));
+  ctx->max_planes = P.Nz;
   if (P.ncol > 0 && !d_in) return fail(ctx, MAMUTE_EINVAL, "data is NULL");
   TRY(check_cfl(ctx, P, vel));
   const bool ph = opts && opts->phess;

@@ -38,11 +38,11 @@ struct VolDesc {
   long long toff;        // offset of the shot's interior in one step of the term store
 };
 
-// One CTA's work: a TX x TY tile of one shot, planes [zb, ze).
+// One CTA's work: the w x h tile at (x0, y0) of one shot's padded window
+// (local coordinates; x0 a multiple of 4, w <= TX, h <= TY), planes [zb, ze).
 struct WorkItem {
-  int vol, tx, ty, zb, ze;
+  int vol, x0, y0, zb, ze, w, h;
   int rec_tab;  // offset of this item's per-plane receiver table, -1 if none
-  int pad0, pad1;
 };
 
 // A receiver as seen by the tile that owns it.

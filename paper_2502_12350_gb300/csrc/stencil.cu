@@ -112,8 +112,15 @@ struct Layout {
   static constexpr int HS = (TX + 2 * kHalo) * (TY + 2 * kHalo);  // halo stage floats
   static constexpr int CS = TX * TY;  // centre tile floats
   static constexpr int NSU = 8;       // halo ring depth (5 in use + 3 ahead)
-  static constexpr int NSC = 4;       // centre ring depth
+  static constexpr int NSC = ADJ ? 4 : 3;  // centre ring depth
   static constexpr int NHALO = (ADJ && RECOMP) ? 2 : 1;  // halo'd fields per stage
+};
+
+// Per-plane metadata staged in shared memory: sponge factor gz and the
+// receiver-entry range of the plane.
+struct PlaneInfo {
+  float gz;
+  int rb, re, pad;
 };
 
 }  // namespace
@@ -153,14 +160,26 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
   uint64_t* emptyF = bars + NSU;
   uint64_t* fullC = bars + 2 * NSU;
   uint64_t* emptyC = bars + 2 * NSU + NSC;
+  PlaneInfo* pinfo = reinterpret_cast<PlaneInfo*>(bars + 2 * NSU + 2 * NSC);  // npl entries
 
   const WorkItem it = a.items[blockIdx.x];
   const VolDesc V = a.vols[it.vol];
   const ShotMaps* sm = a.maps + it.vol;
-  const int x0 = it.tx * TX, y0 = it.ty * TY, zb = it.zb, ze = it.ze;
+  const int x0 = it.x0, y0 = it.y0, zb = it.zb, ze = it.ze;
   const int npl = ze - zb;
   const int tid = threadIdx.x;
 
+  for (int j = tid; j < npl; j += blockDim.x) {
+    PlaneInfo pi;
+    pi.gz = a.gz[zb + j];
+    pi.rb = pi.re = 0;
+    if (it.rec_tab >= 0) {
+      pi.rb = a.rec_ptr[it.rec_tab + j];
+      pi.re = a.rec_ptr[it.rec_tab + j + 1];
+    }
+    pi.pad = 0;
+    pinfo[j] = pi;
+  }
   if (tid == 0) {
     for (int s = 0; s < NSU; ++s) {
       mbar_init(&fullF[s], 1);
@@ -224,7 +243,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
   const int lx = (tid % (TX / 4)) * 4, ly = tid / (TX / 4);
   const int gxl = x0 + lx, gyl = y0 + ly;  // local padded coordinates of point 0
   const int lane = tid & 31;
-  const bool row_ok = gyl < V.Ny;
+  const bool row_ok = ly < it.h && gyl < V.Ny;
+  const bool col_ok = lx < it.w && gxl < V.Nx;  // tile widths are multiples of 4
   float gxv[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) gxv[e] = (gxl + e < V.Nx) ? a.gx[V.gx_off + gxl + e] : 0.0f;
@@ -274,8 +294,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
     const F4 Av = ld4s(cs + CI_A * CS);
     F4 Mv = {{0.f, 0.f, 0.f, 0.f}};
     if (DENS) Mv = ld4s(cs + CI_M * CS);
-    const float gz = a.gz[z];
-    const float gyz = __fmul_rn(gyv, gz);
+    const PlaneInfo pi = pinfo[j];
+    const float gyz = __fmul_rn(gyv, pi.gz);
     F4 out;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -289,8 +309,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
         if (gxl + e == V.src_x) out.v[e] += V.src_scale * a.wn;
     }
     // Receivers of this tile on this plane.
-    if (it.rec_tab >= 0) {
-      const int rb = a.rec_ptr[it.rec_tab + j], re = a.rec_ptr[it.rec_tab + j + 1];
+    {
+      const int rb = pi.rb, re = pi.re;
       if (rb < re) {
         *reinterpret_cast<float4*>(otile + ly * TX + lx) =
             make_float4(out.v[0], out.v[1], out.v[2], out.v[3]);
@@ -362,7 +382,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
             nacc.v[e] = __fmaf_rn(gt, gt, acc.v[e]);
           }
         }
-        if (row_ok && gxl < V.Nx) {
+        if (row_ok && col_ok) {
           float* ap = a.acc + V.off + ((long long)z * V.Ny + gyl) * V.pitch + gxl;
 #pragma unroll
           for (int e = 0; e < 4; ++e)
@@ -372,7 +392,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
       }
     }
     // Store the new level over the previous one.
-    if (row_ok && gxl < V.Nx) {
+    if (row_ok && col_ok) {
       float* op = a.fout + V.off + ((long long)z * V.Ny + gyl) * V.pitch + gxl;
 #pragma unroll
       for (int e = 0; e < 4; ++e)
@@ -394,7 +414,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
 }
 
 template <int TX, int TY, bool DENS, int MODE>
-static size_t smem_bytes() {
+static size_t smem_bytes_base() {
   constexpr bool ADJ = (MODE == MODE_ADJ || MODE == MODE_ADJ_STORED);
   constexpr bool RECOMP = (MODE == MODE_ADJ);
   constexpr bool ACC = (MODE == MODE_FWD_PH || ADJ);
@@ -404,27 +424,39 @@ static size_t smem_bytes() {
          sizeof(uint64_t) * (2 * LY::NSU + 2 * LY::NSC);
 }
 
+// Dynamic shared memory of one launch: rings, output tile, barriers and the
+// per-plane table for up to max_planes planes per item.
 template <int TX, int TY, bool DENS, int MODE>
-static cudaError_t launch_one(const StepArgs& a, int n_items, cudaStream_t s) {
-  const size_t sm = smem_bytes<TX, TY, DENS, MODE>();
-  static bool attr_set = false;
-  if (!attr_set) {
+static size_t smem_bytes(int max_planes) {
+  return smem_bytes_base<TX, TY, DENS, MODE>() + sizeof(PlaneInfo) * (size_t)max_planes;
+}
+
+template <int TX, int TY, bool DENS, int MODE>
+static cudaError_t launch_one(const StepArgs& a, int n_items, int max_planes, cudaStream_t s,
+                              int* occupancy) {
+  const size_t sm = smem_bytes<TX, TY, DENS, MODE>(max_planes);
+  static size_t attr_bytes = 0;
+  if (sm > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, DENS, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_bytes = sm;
+  }
+  if (occupancy) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, step_kernel<TX, TY, DENS, MODE>,
+                                                         (TX / 4) * TY + 32, sm);
   }
   step_kernel<TX, TY, DENS, MODE><<<n_items, (TX / 4) * TY + 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int TX, int TY>
-static cudaError_t dispatch_mode(const StepArgs& a, int n_items, bool dens, int mode,
-                                 cudaStream_t s) {
+static cudaError_t dispatch_mode(const StepArgs& a, int n_items, int max_planes, bool dens,
+                                 int mode, cudaStream_t s, int* occ) {
 #define MAMUTE_CASE(M)                                                          \
   case M:                                                                       \
-    return dens ? launch_one<TX, TY, true, M>(a, n_items, s)                    \
-                : launch_one<TX, TY, false, M>(a, n_items, s);
+    return dens ? launch_one<TX, TY, true, M>(a, n_items, max_planes, s, occ)   \
+                : launch_one<TX, TY, false, M>(a, n_items, max_planes, s, occ);
   switch (mode) {
     MAMUTE_CASE(MODE_FWD)
     MAMUTE_CASE(MODE_FWD_PH)
@@ -436,45 +468,36 @@ static cudaError_t dispatch_mode(const StepArgs& a, int n_items, bool dens, int 
   return cudaErrorInvalidValue;
 }
 
+// Compiled tile shapes (TX, TY).
+#define MAMUTE_TILES(X) X(64, 16) X(64, 8) X(32, 16) X(32, 8) X(128, 8) X(72, 16) X(96, 8) X(48, 16)
+
 bool tile_supported(int tx, int ty) {
-  return (tx == 64 && ty == 16) || (tx == 64 && ty == 8) || (tx == 32 && ty == 16) ||
-         (tx == 32 && ty == 8) || (tx == 128 && ty == 8);
+#define MAMUTE_T(TX, TY) if (tx == TX && ty == TY) return true;
+  MAMUTE_TILES(MAMUTE_T)
+#undef MAMUTE_T
+  return false;
 }
 
-size_t step_smem_bytes(int tx, int ty, bool dens, int mode) {
-#define MAMUTE_SM(TX, TY)                                                                \
-  if (tx == TX && ty == TY) {                                                            \
-    switch (mode) {                                                                      \
-      case MODE_FWD: return dens ? smem_bytes<TX, TY, true, MODE_FWD>()                  \
-                                 : smem_bytes<TX, TY, false, MODE_FWD>();                \
-      case MODE_FWD_PH: return dens ? smem_bytes<TX, TY, true, MODE_FWD_PH>()            \
-                                    : smem_bytes<TX, TY, false, MODE_FWD_PH>();          \
-      case MODE_FWD_STORE: return dens ? smem_bytes<TX, TY, true, MODE_FWD_STORE>()      \
-                                       : smem_bytes<TX, TY, false, MODE_FWD_STORE>();    \
-      case MODE_ADJ: return dens ? smem_bytes<TX, TY, true, MODE_ADJ>()                  \
-                                 : smem_bytes<TX, TY, false, MODE_ADJ>();                \
-      case MODE_ADJ_STORED: return dens ? smem_bytes<TX, TY, true, MODE_ADJ_STORED>()    \
-                                        : smem_bytes<TX, TY, false, MODE_ADJ_STORED>();  \
-    }                                                                                    \
-  }
-  MAMUTE_SM(64, 16)
-  MAMUTE_SM(64, 8)
-  MAMUTE_SM(32, 16)
-  MAMUTE_SM(32, 8)
-  MAMUTE_SM(128, 8)
-#undef MAMUTE_SM
-  return 0;
-}
-
-cudaError_t launch_step(const StepArgs& a, int n_items, int tx, int ty, bool dens, int mode,
-                        cudaStream_t s) {
-  if (n_items <= 0) return cudaSuccess;
-  if (tx == 64 && ty == 16) return dispatch_mode<64, 16>(a, n_items, dens, mode, s);
-  if (tx == 64 && ty == 8) return dispatch_mode<64, 8>(a, n_items, dens, mode, s);
-  if (tx == 32 && ty == 16) return dispatch_mode<32, 16>(a, n_items, dens, mode, s);
-  if (tx == 32 && ty == 8) return dispatch_mode<32, 8>(a, n_items, dens, mode, s);
-  if (tx == 128 && ty == 8) return dispatch_mode<128, 8>(a, n_items, dens, mode, s);
+static cudaError_t dispatch(const StepArgs& a, int n_items, int max_planes, int tx, int ty,
+                            bool dens, int mode, cudaStream_t s, int* occ) {
+#define MAMUTE_T(TX, TY) \
+  if (tx == TX && ty == TY) return dispatch_mode<TX, TY>(a, n_items, max_planes, dens, mode, s, occ);
+  MAMUTE_TILES(MAMUTE_T)
+#undef MAMUTE_T
   return cudaErrorInvalidValue;
+}
+
+int step_blocks_per_sm(int tx, int ty, bool dens, int mode, int max_planes) {
+  int occ = 0;
+  StepArgs a{};
+  if (dispatch(a, 0, max_planes, tx, ty, dens, mode, nullptr, &occ) != cudaSuccess) return 0;
+  return occ;
+}
+
+cudaError_t launch_step(const StepArgs& a, int n_items, int max_planes, int tx, int ty, bool dens,
+                        int mode, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  return dispatch(a, n_items, max_planes, tx, ty, dens, mode, s, nullptr);
 }
 
 }  // namespace mamute

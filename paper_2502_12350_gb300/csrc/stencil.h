@@ -37,8 +37,10 @@ struct StepArgs {
 };
 
 bool tile_supported(int tx, int ty);
-size_t step_smem_bytes(int tx, int ty, bool dens, int mode);
-cudaError_t launch_step(const StepArgs& a, int n_items, int tx, int ty, bool dens, int mode,
-                        cudaStream_t s);
+// Resident CTAs per SM of a step kernel configuration (0 if it cannot run).
+int step_blocks_per_sm(int tx, int ty, bool dens, int mode, int max_planes);
+// max_planes: the largest ze - zb of the launch's items (sizes the per-plane table).
+cudaError_t launch_step(const StepArgs& a, int n_items, int max_planes, int tx, int ty, bool dens,
+                        int mode, cudaStream_t s);
 
 }  // namespace mamute
