@@ -146,6 +146,76 @@ def run_reference(args):
     return 0
 
 
+def run_gradient_bench(args):
+    """FWI gradient throughput (shots/s and Gpt-updates/s of forward + adjoint
+    work) through mamute_gradient, on one GPU."""
+    import ctypes
+
+    import torch
+
+    from paper_2502_12350_gb300 import build, mamute, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    if args.workload == "gradient_single":
+        w = synth.gradient_single() if args.nt is None else synth.gradient_single(nt=args.nt)
+    else:
+        w = synth.batched_shots() if args.nt is None else synth.batched_shots(nt=args.nt)
+    g = mamute.grid_of(w)
+    stream = torch.cuda.current_stream(dev)
+    ctx = mamute.Context(0, stream.cuda_stream)
+    lib = mamute.load()
+    lib.mamute_ctx_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mamute_ctx_last_timing.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_longlong)]
+    lib.mamute_ctx_set_timing(ctx._h, 1)
+    vtrue = torch.from_numpy(w.vel).to(dev)
+    vinit = torch.from_numpy(w.vel_init).to(dev)
+    n_rec = int(w.rec_offset[-1])
+    dobs = torch.empty((n_rec, w.nt), device=dev)
+    ctx.model(g, vtrue, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs,
+              aperture=w.aperture)
+    grad = torch.empty_like(vinit)
+
+    def step():
+        return ctx.gradient(g, vinit, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs,
+                            grad, aperture=w.aperture, n_snapshots=args.snapshots)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches, steps_per_call = 0, 0
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            J = step()
+            sl, tl = ctypes.c_longlong(), ctypes.c_longlong()
+            lib.mamute_ctx_last_timing(ctx._h, None, ctypes.byref(sl), ctypes.byref(tl))
+            launches += tl.value
+            steps_per_call = sl.value
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if w.aperture is not None:
+        pts_shot = [(a[1] - a[0] + 2 * w.border) * (a[3] - a[2] + 2 * w.border) *
+                    (w.nz + 2 * w.border) for a in w.aperture]
+    else:
+        pts_shot = [w.n_padded] * w.n_src
+    line = {"metric": "FWI gradient shots/s", "value": w.n_src / (ms / 1e3), "unit": "shots/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "shots": w.n_src, "nt": w.nt,
+                       "points_per_step": int(sum(pts_shot)), "snapshots": args.snapshots,
+                       "step_launches_per_gradient": steps_per_call},
+            "gpt_updates_per_s": sum(pts_shot) * steps_per_call / (ms / 1e3) / 1e9,
+            "misfit": J, "gpu_launches": int(launches), "clocks": clk.summary()}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,9 +224,17 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--nt", type=int, default=None, help="time steps (default: the workload's 4000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="model", choices=["model", "gradient_single",
+                                                            "gradient_batched"],
+                    help="model: the headline modelling benchmark; gradient_*: FWI gradient "
+                         "shots/s on the 256^3 single-shot or the 64-shot aperture workload")
+    ap.add_argument("--snapshots", type=int, default=0,
+                    help="gradient workloads: revolve slots (0 = from free memory, -1 = all)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "model":
+        return run_gradient_bench(args)
 
     import torch
     import torch.distributed as dist
