@@ -198,10 +198,10 @@ def run_gradient_bench(args):
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
     if w.aperture is not None:
-        pts_shot = [(a[1] - a[0] + 2 * w.border) * (a[3] - a[2] + 2 * w.border) *
-                    (w.nz + 2 * w.border) for a in w.aperture]
+        pts_shot = [int(a[1] - a[0] + 2 * w.border) * int(a[3] - a[2] + 2 * w.border) *
+                    int(w.nz + 2 * w.border) for a in w.aperture]
     else:
-        pts_shot = [w.n_padded] * w.n_src
+        pts_shot = [int(w.n_padded)] * w.n_src
     line = {"metric": "FWI gradient shots/s", "value": w.n_src / (ms / 1e3), "unit": "shots/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -165,6 +165,77 @@ int mamute_gradient_host(mamute_ctx* ctx, const mamute_grid* grid, const float* 
                          const float* d_obs, const mamute_opts* opts, double* misfit,
                          float* grad);
 
+/* Gauss-Newton diagonal of the misfit (learned-preconditioner labels; the
+ * paper's adjoint-state gradient of Sec. 2.1 / Algorithm 3 linearised):
+ *   H(x) = sum_s sum_r sum_m (d d_{s,r}[m] / d c(x))^2
+ * with the Born data taken over the full linear-convolution length of the
+ * nt-step source-side term and the nt-sample impulse response.  Evaluated
+ * by Parseval over an N_f = 2 nt zero-padded DFT: one forward propagation
+ * per shot and one adjoint propagation per receiver, accumulating DFTs of
+ * the imaging term and of the receiver impulse responses, restricted to the
+ * bins where the wavelet spectrum is at least band_rel of its peak
+ * (band_rel <= 0: all bins).  Every shot must record at the same receivers
+ * (same count and coordinates, in the same order).
+ *   hdiag  device [nz][ny][nx], overwritten
+ * Other arguments as mamute_model (no aperture).  Errors: EINVAL (also for
+ * differing receiver sets or more bins than the kernel supports, 128),
+ * ECFL, ENOMEM, ECUDA, ETIMEOUT. */
+int mamute_gn_diagonal(mamute_ctx* ctx, const mamute_grid* grid, const float* vel,
+                       const float* rho, int n_src, const float* src_xyz, const float* wavelet,
+                       const int* rec_offset, const float* rec_xyz, float band_rel, float* hdiag);
+
+/* ---- Learned preconditioner network (not in the paper: the benchmark spec's
+ * third training-system pattern).  A 4-layer 3x3x3 'same' CNN predicts the
+ * log of the Gauss-Newton diagonal from the velocity and the pseudo-Hessian.
+ * All pointers are device pointers.  Activations are channels-last
+ * [D][H][W][16] BF16 (unsigned short bit patterns, fewer channels zero-
+ * padded); weights are FP32 masters [27 taps][16 out][16 in] with taps in
+ * (dz, dy, dx) order, packed to BF16 for the products; products are BF16 x
+ * BF16 with FP32 accumulation on the tensor cores.  Every call synchronises
+ * the context's stream.  Errors: EINVAL for bad sizes or NULL pointers,
+ * ECUDA, ENOMEM. */
+
+/* y = act(conv(x, w) + bias) with zero padding; act = ReLU if relu != 0;
+ * if mask is given, outputs where mask <= 0 are zeroed (ReLU derivative of
+ * the layer input in the input-gradient pass).  w is a packed weight set
+ * (mamute_conv3d_pack): the forward set computes the layer, the backward set
+ * the gradient with respect to the layer input.  y32 [D][H][W][16] FP32
+ * and/or y16 [D][H][W][16] BF16 receive the result (either may be NULL). */
+int mamute_conv3d(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
+                  const unsigned short* w, const float* bias, int relu,
+                  const unsigned short* mask, float* y32, unsigned short* y16);
+
+/* Weight and bias gradients: gw[tap][o][i] = sum_p gy[p][o] x[p + tap - 1][i],
+ * gb[o] = sum_p gy[p][o] (FP32, summed in a fixed order).
+ *   x, gy  [D][H][W][16] BF16;  gw [27][16][16], gb [16] FP32 */
+int mamute_conv3d_wgrad(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
+                        const unsigned short* gy, float* gw, float* gb);
+
+/* Packs FP32 masters w [27][16][16] into the forward BF16 set fwd (same
+ * layout) and, if bwd is not NULL, the input-gradient set
+ * bwd[26 - tap][i][o] = w[tap][o][i]. */
+int mamute_conv3d_pack(mamute_ctx* ctx, const float* w, unsigned short* fwd,
+                       unsigned short* bwd);
+
+/* Masked mean squared error of channel 0 of out [n][16] FP32 against
+ * target [n]: loss = sum_p m_p (out_p - t_p)^2 / n_mask (FP64 sums; mask
+ * [n] or NULL for all ones) to the host, and its gradient gy [n][16] BF16
+ * (channel 0, other channels zero). */
+int mamute_mse_loss(mamute_ctx* ctx, long long n, const float* out, const float* target,
+                    const float* mask, double n_mask, double* loss, unsigned short* gy);
+
+/* Network inputs and targets for n voxels: x16 [n][16] BF16 with channel 0
+ * = (vel - v_ref) / v_scale and channel 1 = max(log(phess / Pmax),
+ * -log_clip) / log_clip, Pmax = max |phess|; if hdiag and target are given,
+ * target[p] = log(hdiag[p] / Pmax).  pmax (host, may be NULL) receives Pmax. */
+int mamute_nn_features(mamute_ctx* ctx, long long n, const float* vel, const float* phess,
+                       const float* hdiag, float v_ref, float v_scale, float log_clip,
+                       unsigned short* x16, float* target, float* pmax);
+
+/* One Adam step (Kingma and Ba) with bias correction on n FP32 parameters. */
+int mamute_adam(mamute_ctx* ctx, int n, float* p, float* m, float* v, const float* g, float lr,
+                float beta1, float beta2, float eps, int step);
+
 /* Checkpoint schedule (host only, no device work; Sec. 2.1 optimal
  * checkpointing after Griewank and Walther).  Plans the reversal of nt steps
  * from the zero initial state with n_slots checkpoint slots.  Writes the

@@ -560,4 +560,88 @@ int oracle_gradient(const oracle_grid* gr, const double* vel, const double* rho,
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Gauss-Newton diagonal building blocks (no aperture; one medium).
+//
+// Jacobian of the recorded data with respect to A(x): the Born source of
+// step n at x is q[n] = a^n(x) dA(x), a^n = g (lap - m2) u^n, injected like
+// the source into u^{n+1}; with G_{r,x}[k] the sample k recorded at r for a
+// unit injection at x in step 0, dd_r[m]/dA(x) = sum_n G_{r,x}[m - n] a^n(x).
+
+// a^n(x) of one shot for every step n < nt and interior cell: a[nt][nz][ny][nx].
+int oracle_forward_terms(const oracle_grid* gr, const double* vel, const double* rho, int shot,
+                         const double* src_xyz, const double* wavelet, double* a) {
+  Medium M = build_medium(*gr, vel, rho);
+  const Dims& d = M.d;
+  const long n = d.n();
+  Coef<double> c = coef_of<double>(M, *gr);
+  long src = node_in(*gr, d, src_xyz + 3 * shot, nullptr);
+  if (src < 0) return -1;
+  const double sc = gr->dt * gr->dt / (gr->dx * gr->dy * gr->dz * M.srho[src]);
+  const int b = gr->border;
+  const long ni = (long)gr->nx * gr->ny * gr->nz;
+  std::vector<double> u0(n, 0.0), u1(n, 0.0);
+  for (int it = 0; it < gr->nt; ++it) {
+    for (long k = 0; k < gr->nz; ++k)
+      for (long j = 0; j < gr->ny; ++j)
+        for (long i = 0; i < gr->nx; ++i) {
+          long p = d.at(i + b, j + b, k + b);
+          double l = lap_field<double>(d, u1.data(), i + b, j + b, k + b, c.ix2, c.iy2, c.iz2);
+          a[it * ni + (k * gr->ny + j) * gr->nx + i] = c.g[p] * (l - c.m2[p] * u1[p]);
+        }
+    step<double>(d, c, u0.data(), u1.data());
+    u0[src] += sc * wavelet[it];
+    std::swap(u0, u1);
+  }
+  return 0;
+}
+
+// Impulse response of a unit injection into u^1 at interior cell (ci, cj, ck),
+// recorded at n_rec receivers for nt samples: G[n_rec][nt].
+int oracle_cell_response(const oracle_grid* gr, const double* vel, const double* rho, int ci,
+                         int cj, int ck, int n_rec, const double* rec_xyz, double* G) {
+  Medium M = build_medium(*gr, vel, rho);
+  Coef<double> c = coef_of<double>(M, *gr);
+  Shot sh;
+  sh.src = M.d.at(ci + gr->border, cj + gr->border, ck + gr->border);
+  sh.src_scale = 1.0;
+  for (int r = 0; r < n_rec; ++r) {
+    long p = node_in(*gr, M.d, rec_xyz + 3 * r, nullptr);
+    if (p < 0) return -1;
+    sh.rec.push_back(p);
+    sh.rsc.push_back(M.srho[p]);
+  }
+  std::vector<double> imp(gr->nt, 0.0);
+  imp[0] = 1.0;
+  forward_shot<double>(*gr, M.d, c, sh, imp.data(), G, nullptr);
+  return 0;
+}
+
+// The same responses for one receiver and every interior cell at once, from
+// the multiplier recursion driven by a unit data impulse at the last sample:
+// lambda^{nt-j}(x) = G_{r,x}[j].  Output G[nt][nz][ny][nx].
+int oracle_receiver_response(const oracle_grid* gr, const double* vel, const double* rho,
+                             const double* rec_xyz1, double* G) {
+  Medium M = build_medium(*gr, vel, rho);
+  const Dims& d = M.d;
+  const long n = d.n();
+  Coef<double> c = coef_of<double>(M, *gr);
+  long rp = node_in(*gr, d, rec_xyz1, nullptr);
+  if (rp < 0) return -1;
+  const int nt = gr->nt, b = gr->border;
+  const long ni = (long)gr->nx * gr->ny * gr->nz;
+  std::vector<double> lam1(n, 0.0), lam2(n, 0.0);
+  for (int k = nt; k >= 1; --k) {
+    adjoint_step(d, c, lam2.data(), lam1.data());
+    if (k == nt) lam2[rp] += M.srho[rp];
+    std::swap(lam1, lam2);  // lam1 = lambda^k
+    const int j = nt - k;
+    for (long kk = 0; kk < gr->nz; ++kk)
+      for (long jj = 0; jj < gr->ny; ++jj)
+        for (long ii = 0; ii < gr->nx; ++ii)
+          G[j * ni + (kk * gr->ny + jj) * gr->nx + ii] = lam1[d.at(ii + b, jj + b, kk + b)];
+  }
+  return 0;
+}
+
 }  // extern "C"

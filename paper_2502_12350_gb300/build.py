@@ -20,7 +20,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
                   "-diag-suppress", "177", "-I", INCLUDE]
 
-SOURCES = ["stencil.cu", "aux.cu", "api.cu", "revolve.cpp", "noalloc.cu"]
+SOURCES = ["stencil_fwd.cu", "stencil_adj.cu", "stencil.cu", "aux.cu", "gn.cu", "conv.cu",
+           "api.cu", "revolve.cpp", "noalloc.cu"]
 
 
 def _nvcc() -> str:

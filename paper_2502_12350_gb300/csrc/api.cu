@@ -14,6 +14,8 @@
 
 #include "../../include/mamute.h"
 #include "aux.h"
+#include "conv.h"
+#include "gn.h"
 #include "common.cuh"
 #include "revolve.h"
 #include "stencil.h"
@@ -70,10 +72,12 @@ struct mamute_ctx {
   std::string err;
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   // scratch (grow-only)
-  DevBuf coefA, coefM, pool[2], psi[2], acc, slots, tstore, dint, rint, dtmp, partial, misfit;
+  DevBuf coefA, coefM, srho, pool[2], psi[2], acc, slots, tstore, dint, rint, dtmp, partial, misfit;
   DevBuf items, vols, maps, cmaps, recptr, rec, colmap, gx, gy, gz, cells, gvals, srccell,
       aitems, arecptr, arec, acolmap, acells, agvals;
   DevBuf hvel, hrho, hseis, hobs, hgrad, hphess;  // staging for the *_host calls
+  DevBuf gnV, gnRe, gnIm, gnS, gnR, gnW, gnBins, gnWts, gnRow;  // GN-diagonal scratch
+  DevBuf nnPartial, nnLoss;  // network scratch
   int* status = nullptr;
   unsigned int* maxbits = nullptr;
   // timing hook
@@ -286,12 +290,15 @@ TileChoice choose_tiles(const std::vector<VolDesc>& vols, bool dens, int mode, i
       }
       if (tiles <= 0) continue;
       const long long waves_sm = (tiles + n_sm - 1) / n_sm;  // CTAs on the busiest SM
-      // Busiest SM's points, plus a charge for halo rows read from L2 and
-      // for idle box rows; an SM with fewer resident slots than its CTAs
-      // serialises them (same cost model).
-      const double halo = (double)(TX + 8) * (TY + 8) / ((double)TX * TY);
-      const double cost = (double)waves_sm * (double)maxarea * (1.0 + 0.05 * (halo - 1.0)) *
-                          (waves_sm > per_sm ? 1.0 : 1.0);
+      // Resident compute warps on a busy SM: per-SM bandwidth falls off below
+      // about 16 warps (too few loads in flight).
+      const double warps = (double)std::min<long long>(per_sm, waves_sm) * ((TX / 4) * TY / 32);
+      const double occ = std::min(1.0, warps / 16.0);
+      // Boxes always load (TX + 8) x (TY + 8) halo planes and TX x TY centre
+      // tiles; the excess over the useful w x h is served from L2.
+      const double box = (double)(TX + 8) * (TY + 8) + 2.0 * TX * TY;
+      const double over = box / (3.0 * (double)maxarea) - 1.0;
+      const double cost = (double)waves_sm * (double)maxarea * (1.0 + 0.1 * std::max(0.0, over)) / occ;
       if (best_cost < 0 || cost < best_cost - 1e-9) {
         best_cost = cost;
         best.tx = TX;
@@ -382,8 +389,8 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   const int fmode = dens ? MODE_FWD : MODE_FWD;
   TileChoice fc = choose_tiles(P.vols, dens, fmode, n_sm, env_int("MAMUTE_TX", 0),
                                env_int("MAMUTE_TY", 0));
-  TileChoice ac = choose_tiles(P.vols, dens, MODE_ADJ, n_sm, env_int("MAMUTE_ADJ_TX", 64),
-                               env_int("MAMUTE_ADJ_TY", 8));
+  TileChoice ac = choose_tiles(P.vols, dens, MODE_ADJ, n_sm, env_int("MAMUTE_ADJ_TX", 0),
+                               env_int("MAMUTE_ADJ_TY", 0));
   if (fc.tilings.empty() || ac.tilings.empty())
     return fail(ctx, MAMUTE_EINVAL, "unsupported tile shape");
   P.tx = fc.tx; P.ty = fc.ty; P.atx = ac.tx; P.aty = ac.ty;
@@ -456,8 +463,10 @@ int setup(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho, bool nee
   const size_t nG = (size_t)P.Nz * P.Ny * P.pitchG;
   CK(ensure(ctx->coefA, nG * 4));
   if (P.dens) CK(ensure(ctx->coefM, nG * 4));
+  if (P.dens) CK(ensure(ctx->srho, (size_t)P.nx * P.ny * P.nz * 8));
   CoefPrepArgs ca{vel, rho, P.nx, P.ny, P.nz, P.b, P.Nx, P.Ny, P.Nz, P.pitchG, P.h, P.dt,
-                  (float*)ctx->coefA.p, P.dens ? (float*)ctx->coefM.p : nullptr};
+                  (float*)ctx->coefA.p, P.dens ? (float*)ctx->coefM.p : nullptr,
+                  P.dens ? (double*)ctx->srho.p : nullptr};
   CK(aux_count(ctx, launch_prep_coef(ca, ctx->stream)));
   const size_t pool = (size_t)P.pool_elems * 4;
   for (int i = 0; i < 2; ++i) CK(ensure(ctx->pool[i], pool));
@@ -669,10 +678,16 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     CK(cudaMemGetInfo(&fr, &tot));
     const double frac = (opts && opts->check_mem > 0.f) ? opts->check_mem : 0.8;
     const double per = 2.0 * (double)pool;
-    slots = (int)std::min<double>(std::floor(frac * (double)fr / per), (double)P.nt);
+    // Slots this context already holds count as available.
+    const double avail = (double)fr + (double)ctx->slots.bytes;
+    slots = (int)std::min<double>(std::floor(frac * avail / per), (double)P.nt);
     if (slots < 0) slots = 0;
   }
-  if (!all_mode && slots > 0) CK(ensure(ctx->slots, (size_t)slots * 2 * pool));
+  // Fewer slots if the allocation fails (fragmentation or a shared device).
+  while (!all_mode && slots > 0 && ensure(ctx->slots, (size_t)slots * 2 * pool) != cudaSuccess) {
+    cudaGetLastError();
+    slots = slots * 3 / 4;
+  }
   const int fmode_first = all_mode ? MODE_FWD_STORE : (ph ? MODE_FWD_PH : MODE_FWD);
   if (all_mode && ph) return fail(ctx, MAMUTE_EINVAL, "phess is not available with n_snapshots = -1");
   int recorded = 0;  // steps whose data sample is recorded
@@ -798,6 +813,152 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   return finish(ctx);
 }
 
+// Gauss-Newton diagonal (see gn.cu): forward propagation of each shot storing
+// the imaging term, adjoint propagation of a unit data impulse at each
+// receiver storing psi, DFT accumulation in blocks of kT steps, Parseval.
+int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* rho, int n_src,
+           const float* src_xyz, const float* wavelet, const int* rec_offset, const float* rec_xyz,
+           float band_rel, float* hdiag) {
+  TRY(check_common(ctx, g, vel, wavelet));
+  if (!hdiag) return fail(ctx, MAMUTE_EINVAL, "hdiag is NULL");
+  if (!rec_offset || n_src < 1) return fail(ctx, MAMUTE_EINVAL, "no shots");
+  const int nr0 = rec_offset[1] - rec_offset[0];
+  if (nr0 < 1) return fail(ctx, MAMUTE_EINVAL, "no receivers");
+  for (int s = 1; s < n_src; ++s) {
+    if (rec_offset[s + 1] - rec_offset[s] != nr0)
+      return fail(ctx, MAMUTE_EINVAL, "every shot must record at the same receivers");
+    for (int r = 0; r < nr0; ++r)
+      for (int d = 0; d < 3; ++d)
+        if (rec_xyz[3 * (long long)(rec_offset[s] + r) + d] != rec_xyz[3 * (long long)r + d])
+          return fail(ctx, MAMUTE_EINVAL, "every shot must record at the same receivers");
+  }
+  Plan P;
+  TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz, nullptr, P));
+  ctx->max_planes = P.Nz;
+  TRY(check_cfl(ctx, P, vel));
+  TRY(setup(ctx, P, vel, rho, true, false));
+  // Retained bins of the N_f = 2 nt DFT: where the wavelet spectrum is at
+  // least band_rel of its peak (all bins for band_rel <= 0).
+  const int nt = P.nt, nf = 2 * nt;
+  std::vector<double> mag(nt + 1);
+  double mmax = 0.0;
+  for (int k = 0; k <= nt; ++k) {
+    double re = 0.0, im = 0.0;
+    for (int n = 0; n < nt; ++n) {
+      const double ph = -2.0 * M_PI * (double)(((long long)k * n) % nf) / nf;
+      re += wavelet[n] * std::cos(ph);
+      im += wavelet[n] * std::sin(ph);
+    }
+    mag[k] = std::sqrt(re * re + im * im);
+    mmax = std::max(mmax, mag[k]);
+  }
+  std::vector<int> bins;
+  std::vector<float> wts;
+  for (int k = 0; k <= nt; ++k)
+    if (band_rel <= 0.f || mag[k] >= band_rel * mmax) {
+      bins.push_back(k);
+      wts.push_back((k == 0 || k == nt) ? 1.0f : 2.0f);
+    }
+  const int nb = (int)bins.size();
+  if (nb > dft_max_bins())
+    return fail(ctx, MAMUTE_EINVAL, "%d frequency bins exceed the limit %d (raise band_rel)", nb,
+                dft_max_bins());
+  const int kT = 32;
+  const long long N = (long long)P.nx * P.ny * P.nz;
+  CK(ensure(ctx->gnV, (size_t)kT * N * 4));
+  CK(ensure(ctx->gnRe, (size_t)nb * N * 4));
+  CK(ensure(ctx->gnIm, (size_t)nb * N * 4));
+  CK(ensure(ctx->gnS, (size_t)nb * N * 4));
+  CK(ensure(ctx->gnR, (size_t)nb * N * 4));
+  CK(ensure(ctx->gnW, (size_t)kT * nb * 8));
+  CK(upload(ctx->gnBins, bins, ctx->stream));
+  CK(upload(ctx->gnWts, wts, ctx->stream));
+  CK(ensure(ctx->gnRow, (size_t)2 * std::max(P.ncol, 1) * 4));
+  for (DevBuf* b : {&ctx->gnRe, &ctx->gnIm, &ctx->gnS, &ctx->gnR})
+    CK(cudaMemsetAsync(b->p, 0, (size_t)nb * N * 4, ctx->stream));
+  float* V = (float*)ctx->gnV.p;
+  float* re = (float*)ctx->gnRe.p;
+  float* im = (float*)ctx->gnIm.p;
+  const size_t pool = (size_t)P.pool_elems * 4;
+  auto flush = [&](int upto, int& done) -> int {  // DFT of samples [done, upto)
+    if (upto > done) {
+      CK(aux_count(ctx, launch_dft(V, N, upto - done, done, nf, (const int*)ctx->gnBins.p, nb,
+                                   (float2*)ctx->gnW.p, re, im, ctx->stream)));
+      done = upto;
+    }
+    return MAMUTE_OK;
+  };
+  // Item ranges per shot (items are grouped by shot).
+  auto range = [](const std::vector<WorkItem>& items, int s, int& b, int& e) {
+    b = 0;
+    while (b < (int)items.size() && items[b].vol < s) ++b;
+    e = b;
+    while (e < (int)items.size() && items[e].vol == s) ++e;
+  };
+  // Source side.
+  for (int s = 0; s < n_src; ++s) {
+    int ib, ie;
+    range(P.items, s, ib, ie);
+    CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
+    CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
+    int done = 0;
+    for (int n = 0; n < nt; ++n) {
+      StepArgs a = fwd_args(ctx, P, n, wavelet, nullptr, MODE_FWD_STORE);
+      a.items = (const WorkItem*)ctx->items.p + ib;
+      a.tstore = V + (size_t)(n % kT) * N - P.vols[s].toff;
+      CK(step_launch(ctx, a, ie - ib, P.tx, P.ty, P.dens, MODE_FWD_STORE));
+      if ((n + 1) % kT == 0) TRY(flush(n + 1, done));
+    }
+    TRY(flush(nt, done));
+    CK(aux_count(ctx, launch_power((long long)nb * N, re, im, (float*)ctx->gnS.p, ctx->stream)));
+  }
+  // Receiver side: shot 0's geometry, a unit data impulse at the last sample.
+  int ib, ie;
+  range(P.aitems, 0, ib, ie);
+  float* zero_row = (float*)ctx->gnRow.p;
+  float* imp_row = zero_row + std::max(P.ncol, 1);
+  CK(cudaMemsetAsync(ctx->gnRow.p, 0, (size_t)2 * std::max(P.ncol, 1) * 4, ctx->stream));
+  for (int r = rec_offset[0]; r < rec_offset[1]; ++r) {
+    int col = -1;
+    for (int c = 0; c < P.ncol; ++c)
+      if (P.acolmap[c] == r) col = c;
+    if (col < 0) return fail(ctx, MAMUTE_EINVAL, "receiver %d not planned", r);
+    const float one = 1.0f;
+    CK(cudaMemsetAsync(imp_row, 0, (size_t)std::max(P.ncol, 1) * 4, ctx->stream));
+    CK(cudaMemcpyAsync(imp_row + col, &one, 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->psi[0].p, 0, pool, ctx->stream));
+    CK(cudaMemsetAsync(ctx->psi[1].p, 0, pool, ctx->stream));
+    int done = 0;
+    for (int j = 0; j < nt; ++j) {  // adjoint index k = nt - j holds G[j]
+      const int k = nt - j;
+      StepArgs a{};
+      a.items = (const WorkItem*)ctx->aitems.p + ib;
+      a.vols = (const VolDesc*)ctx->vols.p;
+      a.maps = (const ShotMaps*)ctx->maps.p;
+      a.cmaps = (const CoefMaps*)ctx->cmaps.p + 1;
+      a.gx = (const float*)ctx->gx.p;
+      a.gy = (const float*)ctx->gy.p;
+      a.gz = (const float*)ctx->gz.p;
+      a.fcur = (k + 1) & 1;
+      a.ucur = 0;
+      a.fout = (float*)ctx->psi[k & 1].p;
+      a.tstore = V + (size_t)(j % kT) * N - P.vols[0].toff;
+      a.rec_ptr = (const int*)ctx->arecptr.p;
+      a.rec = (const RecEntry*)ctx->arec.p;
+      a.rin = (j == 0) ? imp_row : zero_row;
+      a.status = ctx->status;
+      CK(step_launch(ctx, a, ie - ib, P.atx, P.aty, P.dens, MODE_ADJ_TERM));
+      if ((j + 1) % kT == 0) TRY(flush(j + 1, done));
+    }
+    TRY(flush(nt, done));
+    CK(aux_count(ctx, launch_power((long long)nb * N, re, im, (float*)ctx->gnR.p, ctx->stream)));
+    CK(cudaStreamSynchronize(ctx->stream));  // the host impulse value is reused
+  }
+  CK(aux_count(ctx, launch_assemble(N, nb, (const float*)ctx->gnWts.p, (const float*)ctx->gnR.p,
+                                    (const float*)ctx->gnS.p, vel, P.dt, nf, hdiag, ctx->stream)));
+  return finish(ctx);
+}
+
 }  // namespace
 
 extern "C" {
@@ -874,13 +1035,15 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
-  DevBuf* all[] = {&ctx->coefA, &ctx->coefM, &ctx->pool[0], &ctx->pool[1], &ctx->psi[0],
+  DevBuf* all[] = {&ctx->coefA, &ctx->coefM, &ctx->srho, &ctx->pool[0], &ctx->pool[1], &ctx->psi[0],
                    &ctx->psi[1], &ctx->acc, &ctx->slots, &ctx->tstore, &ctx->dint, &ctx->rint, &ctx->dtmp,
                    &ctx->partial, &ctx->misfit, &ctx->items, &ctx->vols, &ctx->maps, &ctx->cmaps,
                    &ctx->recptr, &ctx->rec, &ctx->colmap, &ctx->gx, &ctx->gy, &ctx->gz,
                    &ctx->cells, &ctx->gvals, &ctx->srccell, &ctx->aitems, &ctx->arecptr,
                    &ctx->arec, &ctx->acolmap, &ctx->acells, &ctx->agvals, &ctx->hvel,
-                   &ctx->hrho, &ctx->hseis, &ctx->hobs, &ctx->hgrad, &ctx->hphess};
+                   &ctx->hrho, &ctx->hseis, &ctx->hobs, &ctx->hgrad, &ctx->hphess,
+                   &ctx->gnV, &ctx->gnRe, &ctx->gnIm, &ctx->gnS, &ctx->gnR, &ctx->gnW,
+                   &ctx->gnBins, &ctx->gnWts, &ctx->gnRow, &ctx->nnPartial, &ctx->nnLoss};
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);
@@ -970,6 +1133,101 @@ int mamute_gradient_host(mamute_ctx* ctx, const mamute_grid* g, const float* vel
     CK(cudaMemcpyAsync(opts->phess, ctx->hphess.p, nm, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return MAMUTE_OK;
+}
+
+int mamute_gn_diagonal(mamute_ctx* ctx, const mamute_grid* grid, const float* vel,
+                       const float* rho, int n_src, const float* src_xyz, const float* wavelet,
+                       const int* rec_offset, const float* rec_xyz, float band_rel, float* hdiag) {
+  return run_gn(ctx, grid, vel, rho, n_src, src_xyz, wavelet, rec_offset, rec_xyz, band_rel, hdiag);
+}
+
+// ------------------------------------------------------------ network kernels
+static int nn_begin(mamute_ctx* ctx) {
+  if (!ctx) return MAMUTE_EINVAL;
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  return MAMUTE_OK;
+}
+
+static int nn_end(mamute_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MAMUTE_OK;
+}
+
+int mamute_conv3d(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
+                  const unsigned short* w, const float* bias, int relu,
+                  const unsigned short* mask, float* y32, unsigned short* y16) {
+  TRY(nn_begin(ctx));
+  if (D < 1 || H < 1 || W < 1 || !x || !w || (!y32 && !y16))
+    return fail(ctx, MAMUTE_EINVAL, "conv3d: bad arguments");
+  ConvArgs a{x, w, bias, relu, mask, y32, y16, D, H, W};
+  CK(launch_conv(a, ctx->stream));
+  return nn_end(ctx);
+}
+
+int mamute_conv3d_wgrad(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
+                        const unsigned short* gy, float* gw, float* gb) {
+  TRY(nn_begin(ctx));
+  if (D < 1 || H < 1 || W < 1 || !x || !gy || !gw || !gb)
+    return fail(ctx, MAMUTE_EINVAL, "conv3d_wgrad: bad arguments");
+  CK(ensure(ctx->nnPartial, wgrad_partial_floats() * 4));
+  WgradArgs a{x, gy, (float*)ctx->nnPartial.p, D, H, W};
+  CK(launch_wgrad(a, gw, gb, ctx->stream));
+  return nn_end(ctx);
+}
+
+int mamute_conv3d_pack(mamute_ctx* ctx, const float* w, unsigned short* fwd,
+                       unsigned short* bwd) {
+  TRY(nn_begin(ctx));
+  if (!w || !fwd) return fail(ctx, MAMUTE_EINVAL, "conv3d_pack: bad arguments");
+  CK(launch_pack(w, fwd, bwd, ctx->stream));
+  return nn_end(ctx);
+}
+
+int mamute_mse_loss(mamute_ctx* ctx, long long n, const float* out, const float* target,
+                    const float* mask, double n_mask, double* loss, unsigned short* gy) {
+  TRY(nn_begin(ctx));
+  if (n < 1 || !out || !target || !gy || !(n_mask > 0))
+    return fail(ctx, MAMUTE_EINVAL, "mse_loss: bad arguments");
+  CK(ensure(ctx->nnPartial, std::max<size_t>(wgrad_partial_floats() * 4, (size_t)mse_blocks() * 8)));
+  CK(ensure(ctx->nnLoss, 256));
+  CK(launch_mse(n, out, target, mask, n_mask, gy, (double*)ctx->nnPartial.p,
+                (double*)ctx->nnLoss.p, ctx->stream));
+  if (loss) {
+    double L = 0.0;
+    CK(cudaMemcpyAsync(&L, ctx->nnLoss.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    TRY(nn_end(ctx));
+    *loss = L;
+    return MAMUTE_OK;
+  }
+  return nn_end(ctx);
+}
+
+int mamute_adam(mamute_ctx* ctx, int n, float* p, float* m, float* v, const float* g, float lr,
+                float beta1, float beta2, float eps, int step) {
+  TRY(nn_begin(ctx));
+  if (n < 1 || !p || !m || !v || !g || step < 1)
+    return fail(ctx, MAMUTE_EINVAL, "adam: bad arguments");
+  CK(launch_adam(n, p, m, v, g, lr, beta1, beta2, eps, step, ctx->stream));
+  return nn_end(ctx);
+}
+
+int mamute_nn_features(mamute_ctx* ctx, long long n, const float* vel, const float* phess,
+                       const float* hdiag, float v_ref, float v_scale, float log_clip,
+                       unsigned short* x16, float* target, float* pmax) {
+  TRY(nn_begin(ctx));
+  if (n < 1 || !vel || !phess || !x16 || !(v_scale > 0.f) || !(log_clip > 0.f))
+    return fail(ctx, MAMUTE_EINVAL, "nn_features: bad arguments");
+  CK(launch_features(n, vel, phess, hdiag, ctx->maxbits, v_ref, v_scale, log_clip, x16, target,
+                     ctx->stream));
+  if (pmax) {
+    unsigned int bits = 0;
+    CK(cudaMemcpyAsync(&bits, ctx->maxbits, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    TRY(nn_end(ctx));
+    std::memcpy(pmax, &bits, 4);
+    return MAMUTE_OK;
+  }
+  return nn_end(ctx);
 }
 
 int mamute_revolve_plan(int nt, int n_slots, long long* n_forward, int* n_actions, int* actions) {

@@ -9,11 +9,18 @@ namespace {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// sqrt(rho) of the edge-replicated padded model at any integer node.
-__device__ __forceinline__ double srho_at(const float* rho, int nx, int ny, int nz, int b, int i,
+// sqrt(rho) of the edge-replicated padded model at any integer node, from
+// the per-cell FP64 square roots.
+__device__ __forceinline__ double srho_at(const double* srho, int nx, int ny, int nz, int b, int i,
                                           int j, int k) {
   const int mi = clampi(i - b, 0, nx - 1), mj = clampi(j - b, 0, ny - 1), mk = clampi(k - b, 0, nz - 1);
-  return sqrt((double)rho[((long long)mk * ny + mj) * nx + mi]);
+  return srho[((long long)mk * ny + mj) * nx + mi];
+}
+
+__global__ void sqrt_kernel(const float* __restrict__ rho, long long n, double* __restrict__ out) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x)
+    out[p] = sqrt((double)rho[p]);
 }
 
 // A = c^2 dt^2 / h^2 and M = c^2 dt^2 m2, m2 = lap(sqrt rho) / sqrt rho
@@ -38,15 +45,16 @@ __global__ void prep_coef_kernel(CoefPrepArgs a) {
     const double A2 = cv * cv * a.dt * a.dt;
     a.A[p] = (float)(A2 / (a.h * a.h));
     if (a.M) {
-      const double s0 = srho_at(a.rho, a.nx, a.ny, a.nz, b, i, j, k);
+      const double* sr = a.srho;
+      const double s0 = srho_at(sr, a.nx, a.ny, a.nz, b, i, j, k);
       double sx = c[0] * s0, sy = c[0] * s0, sz = c[0] * s0;
       for (int m = 1; m <= 4; ++m) {
-        sx += c[m] * (srho_at(a.rho, a.nx, a.ny, a.nz, b, i - m, j, k) +
-                      srho_at(a.rho, a.nx, a.ny, a.nz, b, i + m, j, k));
-        sy += c[m] * (srho_at(a.rho, a.nx, a.ny, a.nz, b, i, j - m, k) +
-                      srho_at(a.rho, a.nx, a.ny, a.nz, b, i, j + m, k));
-        sz += c[m] * (srho_at(a.rho, a.nx, a.ny, a.nz, b, i, j, k - m) +
-                      srho_at(a.rho, a.nx, a.ny, a.nz, b, i, j, k + m));
+        sx += c[m] * (srho_at(sr, a.nx, a.ny, a.nz, b, i - m, j, k) +
+                      srho_at(sr, a.nx, a.ny, a.nz, b, i + m, j, k));
+        sy += c[m] * (srho_at(sr, a.nx, a.ny, a.nz, b, i, j - m, k) +
+                      srho_at(sr, a.nx, a.ny, a.nz, b, i, j + m, k));
+        sz += c[m] * (srho_at(sr, a.nx, a.ny, a.nz, b, i, j, k - m) +
+                      srho_at(sr, a.nx, a.ny, a.nz, b, i, j, k + m));
       }
       const double m2 = (sx + sy + sz) / (a.h * a.h) / s0;
       a.M[p] = (float)(A2 * m2);
@@ -176,6 +184,12 @@ int grid_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_prep_coef(const CoefPrepArgs& a, cudaStream_t s) {
+  if (a.M) {
+    const long long nm = (long long)a.nx * a.ny * a.nz;
+    sqrt_kernel<<<grid_for(nm, 256), 256, 0, s>>>(a.rho, nm, a.srho);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const long long n = (long long)a.Nz * a.Ny * a.pitch;
   prep_coef_kernel<<<grid_for(n, 256), 256, 0, s>>>(a);
   return cudaGetLastError();

@@ -15,6 +15,7 @@ struct CoefPrepArgs {
   double h, dt;
   float* A;           // [Nz][Ny][pitch]
   float* M;           // [Nz][Ny][pitch] or null
+  double* srho;       // scratch [nz][ny][nx] (density only)
 };
 
 struct GeomArgs {

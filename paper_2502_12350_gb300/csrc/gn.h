@@ -1,0 +1,20 @@
+// Launch interface of the Gauss-Newton diagonal kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mamute {
+
+size_t dft_smem_bytes(int T, int nb);
+int dft_max_bins();
+// acc (re, im)[nb][N] += sum_{t<T} V[t][N] exp(-2 pi i bins[k] (n0 + t) / nf); W is
+// scratch for T * nb twiddles.
+cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const int* bins, int nb,
+                       float2* W, float* re, float* im, cudaStream_t s);
+// pw += re^2 + im^2, then re = im = 0 (n elements).
+cudaError_t launch_power(long long n, float* re, float* im, float* pw, cudaStream_t s);
+// H[x] = 4 / (c^6 dt^4 nf) sum_k w[k] R[k][x] S[k][x].
+cudaError_t launch_assemble(long long N, int nb, const float* w, const float* R, const float* S,
+                            const float* vel, double dt, int nf, float* H, cudaStream_t s);
+
+}  // namespace mamute

@@ -13,6 +13,7 @@ enum StepMode {
   MODE_FWD_STORE = 2,
   MODE_ADJ = 3,
   MODE_ADJ_STORED = 4,
+  MODE_ADJ_TERM = 5,
 };
 
 struct StepArgs {

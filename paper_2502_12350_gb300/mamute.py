@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.mamute_gradient.argtypes = common + [P, P, ctypes.POINTER(D), P]
             lib.mamute_gradient_host.argtypes = common + [P, P, ctypes.POINTER(D), P]
             lib.mamute_adjoint.argtypes = common + [P, P, P]
+            lib.mamute_gn_diagonal.argtypes = common + [F, P]
             lib.mamute_revolve_plan.argtypes = [I, I, ctypes.POINTER(ctypes.c_longlong),
                                                 ctypes.POINTER(I), P]
             _lib = lib
@@ -198,6 +199,15 @@ class Context:
         self._check(self.lib.mamute_adjoint(self._h, ctypes.byref(grid), _ptr(vel), _ptr(rho),
                                             len(src), _ptr(src), _ptr(wav), _ptr(off), _ptr(rec),
                                             _ptr(d_res), ctypes.byref(o), _ptr(grad)))
+
+
+    def gn_diagonal(self, grid: Grid, vel, rho, src_xyz, wavelet, rec_offset, rec_xyz, hdiag,
+                    band_rel: float = 1e-4):
+        src, wav, off, rec = self._geom(src_xyz, wavelet, rec_offset, rec_xyz)
+        self._check(self.lib.mamute_gn_diagonal(self._h, ctypes.byref(grid), _ptr(vel), _ptr(rho),
+                                                len(src), _ptr(src), _ptr(wav), _ptr(off),
+                                                _ptr(rec), ctypes.c_float(band_rel),
+                                                _ptr(hdiag)))
 
 
 def make_grid(nx, ny, nz, border, h, dt, nt, origin=(0.0, 0.0, 0.0), cerjan=0.015) -> Grid:

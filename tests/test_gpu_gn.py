@@ -1,0 +1,61 @@
+"""GN-diagonal labels on the GPU against the oracle's separable form (same
+band limit); the oracle's separable form is pinned to its brute-force
+definition in test_oracle_gn.py."""
+import numpy as np
+import pytest
+
+from oracle import gn
+from paper_2502_12350_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_12350_gb300 import build, mamute
+    build.build()
+    c = mamute.Context(0)
+    yield c
+    c.close()
+
+
+def _common_receivers(density, seed, nt=120):
+    w = synth.small_case(seed=seed, nx=14, ny=12, nz=10, border=6, nt=nt, density=density,
+                         n_src=3, n_rec=5, fpeak=35.0)
+    one = w.rec_xyz[:5]
+    w.rec_xyz = np.concatenate([one] * w.n_src)
+    w.rec_offset = np.arange(w.n_src + 1, dtype=np.int32) * 5
+    return w
+
+
+@pytest.mark.parametrize("density", [False, True])
+def test_gn_diagonal_matches_oracle(ctx, oracle, density):
+    from paper_2502_12350_gb300 import mamute
+    w = _common_receivers(density, 61 + int(density))
+    og = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
+    ref = gn.separable(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho,
+                       band_rel=1e-4)
+    dev = torch.device("cuda:0")
+    vel = torch.from_numpy(w.vel).to(dev)
+    rho = None if w.rho is None else torch.from_numpy(w.rho).to(dev)
+    H = torch.full_like(vel, float("nan"))
+    ctx.gn_diagonal(mamute.grid_of(w), vel, rho, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                    H, band_rel=1e-4)
+    got = H.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all() and got.min() > 0
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
+
+
+def test_gn_rejects_differing_receivers(ctx):
+    from paper_2502_12350_gb300 import mamute
+    w = synth.small_case(seed=63, nx=14, ny=12, nz=10, border=6, nt=40, n_src=2, n_rec=4)
+    dev = torch.device("cuda:0")
+    vel = torch.from_numpy(w.vel).to(dev)
+    H = torch.empty_like(vel)
+    with pytest.raises(mamute.MamuteError) as e:
+        ctx.gn_diagonal(mamute.grid_of(w), vel, None, w.src_xyz, w.wavelet, w.rec_offset,
+                        w.rec_xyz, H)
+    assert e.value.code == mamute.EINVAL
