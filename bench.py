@@ -95,8 +95,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(nt=None):
+def workload(nt=None, kind="model"):
     from paper_2502_12350_gb300 import synth
+    if kind == "model_small":
+        return synth.forward_small() if nt is None else synth.forward_small(nt=nt)
     return synth.forward_density() if nt is None else synth.forward_density(nt=nt)
 
 
@@ -224,8 +226,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--nt", type=int, default=None, help="time steps (default: the workload's 4000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="model", choices=["model", "gradient_single",
-                                                            "gradient_batched"],
+    ap.add_argument("--workload", default="model", choices=["model", "model_small",
+                                                            "gradient_single", "gradient_batched"],
                     help="model: the headline modelling benchmark; gradient_*: FWI gradient "
                          "shots/s on the 256^3 single-shot or the 64-shot aperture workload")
     ap.add_argument("--snapshots", type=int, default=0,
@@ -233,7 +235,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload != "model":
+    if args.workload.startswith("gradient"):
         return run_gradient_bench(args)
 
     import torch
@@ -253,7 +255,7 @@ def main():
     if world > 1:
         dist.barrier()
 
-    w = workload(args.nt)
+    w = workload(args.nt, args.workload)
     nt = w.nt
     g = mamute.grid_of(w)
     stream = torch.cuda.current_stream(dev)
@@ -266,7 +268,7 @@ def main():
                                            ctypes.POINTER(ctypes.c_longlong)]
     lib.mamute_ctx_set_timing(ctx._h, 1)
     vel = torch.from_numpy(w.vel).to(dev)
-    rho = torch.from_numpy(w.rho).to(dev)
+    rho = None if w.rho is None else torch.from_numpy(w.rho).to(dev)
     n_rec = int(w.rec_offset[-1])
     seis = torch.empty((n_rec, nt), device=dev)
 
@@ -305,13 +307,13 @@ def main():
 
     # End to end through the host-buffer entry point (pinned host memory).
     vel_h = torch.from_numpy(w.vel).pin_memory()
-    rho_h = torch.from_numpy(w.rho).pin_memory()
+    rho_h = None if w.rho is None else torch.from_numpy(w.rho).pin_memory()
     seis_h = torch.empty((n_rec, nt), pin_memory=True)
     e2e_steps = max(1, min(args.steps, 3))
 
     def host_step():
-        ctx.model_host(g, vel_h.numpy(), rho_h.numpy(), w.src_xyz, w.wavelet, w.rec_offset,
-                       w.rec_xyz, seis_h.numpy())
+        ctx.model_host(g, vel_h.numpy(), None if rho_h is None else rho_h.numpy(), w.src_xyz,
+                       w.wavelet, w.rec_offset, w.rec_xyz, seis_h.numpy())
 
     host_step()
     torch.cuda.synchronize()
@@ -324,7 +326,8 @@ def main():
 
     peak, peak_kind = _peaks()
     kernel_ms = statistics.median(loop_ms) / max(step_launches, 1)
-    achieved = BYTES_PER_PT * w.n_padded / (kernel_ms / 1e3) / 1e9
+    bpp = BYTES_PER_PT if w.rho is not None else 16
+    achieved = bpp * w.n_padded / (kernel_ms / 1e3) / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if os.path.exists(prof):
@@ -339,18 +342,20 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"forward_512x512x256_density_{nt}steps",
+        "config": {"workload": w.name + f"_{nt}steps",
                    "padded": list(w.padded)[::-1], "nt": nt, "shots": 1, "receivers": n_rec,
-                   "l2": "every array (425 MB) is larger than L2",
+                   "l2": ("every array (%d MB) is larger than L2" % (w.n_padded * 4 // 2**20)
+                          if w.n_padded * 4 > 129 * 2**20 else
+                          "arrays fit in L2: the HBM roofline is reported but not binding"),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": e2e, "unit": UNIT,
-                "h2d_bytes_per_step": int(vel_h.numel() * 4 + rho_h.numel() * 4),
+                "h2d_bytes_per_step": int(vel_h.numel() * 4 + (0 if rho_h is None else rho_h.numel() * 4)),
                 "d2h_bytes_per_step": int(seis_h.numel() * 4)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "step_kernel<density,forward>",
-                     "bytes_per_point": BYTES_PER_PT, "kernel_ms": kernel_ms},
+                     "kernel": "step_kernel<forward>",
+                     "bytes_per_point": bpp, "kernel_ms": kernel_ms},
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:

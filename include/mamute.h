@@ -89,6 +89,11 @@ typedef struct {
  *   phess           device [nz][ny][nx] or NULL: receives the pseudo-Hessian
  *                   sum_s sum_n (g (lap - m2) u_s^n)^2 of the forward pass
  *                   (overwritten).
+ *   tiles           work decomposition of the time-step kernels: {forward tile
+ *                   width, height, z blocks, adjoint tile width, height, z
+ *                   blocks}; 0 entries are chosen by the library's cost model
+ *                   (an autotuner may pass measured choices; the result does
+ *                   not depend on them).  An unsupported shape is EINVAL.
  * A NULL options pointer means all defaults. */
 typedef struct {
   float check_mem;
@@ -96,6 +101,7 @@ typedef struct {
   int zero_top_planes;
   const int* aperture;
   float* phess;
+  int tiles[6];
 } mamute_opts;
 
 /* Creates a context on `device` issuing work on `cuda_stream` (a cudaStream_t;

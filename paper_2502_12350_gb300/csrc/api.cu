@@ -87,6 +87,9 @@ struct mamute_ctx {
   double loop_ms = 0.0;
   long long step_launches = 0, launches = 0;
   int max_planes = 1;  // planes per work item of the current call
+  // captured time loop of the last mamute_model call and its signature
+  cudaGraphExec_t graph = nullptr;
+  std::vector<unsigned long long> graph_key;
 };
 
 namespace {
@@ -178,8 +181,8 @@ int max_piece(const std::vector<int>& b) {
   return m;
 }
 
-// Receiver tables for one tiling.
-void build_receivers(Plan& P, int TX, const std::vector<std::vector<int>>& recnode,
+// Receiver tables for one tiling (items ordered z block, row, column).
+void build_receivers(Plan& P, int TX, int zsplit, const std::vector<std::vector<int>>& recnode,
                      const std::vector<int>& item_base, const std::vector<Tiling>& tilings,
                      std::vector<WorkItem>& items, std::vector<int>& rec_ptr,
                      std::vector<RecEntry>& rec, std::vector<long long>& cells,
@@ -196,8 +199,11 @@ void build_receivers(Plan& P, int TX, const std::vector<std::vector<int>>& recno
     const Tiling& T = tilings[s];
     const int ti = (int)(std::upper_bound(T.xs.begin(), T.xs.end(), lx) - T.xs.begin()) - 1;
     const int tj = (int)(std::upper_bound(T.ys.begin(), T.ys.end(), ly) - T.ys.begin()) - 1;
-    const int ncols = (int)T.xs.size() - 1;
-    const int item = item_base[s] + tj * ncols + ti;
+    const int ncols = (int)T.xs.size() - 1, nrows = (int)T.ys.size() - 1;
+    const int Nz = P.vols[s].Nz;
+    const int zlen = (Nz + zsplit - 1) / zsplit;
+    const int zb = std::min(lz / zlen, zsplit - 1);
+    const int item = item_base[s] + (zb * nrows + tj) * ncols + ti;
     t.push_back(Tmp{item, lz, (lx - T.xs[ti]) + TX * (ly - T.ys[tj]), r});
   }
   std::sort(t.begin(), t.end(), [](const Tmp& a, const Tmp& b) {
@@ -247,63 +253,70 @@ void build_receivers(Plan& P, int TX, const std::vector<std::vector<int>>& recno
   }
 }
 
-// Chooses, among the compiled tile shapes, the shape and the row split that
-// minimise the work of the busiest SM (ceil(tiles / SMs) x largest tile),
-// so that no long full-depth column is left for a second, nearly empty wave.
-// MAMUTE_TX / MAMUTE_TY force a shape.
+// Chooses, among the compiled tile shapes, the shape, a row refinement and a
+// split of the planes into z blocks that minimise the work of the busiest
+// SM: ceil(items / SMs) items of (box-bound points x planes), divided by a
+// factor for the resident warps (per-SM bandwidth falls off below about
+// 16 warps).  Items beyond the resident slots run in later waves, which the
+// same count captures.  MAMUTE_TX / MAMUTE_TY force a shape.
 struct TileChoice {
-  int tx = 64, ty = 16;
+  int tx = 64, ty = 16, zsplit = 1;
   std::vector<Tiling> tilings;
 };
 
 TileChoice choose_tiles(const std::vector<VolDesc>& vols, bool dens, int mode, int n_sm,
-                        int force_tx, int force_ty) {
+                        int force_tx, int force_ty, int force_z) {
   static const int shapes[][2] = {{64, 16}, {72, 16}, {48, 16}, {96, 8}, {64, 8},
                                   {128, 8}, {32, 16}, {32, 8}};
+  static const int zsplits[] = {1, 2, 3, 4, 6, 8};
   TileChoice best;
   double best_cost = -1.0;
+  const int Nz = vols.empty() ? 1 : vols[0].Nz;
   for (const auto& sh : shapes) {
     const int TX = sh[0], TY = sh[1];
     if (force_tx > 0 && (TX != force_tx || TY != force_ty)) continue;
     if (!tile_supported(TX, TY)) continue;
-    const int per_sm = step_blocks_per_sm(TX, TY, dens, mode, vols.empty() ? 1 : vols[0].Nz);
+    const int per_sm = step_blocks_per_sm(TX, TY, dens, mode, Nz);
     if (per_sm < 1) continue;
-    // Row refinement factor r: rows = r * ceil(Ny / TY) (r = 1 keeps the
-    // largest tiles); widths always use the fewest columns.
-    for (int r = 1; r <= 3; ++r) {
+    const int warps_cta = (TX / 4) * TY / 32;
+    for (int r = 1; r <= 2; ++r) {
       std::vector<Tiling> tl;
-      long long tiles = 0, maxarea = 0, total = 0;
+      long long tiles = 0;
+      double maxpts = 0.0;
+      bool ok = true;
       for (const VolDesc& V : vols) {
         Tiling T;
         const int ncols = (V.Nx + TX - 1) / TX;
         const int nrows = std::min(V.Ny, r * ((V.Ny + TY - 1) / TY));
         T.xs = split(V.Nx, ncols, 4);
         T.ys = split(V.Ny, nrows, 1);
-        if (max_piece(T.xs) > TX || max_piece(T.ys) > TY) {
-          T.xs.clear();
-        }
-        if (T.xs.empty()) { tiles = -1; break; }
+        if (max_piece(T.xs) > TX || max_piece(T.ys) > TY) { ok = false; break; }
+        // rows refined only while tiles stay at least half full
+        if (r > 1 && 2 * (V.Ny / nrows) < TY) { ok = false; break; }
         tiles += (long long)(T.xs.size() - 1) * (T.ys.size() - 1);
-        maxarea = std::max<long long>(maxarea, (long long)max_piece(T.xs) * max_piece(T.ys));
-        total += (long long)V.Nx * V.Ny;
+        // a CTA computes its whole box even when the tile is smaller
+        maxpts = std::max(maxpts, std::max((double)max_piece(T.xs) * max_piece(T.ys),
+                                           0.6 * TX * TY));
         tl.push_back(std::move(T));
       }
-      if (tiles <= 0) continue;
-      const long long waves_sm = (tiles + n_sm - 1) / n_sm;  // CTAs on the busiest SM
-      // Resident compute warps on a busy SM: per-SM bandwidth falls off below
-      // about 16 warps (too few loads in flight).
-      const double warps = (double)std::min<long long>(per_sm, waves_sm) * ((TX / 4) * TY / 32);
-      const double occ = std::min(1.0, warps / 16.0);
-      // Boxes always load (TX + 8) x (TY + 8) halo planes and TX x TY centre
-      // tiles; the excess over the useful w x h is served from L2.
-      const double box = (double)(TX + 8) * (TY + 8) + 2.0 * TX * TY;
-      const double over = box / (3.0 * (double)maxarea) - 1.0;
-      const double cost = (double)waves_sm * (double)maxarea * (1.0 + 0.1 * std::max(0.0, over)) / occ;
-      if (best_cost < 0 || cost < best_cost - 1e-9) {
-        best_cost = cost;
-        best.tx = TX;
-        best.ty = TY;
-        best.tilings = tl;
+      if (!ok || tiles <= 0) continue;
+      for (int zs : zsplits) {
+        if (force_z > 0 && zs != force_z) continue;
+        if (force_z <= 0 && zs > 1 && Nz / zs < 32) break;
+        const long long items = tiles * zs;
+        const long long per = (items + n_sm - 1) / n_sm;  // items on the busiest SM
+        const double warps = (double)std::min<long long>(per_sm, per) * warps_cta;
+        const double occ = std::min(1.0, warps / 16.0);
+        // z-block priming reads 8 extra halo planes of one of ~4 arrays
+        const double planes = (double)((Nz + zs - 1) / zs) + (zs > 1 ? 2.0 : 0.0);
+        const double cost = (double)per * maxpts * planes / occ;
+        if (best_cost < 0 || cost < best_cost * (1.0 - 1e-3)) {
+          best_cost = cost;
+          best.tx = TX;
+          best.ty = TY;
+          best.zsplit = zs;
+          best.tilings = tl;
+        }
       }
     }
   }
@@ -311,7 +324,8 @@ TileChoice choose_tiles(const std::vector<VolDesc>& vols, bool dens, int mode, i
 }
 
 int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, const float* src_xyz,
-               const int* rec_offset, const float* rec_xyz, const int* aperture, Plan& P) {
+               const int* rec_offset, const float* rec_xyz, const int* aperture, Plan& P,
+               const int* tiles = nullptr) {
   if (!g) return fail(ctx, MAMUTE_EINVAL, "grid is NULL");
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->border < 0 || g->nt < 1)
     return fail(ctx, MAMUTE_EINVAL, "bad grid dimensions");
@@ -387,10 +401,11 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (n_sm < 1) n_sm = 1;
   const int fmode = dens ? MODE_FWD : MODE_FWD;
-  TileChoice fc = choose_tiles(P.vols, dens, fmode, n_sm, env_int("MAMUTE_TX", 0),
-                               env_int("MAMUTE_TY", 0));
-  TileChoice ac = choose_tiles(P.vols, dens, MODE_ADJ, n_sm, env_int("MAMUTE_ADJ_TX", 0),
-                               env_int("MAMUTE_ADJ_TY", 0));
+  auto pick = [&](int i, const char* env) { return (tiles && tiles[i] > 0) ? tiles[i] : env_int(env, 0); };
+  TileChoice fc = choose_tiles(P.vols, dens, fmode, n_sm, pick(0, "MAMUTE_TX"), pick(1, "MAMUTE_TY"),
+                               pick(2, "MAMUTE_ZSPLIT"));
+  TileChoice ac = choose_tiles(P.vols, dens, MODE_ADJ, n_sm, pick(3, "MAMUTE_ADJ_TX"),
+                               pick(4, "MAMUTE_ADJ_TY"), pick(5, "MAMUTE_ADJ_ZSPLIT"));
   if (fc.tilings.empty() || ac.tilings.empty())
     return fail(ctx, MAMUTE_EINVAL, "unsupported tile shape");
   P.tx = fc.tx; P.ty = fc.ty; P.atx = ac.tx; P.aty = ac.ty;
@@ -401,22 +416,24 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
       const VolDesc& V = P.vols[s];
       const Tiling& T = C.tilings[s];
       base.push_back((int)items.size());
-      for (size_t tj = 0; tj + 1 < T.ys.size(); ++tj)
-        for (size_t ti = 0; ti + 1 < T.xs.size(); ++ti)
-          items.push_back(WorkItem{s, T.xs[ti], T.ys[tj], 0, V.Nz, T.xs[ti + 1] - T.xs[ti],
-                                   T.ys[tj + 1] - T.ys[tj], -1});
+      const int zlen = (V.Nz + C.zsplit - 1) / C.zsplit;
+      for (int zb = 0; zb < C.zsplit; ++zb)
+        for (size_t tj = 0; tj + 1 < T.ys.size(); ++tj)
+          for (size_t ti = 0; ti + 1 < T.xs.size(); ++ti)
+            items.push_back(WorkItem{s, T.xs[ti], T.ys[tj], zb * zlen, std::min(V.Nz, (zb + 1) * zlen),
+                                     T.xs[ti + 1] - T.xs[ti], T.ys[tj + 1] - T.ys[tj], -1});
     }
   };
   std::vector<int> base;
   make_items(fc, P.items, base);
-  build_receivers(P, P.tx, recnode, base, fc.tilings, P.items, P.rec_ptr, P.rec, P.rec_cell,
-                  P.rec_g, P.colmap, n_rec, rcell, rshot);
+  build_receivers(P, P.tx, fc.zsplit, recnode, base, fc.tilings, P.items, P.rec_ptr, P.rec,
+                  P.rec_cell, P.rec_g, P.colmap, n_rec, rcell, rshot);
   make_items(ac, P.aitems, base);
-  build_receivers(P, P.atx, recnode, base, ac.tilings, P.aitems, P.arec_ptr, P.arec,
+  build_receivers(P, P.atx, ac.zsplit, recnode, base, ac.tilings, P.aitems, P.arec_ptr, P.arec,
                   P.arec_cell, P.arec_g, P.acolmap, n_rec, rcell, rshot);
   if (env_int("MAMUTE_VERBOSE", 0))
-    fprintf(stderr, "mamute plan: %d shots, forward tile %dx%d (%zu CTAs), adjoint tile %dx%d (%zu CTAs)\n",
-            n_src, P.tx, P.ty, P.items.size(), P.atx, P.aty, P.aitems.size());
+    fprintf(stderr, "mamute plan: %d shots, forward tile %dx%d/%dz (%zu CTAs), adjoint tile %dx%d/%dz (%zu CTAs)\n",
+            n_src, P.tx, P.ty, fc.zsplit, P.items.size(), P.atx, P.aty, ac.zsplit, P.aitems.size());
   return MAMUTE_OK;
 }
 
@@ -613,7 +630,7 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   TRY(check_common(ctx, g, vel, wavelet));
   Plan P;
   TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz,
-                 opts ? opts->aperture : nullptr, P));
+                 opts ? opts->aperture : nullptr, P, opts ? opts->tiles : nullptr));
   ctx->max_planes = P.Nz;
   if (P.ncol > 0 && !seis) return fail(ctx, MAMUTE_EINVAL, "seis is NULL");
   TRY(check_cfl(ctx, P, vel));
@@ -625,9 +642,71 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   if (ph) CK(cudaMemsetAsync(ctx->acc.p, 0, pool, ctx->stream));
   CK(ensure(ctx->dint, (size_t)P.nt * std::max(P.ncol, 1) * 4));
   const int mode = ph ? MODE_FWD_PH : MODE_FWD;
-  for (int n = 0; n < P.nt; ++n) {
-    StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
-    CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+  // The time loop is captured into a CUDA graph and replayed while the plan,
+  // the buffers and the wavelet stay the same (MAMUTE_GRAPHS=0 disables).
+  std::vector<unsigned long long> key;
+  const bool use_graph = env_int("MAMUTE_GRAPHS", 1) != 0 && P.nt >= 8;
+  if (use_graph) {
+    auto push = [&](const void* p) { key.push_back((unsigned long long)(uintptr_t)p); };
+    key.push_back((unsigned long long)P.nt);
+    key.push_back((unsigned long long)P.items.size());
+    key.push_back(((unsigned long long)P.tx << 32) | (unsigned)P.ty);
+    key.push_back((unsigned long long)mode * 2 + P.dens);
+    key.push_back((unsigned long long)P.ncol);
+    key.push_back((unsigned long long)ctx->max_planes);
+    for (const DevBuf* b : {&ctx->items, &ctx->vols, &ctx->maps, &ctx->cmaps, &ctx->gx, &ctx->gy,
+                            &ctx->gz, &ctx->recptr, &ctx->rec, &ctx->acc, &ctx->dint,
+                            &ctx->pool[0], &ctx->pool[1]})
+      push(b->p);
+    for (int n = 0; n < P.nt; ++n) {
+      unsigned int u;
+      std::memcpy(&u, &wavelet[n], 4);
+      key.push_back(u);
+    }
+  }
+  auto launch_all = [&]() -> int {
+    for (int n = 0; n < P.nt; ++n) {
+      StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
+      CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+    }
+    return MAMUTE_OK;
+  };
+  if (!use_graph) {
+    TRY(launch_all());
+  } else {
+    if (!ctx->graph || ctx->graph_key != key) {
+      if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+      }
+      const bool timing = ctx->timing;
+      const long long sl0 = ctx->step_launches, l0 = ctx->launches;
+      ctx->timing = false;  // no event records inside the capture
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = launch_all();
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+      ctx->timing = timing;
+      ctx->step_launches = sl0;
+      ctx->launches = l0;
+      if (rc != MAMUTE_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+      }
+      CK(e);
+      e = cudaGraphInstantiate(&ctx->graph, gr, 0);
+      cudaGraphDestroy(gr);
+      CK(e);
+      ctx->graph_key = key;
+    }
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+    if (ctx->timing) {
+      CK(cudaEventRecord(ctx->ev1, ctx->stream));
+      ctx->ev0_set = true;
+    }
+    ctx->step_launches = P.nt;
+    ctx->launches += P.nt;
   }
   CK(aux_count(ctx, launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol, seis,
                      ctx->stream)));
@@ -648,7 +727,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   if (!grad) return fail(ctx, MAMUTE_EINVAL, "grad is NULL");
   Plan P;
   TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz,
-                 opts ? opts->aperture : nullptr, P));
+                 opts ? opts->aperture : nullptr, P, opts ? opts->tiles : nullptr));
   ctx->max_planes = P.Nz;
   if (P.ncol > 0 && !d_in) return fail(ctx, MAMUTE_EINVAL, "data is NULL");
   TRY(check_cfl(ctx, P, vel));
@@ -1049,6 +1128,7 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
   if (ctx->maxbits) cudaFree(ctx->maxbits);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   delete ctx;
 }
 

@@ -1,0 +1,90 @@
+"""Learned vs plain preconditioned FWI on the 160x160x80 workload.
+
+Trains the GN-diagonal network on seeded models of the layered family
+(same acquisition as the inversion: 12 shots, 64 receivers, 1500 steps),
+then inverts a held-out model twice from the same blurred start: with the
+pseudo-Hessian preconditioner and with the learned one (falling back to the
+pseudo-Hessian step when the learned step fails Armijo).  Writes a JSON
+report with misfit against wall time for both runs.
+
+    python -m paper_2502_12350_gb300.experiment --out report.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--train-models", type=int, default=48)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--nt", type=int, default=1500)
+    ap.add_argument("--nx", type=int, default=160)
+    ap.add_argument("--ny", type=int, default=160)
+    ap.add_argument("--nz", type=int, default=80)
+    ap.add_argument("--test-model", type=int, default=5400)
+    args = ap.parse_args(argv)
+
+    from . import build, cnn, fwi, learned, mamute, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = mamute.Context(0)
+    report = {"config": vars(args)}
+
+    def wl(mid):
+        return synth.fwi_small(model_id=mid, nt=args.nt, nx=args.nx, ny=args.ny, nz=args.nz)
+
+    net = cnn.Net(ctx, seed=1)
+    t0 = time.perf_counter()
+    train_ids = list(range(5000, 5000 + args.train_models))
+    test_ids = list(range(5380, 5384))
+    data = learned.dataset(ctx, net, wl, train_ids, seed=1)
+    held = learned.dataset(ctx, net, wl, test_ids, seed=2)
+    torch.cuda.synchronize()
+    report["label_seconds"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = learned.train(net, data, args.epochs, lr=2e-3, log=print)
+    torch.cuda.synchronize()
+    report["train_seconds"] = time.perf_counter() - t0
+    report["train_loss"] = hist
+    errs = learned.log_errors(net, held)
+    report["heldout_log_rms"] = {"network": [e[0] for e in errs],
+                                 "pseudo_hessian_rescaled": [e[1] for e in errs]}
+    print("held-out RMS log error (network, rescaled P):", errs)
+
+    w = wl(args.test_model)
+    g = mamute.grid_of(w)
+    vt = torch.from_numpy(w.vel).to(dev)
+    dobs = torch.empty((int(w.rec_offset[-1]), w.nt), device=dev)
+    ctx.model(g, vt, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs)
+    vmin, vmax = float(w.vel.min()) * 0.9, float(w.vel.max()) * 1.1
+    runs = {}
+    for kind in ("pseudo", "learned"):
+        prob = fwi.Problem(ctx, w, dobs, vmin, vmax)
+        res = fwi.run(prob, w.vel_init.astype(np.float64), args.iters, precond=kind, net=net)
+        err = float(np.sqrt(np.mean((res.vel - w.vel) ** 2)))
+        runs[kind] = {"history": [(t, J, k) for t, J, k in res.history],
+                      "model_rms_error": err, "gradients": res.n_gradients,
+                      "forward_models": res.n_forward}
+        print(kind, "final misfit", res.history[-1][1], "model error", err,
+              "time", res.history[-1][0])
+    # wall time for each run to reach the plain run's final misfit
+    target = runs["pseudo"]["history"][-1][1]
+    for kind in runs:
+        t_hit = next((t for t, J, _ in runs[kind]["history"] if J <= target), None)
+        runs[kind]["seconds_to_plain_final_misfit"] = t_hit
+    report["fwi"] = runs
+    with open(args.out, "w") as f:
+        json.dump(report, f, indent=1)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

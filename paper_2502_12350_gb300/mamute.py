@@ -39,7 +39,7 @@ class Grid(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("check_mem", ctypes.c_float), ("n_snapshots", ctypes.c_int),
                 ("zero_top_planes", ctypes.c_int), ("aperture", ctypes.c_void_p),
-                ("phess", ctypes.c_void_p)]
+                ("phess", ctypes.c_void_p), ("tiles", ctypes.c_int * 6)]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -149,11 +149,13 @@ class Context:
         return src, wav, off, rec
 
     @staticmethod
-    def _opts(check_mem=0.8, n_snapshots=0, zero_top_planes=0, aperture=None, phess=None):
+    def _opts(check_mem=0.8, n_snapshots=0, zero_top_planes=0, aperture=None, phess=None,
+              tiles=None):
         ap = None if aperture is None else np.ascontiguousarray(aperture, np.int32)
         o = Opts(check_mem, n_snapshots, zero_top_planes,
                  None if ap is None else ap.ctypes.data, None if phess is None else phess.data_ptr()
-                 if not isinstance(phess, np.ndarray) else phess.ctypes.data)
+                 if not isinstance(phess, np.ndarray) else phess.ctypes.data,
+                 (ctypes.c_int * 6)(*(list(tiles) if tiles is not None else [0] * 6)))
         return o, ap
 
     def model(self, grid: Grid, vel, rho, src_xyz, wavelet, rec_offset, rec_xyz, seis, **opts):

@@ -64,10 +64,10 @@ def test_conv_forward_and_input_gradient(net_mod, shape):
     mask = _rand_act(rng, D, H, W, 16)
     g16 = torch.zeros((D, H, W, 16), dtype=torch.int16, device=dev)
     g32 = torch.zeros((D, H, W, 16), device=dev)
-    net._check(lib.mamute_conv3d(ctx._h, D, H, W, cnn._p(torch.from_numpy(_bf16_bits(gy)).to(dev)),
-                                 cnn._p(net.wb[0]), None, 0,
-                                 cnn._p(torch.from_numpy(_bf16_bits(mask)).to(dev)), cnn._p(g32),
-                                 cnn._p(g16)))
+    gyt = torch.from_numpy(_bf16_bits(gy)).to(dev)  # held: the call gets raw pointers
+    mt = torch.from_numpy(_bf16_bits(mask)).to(dev)
+    net._check(lib.mamute_conv3d(ctx._h, D, H, W, cnn._p(gyt), cnn._p(net.wb[0]), None, 0,
+                                 cnn._p(mt), cnn._p(g32), cnn._p(g16)))
     refg = conv.backward_input(np.moveaxis(gy, -1, 0), wo) * (np.moveaxis(mask, -1, 0) > 0)
     gotg = np.moveaxis(g32.cpu().numpy(), -1, 0)
     assert np.abs(gotg - refg).max() <= 1e-5 * np.abs(refg).max()
@@ -85,10 +85,10 @@ def test_weight_gradient(net_mod, shape):
     net = cnn.Net(ctx)
     gw = torch.zeros((27, 16, 16), device=dev)
     gb = torch.zeros(16, device=dev)
-    net._check(net.lib.mamute_conv3d_wgrad(ctx._h, D, H, W,
-                                           cnn._p(torch.from_numpy(_bf16_bits(x)).to(dev)),
-                                           cnn._p(torch.from_numpy(_bf16_bits(gy)).to(dev)),
-                                           cnn._p(gw), cnn._p(gb)))
+    xt = torch.from_numpy(_bf16_bits(x)).to(dev)  # held: the call gets raw pointers
+    gyt = torch.from_numpy(_bf16_bits(gy)).to(dev)
+    net._check(net.lib.mamute_conv3d_wgrad(ctx._h, D, H, W, cnn._p(xt), cnn._p(gyt), cnn._p(gw),
+                                           cnn._p(gb)))
     rw, rb = conv.backward_weight(np.moveaxis(x, -1, 0), np.moveaxis(gy, -1, 0))
     got = cnn.to_oracle_layout(gw.cpu().numpy())
     assert np.abs(got - rw).max() <= 1e-5 * np.abs(rw).max()

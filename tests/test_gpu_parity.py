@@ -104,6 +104,22 @@ def test_tiles_bitwise_identical(ctx, monkeypatch, tile):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("zsplit", [2, 3, 6])
+def test_z_blocks_bitwise_identical(ctx, monkeypatch, zsplit):
+    """Splitting the planes into z blocks (each primed from its neighbours'
+    planes) changes nothing; the gradient too (adjoint z blocks)."""
+    w = synth.small_case(seed=13, nx=30, ny=26, nz=28, border=6, nt=35, n_src=2, n_rec=8)
+    ref = gpu_model(ctx, w)
+    dobs = np.zeros_like(ref)
+    Jr, gr = gpu_gradient(ctx, w, dobs, n_snapshots=3)
+    monkeypatch.setenv("MAMUTE_ZSPLIT", str(zsplit))
+    monkeypatch.setenv("MAMUTE_ADJ_ZSPLIT", str(zsplit))
+    np.testing.assert_array_equal(gpu_model(ctx, w), ref)
+    J, g = gpu_gradient(ctx, w, dobs, n_snapshots=3)
+    assert J == Jr
+    np.testing.assert_array_equal(g, gr)
+
+
 def test_host_entry_point_matches_device(ctx):
     from paper_2502_12350_gb300 import mamute
     w = synth.small_case(seed=5)
