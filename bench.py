@@ -32,6 +32,38 @@ UNIT = "Gpt/s"
 BYTES_PER_PT = 20  # read u^n, u^{n-1}, A, A m2; write u^{n+1}
 
 
+KERNEL_SOURCES = ["paper_2502_12350_gb300/csrc/stencil_impl.cuh",
+                  "paper_2502_12350_gb300/csrc/stencil_fwd.cu",
+                  "paper_2502_12350_gb300/csrc/common.cuh"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(w):
+    """DRAM bytes per launch of the forward step from the committed ncu
+    summary of this workload, or None if the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_forward_{w.name}.md")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        if fields.get("source_sha256") != kernel_source_hash():
+            return None
+        return int(fields["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -218,6 +250,89 @@ def run_gradient_bench(args):
     return 0
 
 
+def run_cnn_bench(args):
+    """Training step of the preconditioner network (4 convolutions forward,
+    3 input gradients, 4 weight gradients, loss, Adam) on the 160x160x80
+    volume; FLOPs count the channel-padded (16 x 16) products."""
+    import torch
+
+    from paper_2502_12350_gb300 import build, cnn, mamute
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = mamute.Context(0)
+    D, H, W = 80, 160, 160
+    net = cnn.Net(ctx, seed=0)
+    rng = np.random.default_rng(0)
+    x = np.zeros((D, H, W, 16), np.float32)
+    x[..., :2] = rng.standard_normal((D, H, W, 2))
+    bits = (x.view(np.uint32) >> 16).astype(np.uint16).view(np.int16)
+    xt = torch.from_numpy(bits).to(dev)
+    tt = torch.from_numpy(rng.standard_normal((D, H, W)).astype(np.float32)).to(dev)
+    for _ in range(args.warmup):
+        net.train_step(xt, tt)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        net.train_step(xt, tt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    flops = 11 * 2.0 * 27 * 16 * 16 * D * H * W  # 4 fwd + 3 dgrad + 4 wgrad convolutions
+    peak = 1913.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        pass
+    tf = flops / (ms / 1e3) / 1e12
+    line = {"metric": "network training step TFLOP/s", "value": tf, "unit": "TFLOP/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic", "config": {"workload": "cnn_4x3^3_16ch_80x160x160"},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tf / peak, "traffic": None, "peak_kind": "measured"}}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gn_bench(args):
+    """Exact Gauss-Newton-diagonal labels of the 160x160x80 learned-
+    preconditioner workload (12 shots, 64 receivers, 1500 steps)."""
+    import time as _t
+
+    import torch
+
+    from paper_2502_12350_gb300 import build, mamute, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = mamute.Context(0)
+    w = synth.fwi_small(model_id=5000) if args.nt is None else synth.fwi_small(model_id=5000, nt=args.nt)
+    g = mamute.grid_of(w)
+    v = torch.from_numpy(w.vel).to(dev)
+    hd = torch.empty_like(v)
+    for _ in range(args.warmup):
+        ctx.gn_diagonal(g, v, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, hd)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    for _ in range(args.steps):
+        ctx.gn_diagonal(g, v, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, hd)
+    torch.cuda.synchronize()
+    sec = (_t.perf_counter() - t0) / args.steps
+    props = w.n_src + int(w.rec_offset[1])
+    line = {"metric": "GN-diagonal labels/s", "value": 1.0 / sec, "unit": "models/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nt": w.nt, "propagations": props,
+                       "gpt_updates_per_s": props * w.n_padded * w.nt / sec / 1e9}}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,8 +341,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--nt", type=int, default=None, help="time steps (default: the workload's 4000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="model", choices=["model", "model_small",
-                                                            "gradient_single", "gradient_batched"],
+    ap.add_argument("--workload", default="model",
+                    choices=["model", "model_small", "gradient_single", "gradient_batched", "cnn",
+                             "gn_labels"],
                     help="model: the headline modelling benchmark; gradient_*: FWI gradient "
                          "shots/s on the 256^3 single-shot or the 64-shot aperture workload")
     ap.add_argument("--snapshots", type=int, default=0,
@@ -237,6 +353,10 @@ def main():
         return run_reference(args)
     if args.workload.startswith("gradient"):
         return run_gradient_bench(args)
+    if args.workload == "cnn":
+        return run_cnn_bench(args)
+    if args.workload == "gn_labels":
+        return run_gn_bench(args)
 
     import torch
     import torch.distributed as dist
@@ -328,14 +448,7 @@ def main():
     kernel_ms = statistics.median(loop_ms) / max(step_launches, 1)
     bpp = BYTES_PER_PT if w.rho is not None else 16
     achieved = bpp * w.n_padded / (kernel_ms / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                traffic = json.load(f).get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = kernel_traffic(w)
 
     clocks = clk.summary()
     line = {

@@ -90,6 +90,8 @@ struct mamute_ctx {
   // captured time loop of the last mamute_model call and its signature
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned long long> graph_key;
+  cudaStream_t capture = nullptr;  // private stream the time loop is captured on
+  std::vector<ShotMaps> hmaps;     // host copy of the uploaded shot maps
 };
 
 namespace {
@@ -268,7 +270,7 @@ TileChoice choose_tiles(const std::vector<VolDesc>& vols, bool dens, int mode, i
                         int force_tx, int force_ty, int force_z) {
   static const int shapes[][2] = {{64, 16}, {72, 16}, {48, 16}, {96, 8}, {64, 8},
                                   {128, 8}, {32, 16}, {32, 8}};
-  static const int zsplits[] = {1, 2, 3, 4, 6, 8};
+  static const int zsplits[] = {1, 2, 3, 4, 6, 8, 12, 16};
   TileChoice best;
   double best_cost = -1.0;
   const int Nz = vols.empty() ? 1 : vols[0].Nz;
@@ -302,7 +304,7 @@ TileChoice choose_tiles(const std::vector<VolDesc>& vols, bool dens, int mode, i
       if (!ok || tiles <= 0) continue;
       for (int zs : zsplits) {
         if (force_z > 0 && zs != force_z) continue;
-        if (force_z <= 0 && zs > 1 && Nz / zs < 32) break;
+        if (force_z <= 0 && zs > 1 && Nz / zs < 8) break;
         const long long items = tiles * zs;
         const long long per = (items + n_sm - 1) / n_sm;  // items on the busiest SM
         const double warps = (double)std::min<long long>(per_sm, per) * warps_cta;
@@ -371,7 +373,10 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
     V.border = P.b; V.nxi = a1 - a0; V.nyi = a3 - a2; V.nzi = P.nz;
     V.slab = round_up((long long)V.Nz * V.Ny * V.pitch, 64);
     V.off = off; off += V.slab;
-    V.toff = toff; toff += (long long)V.nxi * V.nyi * V.nzi;
+    // Term-store rows start on a 16-byte boundary of the local x axis (TMA).
+    V.txoff = P.b & ~3;
+    V.tpitch = (int)round_up(P.b - V.txoff + V.nxi, 4);
+    V.toff = toff; toff += (long long)V.tpitch * V.nyi * V.nzi;
     V.gx_off = (int)P.gx.size(); V.gy_off = (int)P.gy.size();
     std::vector<float> px = sponge(V.Nx, P.b, g->cerjan), py = sponge(V.Ny, P.b, g->cerjan);
     P.gx.insert(P.gx.end(), px.begin(), px.end());
@@ -540,6 +545,7 @@ int setup(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho, bool nee
     if (!ok) return fail(ctx, MAMUTE_ECUDA, "cuTensorMapEncodeTiled failed (shot %d)", (int)s);
   }
   CK(upload(ctx->maps, maps, ctx->stream));
+  ctx->hmaps = maps;
   std::vector<CoefMaps> cm(2);  // [0]: forward tile boxes, [1]: adjoint tile boxes
   for (int v = 0; v < 2; ++v) {
     const int bx = v ? P.atx : P.tx, by = v ? P.aty : P.ty;
@@ -679,13 +685,20 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
       }
+      // Captured on a private stream (the caller's may be the legacy default
+      // stream, which cannot be captured); the graph runs on the caller's.
+      if (!ctx->capture) CK(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+      CK(cudaStreamSynchronize(ctx->stream));
       const bool timing = ctx->timing;
       const long long sl0 = ctx->step_launches, l0 = ctx->launches;
+      cudaStream_t user = ctx->stream;
       ctx->timing = false;  // no event records inside the capture
+      ctx->stream = ctx->capture;
       cudaGraph_t gr = nullptr;
-      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      const int rc = launch_all();
-      cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+      cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+      const int rc = e == cudaSuccess ? launch_all() : MAMUTE_OK;
+      if (e == cudaSuccess) e = cudaStreamEndCapture(ctx->stream, &gr);
+      ctx->stream = user;
       ctx->timing = timing;
       ctx->step_launches = sl0;
       ctx->launches = l0;
@@ -750,6 +763,24 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   int slots = 0;
   if (all_mode) {
     CK(ensure(ctx->tstore, (size_t)P.nt * P.term_elems * 4));
+    bool pads = false;
+    for (const VolDesc& V : P.vols) pads = pads || V.txoff != V.border || V.tpitch != V.nxi;
+    if (pads) CK(cudaMemsetAsync(ctx->tstore.p, 0, (size_t)P.nt * P.term_elems * 4, ctx->stream));
+    for (size_t s = 0; s < P.vols.size(); ++s) {
+      const VolDesc& V = P.vols[s];
+      cuuint64_t dims[4] = {(cuuint64_t)V.tpitch, (cuuint64_t)V.nyi, (cuuint64_t)V.nzi,
+                            (cuuint64_t)P.nt};
+      cuuint64_t strides[3] = {(cuuint64_t)V.tpitch * 4, (cuuint64_t)V.tpitch * V.nyi * 4,
+                               (cuuint64_t)P.term_elems * 4};
+      cuuint32_t box[4] = {(cuuint32_t)P.atx, (cuuint32_t)P.aty, 1, 1};
+      cuuint32_t es[4] = {1, 1, 1, 1};
+      if (ctx->encode(&ctx->hmaps[s].m[12], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                      (float*)ctx->tstore.p + V.toff, dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE))
+        return fail(ctx, MAMUTE_ECUDA, "cuTensorMapEncodeTiled failed (term store)");
+    }
+    CK(upload(ctx->maps, ctx->hmaps, ctx->stream));
   } else if (nsnap > 0) {
     slots = std::min(nsnap, P.nt);
   } else {
@@ -816,7 +847,8 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     a.wn = 0.f;
     a.fout = (float*)ctx->psi[k & 1].p;
     a.acc = (float*)ctx->acc.p;
-    a.tstore = all_mode ? (float*)ctx->tstore.p + (size_t)i * P.term_elems : nullptr;
+    a.tstore = nullptr;
+    a.tstep = i;  // the all-states adjoint reads the term of step i through its map
     a.rec_ptr = (const int*)ctx->arecptr.p;
     a.rec = (const RecEntry*)ctx->arec.p;
     a.dout = nullptr;
@@ -915,6 +947,17 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz, nullptr, P));
   ctx->max_planes = P.Nz;
   TRY(check_cfl(ctx, P, vel));
+  // Compact interior term layout: slot k of the ring is [nz][ny][nx].
+  {
+    long long toff = 0;
+    for (VolDesc& V : P.vols) {
+      V.txoff = V.border;
+      V.tpitch = V.nxi;
+      V.toff = toff;
+      toff += (long long)V.nxi * V.nyi * V.nzi;
+    }
+    P.term_elems = toff;
+  }
   TRY(setup(ctx, P, vel, rho, true, false));
   // Retained bins of the N_f = 2 nt DFT: where the wavelet spectrum is at
   // least band_rel of its peak (all bins for band_rel <= 0).
@@ -1129,6 +1172,7 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
   delete ctx;
 }
 

@@ -32,7 +32,7 @@ struct VolDesc {
   float src_scale;       // dt^2 / (h^3 sqrt(rho(x_s)))
   int border;            // sponge cells on each face
   int nxi, nyi, nzi;     // interior (model) extent of the window
-  int pad0;
+  int txoff, tpitch;     // term store rows: local x in [txoff, txoff + tpitch)
   long long off;         // element offset of the shot's arrays in each pool
   long long slab;        // elements per wavefield array (Nz * Ny * pitch, rounded)
   long long toff;        // offset of the shot's interior in one step of the term store
@@ -63,8 +63,9 @@ struct RecEntry {
 //   [8] accumulator centre F (pseudo-Hessian)
 //   [9] u0 halo A  [10] u1 halo A    (forward field read by the imaging)
 //  [11] accumulator centre A (imaging)
+//  [12] term store (x, y, z, step) centre A, 4-D (all-states adjoint)
 struct ShotMaps {
-  CUtensorMap m[12];
+  CUtensorMap m[13];
 };
 
 // Global coefficient maps: [0] A centre, [1] M = A m2 centre.
@@ -126,6 +127,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, int
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
       "l"(m), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* m, int x, int y, int z,
+                                            int w, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(m), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
       : "memory");
 }
 

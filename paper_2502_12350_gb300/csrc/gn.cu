@@ -9,7 +9,7 @@ namespace mamute {
 
 namespace {
 
-constexpr int kPts = 128;   // points per CTA
+constexpr int kPts = 64;    // points per CTA
 constexpr int kChunk = 16;  // frequency bins per thread
 
 // Twiddles W[t][k] = exp(-2 pi i bins[k] (n0 + t) / nf) for one time block.
@@ -26,7 +26,7 @@ __global__ void twiddle_kernel(int T, int n0, int nf, const int* __restrict__ bi
 
 // acc[k][x] += sum_t V[t][x] W[t][k] for kPts points per CTA; thread
 // (p, c) owns point p and bins [c kChunk, (c+1) kChunk).
-__global__ void dft_kernel(const float* __restrict__ V, long long N, int T, int nb,
+__global__ void __launch_bounds__(512) dft_kernel(const float* __restrict__ V, long long N, int T, int nb,
                            const float2* __restrict__ W, float* __restrict__ re,
                            float* __restrict__ im) {
   extern __shared__ float sm[];
@@ -112,7 +112,7 @@ int blocks_for(long long n) {
 
 size_t dft_smem_bytes(int T, int nb) { return sizeof(float) * T * kPts + sizeof(float2) * T * nb; }
 
-int dft_max_bins() { return (1024 / kPts) * kChunk; }
+int dft_max_bins() { return (512 / kPts) * kChunk; }
 
 cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const int* bins, int nb,
                        float2* W, float* re, float* im, cudaStream_t s) {

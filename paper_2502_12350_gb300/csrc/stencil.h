@@ -30,6 +30,7 @@ struct StepArgs {
   float* fout;            // pool receiving the new level (buffer fcur ^ 1)
   float* acc;             // accumulator pool (pseudo-Hessian or imaging)
   float* tstore;          // imaging-term store for this step (all-states mode)
+  int tstep;              // step index of the term read by the all-states adjoint
   const int* rec_ptr;     // per-item per-plane receiver offsets
   const RecEntry* rec;    // receiver entries
   float* dout;            // forward: data row of this step (internal columns), may be null

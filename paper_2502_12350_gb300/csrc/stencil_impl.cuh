@@ -149,11 +149,12 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
   constexpr bool ADJ = (MODE == MODE_ADJ || MODE == MODE_ADJ_STORED || MODE == MODE_ADJ_TERM);
   constexpr bool RECOMP = (MODE == MODE_ADJ);
   constexpr bool ACC = (MODE == MODE_FWD_PH || MODE == MODE_ADJ || MODE == MODE_ADJ_STORED);
+  constexpr bool TERM = (MODE == MODE_ADJ_STORED);  // stored imaging term as a centre array
   using LY = Layout<TX, TY, ADJ, RECOMP>;
   constexpr int NCT = LY::NCT, HS = LY::HS, CS = LY::CS, NSU = LY::NSU, NSC = LY::NSC;
   constexpr int NHALO = LY::NHALO;
-  constexpr int NC = 2 + (DENS ? 1 : 0) + (ACC ? 1 : 0);  // centre arrays per stage
-  constexpr int CI_PREV = 0, CI_A = 1, CI_M = 2, CI_ACC = DENS ? 3 : 2;
+  constexpr int NC = 2 + (DENS ? 1 : 0) + (ACC ? 1 : 0) + (TERM ? 1 : 0);  // centre arrays
+  constexpr int CI_PREV = 0, CI_A = 1, CI_M = 2, CI_ACC = DENS ? 3 : 2, CI_T = CI_ACC + 1;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* ring = reinterpret_cast<float*>(smem_raw);           // NSU * NHALO * HS
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
   const CUtensorMap* mapP = &sm->m[fbase + 2 * (a.fcur ^ 1) + 1];
   const CUtensorMap* mapU = &sm->m[9 + a.ucur];  // forward field for imaging
   const CUtensorMap* mapAcc = &sm->m[ADJ ? 11 : 8];
+  const CUtensorMap* mapT = &sm->m[12];
   const CUtensorMap* mapA = &a.cmaps->m[0];
   const CUtensorMap* mapM = &a.cmaps->m[1];
 
@@ -216,6 +218,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
       if (DENS) tmap_acquire(mapM);
       if (RECOMP) tmap_acquire(mapU);
       if (ACC) tmap_acquire(mapAcc);
+      if (TERM) tmap_acquire(mapT);
       const int nu = npl + 2 * kHalo;
       const int cx = V.cx0 + x0, cy = V.cy0 + y0;
       for (int i = 0; i < nu; ++i) {
@@ -236,6 +239,9 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
           tma_load_3d(cd + CI_A * CS, mapA, cx, cy, q, &fullC[c]);
           if (DENS) tma_load_3d(cd + CI_M * CS, mapM, cx, cy, q, &fullC[c]);
           if (ACC) tma_load_3d(cd + CI_ACC * CS, mapAcc, x0, y0, q, &fullC[c]);
+          if (TERM)
+            tma_load_4d(cd + CI_T * CS, mapT, x0 - V.txoff, y0 - V.border, q - V.border, a.tstep,
+                        &fullC[c]);
         }
       }
     }
@@ -350,7 +356,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
         for (int e = 0; e < 4; ++e) {
           const int xi = gxl + e - b;
           if (xi >= 0 && xi < V.nxi)
-            a.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.nxi + xi] = out.v[e];
+            a.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.tpitch + (gxl + e - V.txoff)] =
+                out.v[e];
         }
       }
     }
@@ -364,14 +371,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
 #pragma unroll
         for (int e = 0; e < 4; ++e) t.v[e] = img_term(qu[4].v[e], Av.v[e], Mv.v[e], lu[e], DENS);
       } else if (MODE == MODE_ADJ_STORED) {
-        const int b = V.border, zi = z - b, yi = gyl - b;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int xi = gxl + e - b;
-          t.v[e] = 0.0f;
-          if (xi >= 0 && xi < V.nxi && yi >= 0 && yi < V.nyi && zi >= 0 && zi < V.nzi)
-            t.v[e] = a.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.nxi + xi];
-        }
+        t = ld4s(cs + CI_T * CS);
       } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e) t.v[e] = img_term(q[4].v[e], Av.v[e], Mv.v[e], lap[e], DENS);
@@ -383,7 +383,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
           for (int e = 0; e < 4; ++e) {
             const int xi = gxl + e - b;
             if (xi >= 0 && xi < V.nxi)
-              a.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.nxi + xi] = t.v[e];
+              a.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.tpitch + (gxl + e - V.txoff)] =
+                  t.v[e];
           }
         }
       } else {
@@ -436,7 +437,7 @@ static size_t smem_bytes_base() {
   constexpr bool RECOMP = (MODE == MODE_ADJ);
   constexpr bool ACC = (MODE == MODE_FWD_PH || MODE == MODE_ADJ || MODE == MODE_ADJ_STORED);
   using LY = Layout<TX, TY, ADJ, RECOMP>;
-  constexpr int NC = 2 + (DENS ? 1 : 0) + (ACC ? 1 : 0);
+  constexpr int NC = 2 + (DENS ? 1 : 0) + (ACC ? 1 : 0) + (MODE == MODE_ADJ_STORED ? 1 : 0);
   return sizeof(float) * (size_t)(LY::NSU * LY::NHALO * LY::HS + LY::NSC * NC * LY::CS + LY::CS) +
          sizeof(uint64_t) * (2 * LY::NSU + 2 * LY::NSC);
 }

@@ -61,7 +61,7 @@ class Problem:
         J = self.ctx.gradient(self.grid, vt, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
                               self.d_obs, g, phess=ph)
         self.n_grad += 1
-        return J, g.cpu().numpy().astype(np.float64), ph
+        return J, g.cpu().numpy().astype(np.float64).ravel(), ph
 
     def misfit(self, v: np.ndarray) -> float:
         vt = torch.from_numpy(v.astype(np.float32)).to(self.dev)
@@ -104,9 +104,9 @@ def two_loop(g, pairs, diag):
     return -r
 
 
-def _diag(h):
+def _diag(h, water=0.05):
     h = np.asarray(h, np.float64).ravel()
-    return 1.0 / (h + 1e-3 * h.max())
+    return 1.0 / (h + water * h.max())
 
 
 def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net=None,
@@ -131,11 +131,18 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
         out = net.forward(x16)
         return _diag(pmax * np.exp(out.cpu().numpy().astype(np.float64)))
 
-    def line_search(d, J, g, x, max_bt, alpha):
+    def line_search(d, J, g, x, max_bt, alpha, expand):
         for _ in range(max_bt + 1):
             xn = prob.project(x + alpha * d)
             Jn = prob.misfit(xn.reshape(shape))
             if Jn <= J + c1 * np.dot(g, xn - x):
+                # without curvature information, grow the step while it pays
+                for _ in range(4 if expand else 0):
+                    xe = prob.project(x + 2.0 * alpha * d)
+                    Je = prob.misfit(xe.reshape(shape))
+                    if Je >= Jn:
+                        break
+                    xn, Jn, alpha = xe, Je, 2.0 * alpha
                 return xn, Jn
             alpha *= 0.5
         return None, None
@@ -150,7 +157,7 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
                 d = two_loop(g, pairs, diag_for(kind, x, ph))
             alpha = first_step / max(np.abs(d).max(), 1e-30) if not pairs else 1.0
             nb = learned_backtracks if (kind == "learned") else max_backtracks
-            xn, Jn = line_search(d, J, g, x, nb, alpha)
+            xn, Jn = line_search(d, J, g, x, nb, alpha, expand=not pairs)
             if xn is not None:
                 accepted = (kind, xn, Jn)
                 break

@@ -59,3 +59,18 @@ def test_gn_rejects_differing_receivers(ctx):
         ctx.gn_diagonal(mamute.grid_of(w), vel, None, w.src_xyz, w.wavelet, w.rec_offset,
                         w.rec_xyz, H)
     assert e.value.code == mamute.EINVAL
+
+
+def test_gn_diagonal_full_band(ctx, oracle):
+    """All nt + 1 one-sided bins (the largest DFT configuration: 121 bins)."""
+    from paper_2502_12350_gb300 import mamute
+    w = _common_receivers(False, 64, nt=120)
+    og = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
+    ref = gn.separable(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz)
+    dev = torch.device("cuda:0")
+    vel = torch.from_numpy(w.vel).to(dev)
+    H = torch.full_like(vel, float("nan"))
+    ctx.gn_diagonal(mamute.grid_of(w), vel, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                    H, band_rel=0.0)
+    got = H.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
