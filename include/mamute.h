@@ -233,7 +233,8 @@ int mamute_mse_loss(mamute_ctx* ctx, long long n, const float* out, const float*
 /* Network inputs and targets for n voxels: x16 [n][16] BF16 with channel 0
  * = (vel - v_ref) / v_scale and channel 1 = max(log(phess / Pmax),
  * -log_clip) / log_clip, Pmax = max |phess|; if hdiag and target are given,
- * target[p] = log(hdiag[p] / Pmax).  pmax (host, may be NULL) receives Pmax. */
+ * target[p] = log(hdiag[p] / phess[p]).  pmax (host, may be NULL) receives
+ * Pmax. */
 int mamute_nn_features(mamute_ctx* ctx, long long n, const float* vel, const float* phess,
                        const float* hdiag, float v_ref, float v_scale, float log_clip,
                        unsigned short* x16, float* target, float* pmax);

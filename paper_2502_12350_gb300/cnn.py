@@ -2,7 +2,8 @@
 
 A 4-layer 3x3x3 'same' CNN, conv(2->16) ReLU conv(16->16) ReLU
 conv(16->16) ReLU conv(16->1), maps (normalised velocity, log
-pseudo-Hessian) to log(H / Pmax), H the Gauss-Newton diagonal.  Every
+pseudo-Hessian) to log(H / P) - offset, H the Gauss-Newton diagonal and
+P the pseudo-Hessian.  Every
 convolution, gradient, loss and optimizer update runs in libmamute's
 kernels (BF16 products, FP32 accumulation and masters); this module only
 holds the device buffers (torch tensors as memory) and sequences the calls.
@@ -75,6 +76,7 @@ class Net:
         self.wf = [torch.zeros((TAPS, C, C), dtype=torch.int16, device=self.dev) for _ in ws]
         self.wb = [torch.zeros((TAPS, C, C), dtype=torch.int16, device=self.dev) for _ in ws]
         self.step = 0
+        self.offset = 0.0  # added to the output: prediction of log(H / P)
         self._shape = None
         self.pack()
 

@@ -78,6 +78,7 @@ struct mamute_ctx {
   DevBuf hvel, hrho, hseis, hobs, hgrad, hphess;  // staging for the *_host calls
   DevBuf gnV, gnRe, gnIm, gnS, gnR, gnW, gnBins, gnWts, gnRow;  // GN-diagonal scratch
   DevBuf nnPartial, nnLoss;  // network scratch
+  DevBuf slotmaps;           // tensor maps of the checkpoint slots
   int* status = nullptr;
   unsigned int* maxbits = nullptr;
   // timing hook
@@ -574,6 +575,13 @@ cudaError_t step_launch(mamute_ctx* ctx, const StepArgs& a, int n_items, int tx,
   return e;
 }
 
+constexpr int kShotMapStride = (int)(sizeof(ShotMaps) / sizeof(CUtensorMap));
+
+// Map m[idx] of shot 0 in the uploaded per-shot map array.
+const CUtensorMap* shot_map(mamute_ctx* ctx, int idx) {
+  return &((const ShotMaps*)ctx->maps.p)[0].m[idx];
+}
+
 StepArgs fwd_args(mamute_ctx* ctx, const Plan& P, int n, const float* wavelet, float* dout,
                   int mode) {
   StepArgs a{};
@@ -584,8 +592,10 @@ StepArgs fwd_args(mamute_ctx* ctx, const Plan& P, int n, const float* wavelet, f
   a.gx = (const float*)ctx->gx.p;
   a.gy = (const float*)ctx->gy.p;
   a.gz = (const float*)ctx->gz.p;
-  a.fcur = n & 1;
-  a.ucur = 0;
+  a.mF = shot_map(ctx, 2 * (n & 1));            // u^n, halo
+  a.mP = shot_map(ctx, 2 * ((n + 1) & 1) + 1);  // u^{n-1}, centre
+  a.mU = a.mF;
+  a.sF = a.sP = a.sU = kShotMapStride;
   a.wn = wavelet[n];
   a.fout = (float*)ctx->pool[(n + 1) & 1].p;
   a.acc = (float*)ctx->acc.p;
@@ -800,15 +810,65 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   }
   const int fmode_first = all_mode ? MODE_FWD_STORE : (ph ? MODE_FWD_PH : MODE_FWD);
   if (all_mode && ph) return fail(ctx, MAMUTE_EINVAL, "phess is not available with n_snapshots = -1");
-  int recorded = 0;  // steps whose data sample is recorded
+  // Buffers of the forward state: the two working pools (slot -1) or the two
+  // halves of a checkpoint slot.  A restore only switches the state to the
+  // slot's halves; the next step reads them through the slot's own maps and
+  // writes to a working pool.
+  struct Buf {
+    int slot, part;
+    bool operator==(const Buf& o) const { return slot == o.slot && part == o.part; }
+  };
+  const int nvol = (int)P.vols.size();
+  if (!all_mode && slots > 0) {
+    std::vector<CUtensorMap> sm((size_t)slots * nvol * 6);
+    for (int k = 0; k < slots; ++k)
+      for (int v = 0; v < nvol; ++v)
+        for (int q = 0; q < 2; ++q) {
+          const VolDesc& V = P.vols[v];
+          const float* base = (const float*)((const char*)ctx->slots.p + ((size_t)k * 2 + q) * pool) + V.off;
+          CUtensorMap* m = &sm[((size_t)k * nvol + v) * 6 + q * 3];
+          if (encode3d(ctx, m + 0, base, V.Nx, V.Ny, V.Nz, V.pitch, P.tx + 8, P.ty + 8) ||
+              encode3d(ctx, m + 1, base, V.Nx, V.Ny, V.Nz, V.pitch, P.tx, P.ty) ||
+              encode3d(ctx, m + 2, base, V.Nx, V.Ny, V.Nz, V.pitch, P.atx + 8, P.aty + 8))
+            return fail(ctx, MAMUTE_ECUDA, "cuTensorMapEncodeTiled failed (checkpoint slot)");
+        }
+    CK(upload(ctx->slotmaps, sm, ctx->stream));
+  }
+  auto buf_ptr = [&](Buf b) -> char* {
+    return b.slot < 0 ? (char*)ctx->pool[b.part].p
+                      : (char*)ctx->slots.p + ((size_t)b.slot * 2 + b.part) * pool;
+  };
+  // role 0: forward halo, 1: forward centre, 2: adjoint-box halo
+  auto buf_map = [&](Buf b, int role, const CUtensorMap** m, int* stride) {
+    if (b.slot < 0) {
+      static const int idx[3][2] = {{0, 2}, {1, 3}, {9, 10}};
+      *m = shot_map(ctx, idx[role][b.part]);
+      *stride = kShotMapStride;
+    } else {
+      *m = (const CUtensorMap*)ctx->slotmaps.p + ((size_t)b.slot * nvol) * 6 + b.part * 3 + role;
+      *stride = 6;
+    }
+  };
+  Buf cur{-1, 0}, prev{-1, 1};  // u^0 and u^{-1}
+  int sn = 0;                   // time level held in cur
+  int recorded = 0;             // steps whose data sample is recorded
   auto fwd_step = [&](int n, bool first_sweep) -> int {
     const bool rec = first_sweep && n >= recorded;
     const int mode = rec ? fmode_first : MODE_FWD;
     StepArgs a = fwd_args(ctx, P, n, wavelet,
                           (rec && residual_mode) ? (float*)ctx->dint.p + (size_t)n * P.ncol : nullptr,
                           mode);
+    Buf out = prev.slot < 0 ? prev : Buf{-1, cur.slot < 0 ? 1 - cur.part : 0};
+    buf_map(cur, 0, &a.mF, &a.sF);
+    buf_map(prev, 1, &a.mP, &a.sP);
+    a.mU = a.mF;
+    a.sU = a.sF;
+    a.fout = (float*)buf_ptr(out);
     CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
     if (rec) recorded = n + 1;
+    prev = cur;
+    cur = out;
+    sn = n + 1;
     return MAMUTE_OK;
   };
   // Residual in the adjoint tile's column order: r = d - d_obs (or r = d_res).
@@ -842,8 +902,12 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     a.gx = (const float*)ctx->gx.p;
     a.gy = (const float*)ctx->gy.p;
     a.gz = (const float*)ctx->gz.p;
-    a.fcur = (k + 1) & 1;
-    a.ucur = i & 1;
+    a.mF = shot_map(ctx, 4 + 2 * ((k + 1) & 1));  // psi^{k+1}, halo
+    a.mP = shot_map(ctx, 5 + 2 * (k & 1));        // psi^{k+2}, centre
+    a.sF = a.sP = kShotMapStride;
+    // u^i: the current level, or the previous one after the final extra step
+    const Buf u = (sn == i) ? cur : prev;
+    buf_map(u, 2, &a.mU, &a.sU);
     a.wn = 0.f;
     a.fout = (float*)ctx->psi[k & 1].p;
     a.acc = (float*)ctx->acc.p;
@@ -882,30 +946,35 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
         case REV_ADVANCE:
           for (int n = A.a; n < A.b; ++n) TRY(fwd_step(n, first_reverse));
           break;
-        case REV_STORE: {
-          char* dst = (char*)ctx->slots.p + (size_t)A.a * 2 * pool;
-          CK(cudaMemcpyAsync(dst, ctx->pool[0].p, pool, cudaMemcpyDeviceToDevice, ctx->stream));
-          CK(cudaMemcpyAsync(dst + pool, ctx->pool[1].p, pool, cudaMemcpyDeviceToDevice, ctx->stream));
+        case REV_STORE: {  // slot half (m & 1) holds u^m
+          const Buf dc{A.a, sn & 1}, dp{A.a, (sn + 1) & 1};
+          if (!(dc == cur))
+            CK(cudaMemcpyAsync(buf_ptr(dc), buf_ptr(cur), pool, cudaMemcpyDeviceToDevice, ctx->stream));
+          if (!(dp == prev))
+            CK(cudaMemcpyAsync(buf_ptr(dp), buf_ptr(prev), pool, cudaMemcpyDeviceToDevice, ctx->stream));
           break;
         }
         case REV_RESTORE:
           if (A.a < 0) {
             CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
             CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
+            cur = Buf{-1, 0};
+            prev = Buf{-1, 1};
           } else {
-            const char* src = (const char*)ctx->slots.p + (size_t)A.a * 2 * pool;
-            CK(cudaMemcpyAsync(ctx->pool[0].p, src, pool, cudaMemcpyDeviceToDevice, ctx->stream));
-            CK(cudaMemcpyAsync(ctx->pool[1].p, src + pool, pool, cudaMemcpyDeviceToDevice, ctx->stream));
+            cur = Buf{A.a, A.b & 1};
+            prev = Buf{A.a, (A.b + 1) & 1};
           }
+          sn = A.b;
           break;
         case REV_REVERSE:
           if (first_reverse) {
-            // The last forward step yields the final data sample; it
-            // overwrites u^{nt-2}, which no reversal needs.
+            // The last forward step yields the final data sample; u^{nt-1}
+            // stays in the previous-level buffer.
             if (recorded < P.nt) TRY(fwd_step(P.nt - 1, true));
             TRY(begin_adjoint());
             first_reverse = false;
           }
+          if (!(sn == A.a || sn == A.a + 1)) return fail(ctx, MAMUTE_ECUDA, "checkpoint plan out of step");
           TRY(adj_step(A.a));
           break;
       }
@@ -985,72 +1054,97 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   if (nb > dft_max_bins())
     return fail(ctx, MAMUTE_EINVAL, "%d frequency bins exceed the limit %d (raise band_rel)", nb,
                 dft_max_bins());
-  const int kT = 32;
+  // Shots are propagated together and receivers B at a time (one unit
+  // impulse per shot window), so each batch is one launch per step; the DFT
+  // accumulators hold every window of the batch.
+  const int kT = 64;
   const long long N = (long long)P.nx * P.ny * P.nz;
-  CK(ensure(ctx->gnV, (size_t)kT * N * 4));
-  CK(ensure(ctx->gnRe, (size_t)nb * N * 4));
-  CK(ensure(ctx->gnIm, (size_t)nb * N * 4));
+  int B = n_src;
+  {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    const double per_vol = ((double)2 * nb + kT) * (double)N * 4.0;
+    const double fixed = 2.0 * nb * (double)N * 4.0;  // S and R
+    B = (int)std::max(1.0, std::min((double)n_src, (0.6 * (double)fr - fixed) / per_vol));
+  }
+  CK(ensure(ctx->gnV, (size_t)kT * B * N * 4));
+  CK(ensure(ctx->gnRe, (size_t)nb * B * N * 4));
+  CK(ensure(ctx->gnIm, (size_t)nb * B * N * 4));
   CK(ensure(ctx->gnS, (size_t)nb * N * 4));
   CK(ensure(ctx->gnR, (size_t)nb * N * 4));
   CK(ensure(ctx->gnW, (size_t)kT * nb * 8));
   CK(upload(ctx->gnBins, bins, ctx->stream));
   CK(upload(ctx->gnWts, wts, ctx->stream));
   CK(ensure(ctx->gnRow, (size_t)2 * std::max(P.ncol, 1) * 4));
-  for (DevBuf* b : {&ctx->gnRe, &ctx->gnIm, &ctx->gnS, &ctx->gnR})
-    CK(cudaMemsetAsync(b->p, 0, (size_t)nb * N * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->gnRe.p, 0, (size_t)nb * B * N * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->gnIm.p, 0, (size_t)nb * B * N * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->gnS.p, 0, (size_t)nb * N * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->gnR.p, 0, (size_t)nb * N * 4, ctx->stream));
   float* V = (float*)ctx->gnV.p;
   float* re = (float*)ctx->gnRe.p;
   float* im = (float*)ctx->gnIm.p;
   const size_t pool = (size_t)P.pool_elems * 4;
-  auto flush = [&](int upto, int& done) -> int {  // DFT of samples [done, upto)
-    if (upto > done) {
-      CK(aux_count(ctx, launch_dft(V, N, upto - done, done, nf, (const int*)ctx->gnBins.p, nb,
-                                   (float2*)ctx->gnW.p, re, im, ctx->stream)));
-      done = upto;
-    }
-    return MAMUTE_OK;
-  };
-  // Item ranges per shot (items are grouped by shot).
-  auto range = [](const std::vector<WorkItem>& items, int s, int& b, int& e) {
+  // Item ranges of the windows [v0, v1) (items are grouped by window).
+  auto range = [](const std::vector<WorkItem>& items, int v0, int v1, int& b, int& e) {
     b = 0;
-    while (b < (int)items.size() && items[b].vol < s) ++b;
+    while (b < (int)items.size() && items[b].vol < v0) ++b;
     e = b;
-    while (e < (int)items.size() && items[e].vol == s) ++e;
+    while (e < (int)items.size() && items[e].vol < v1) ++e;
   };
-  // Source side.
-  for (int s = 0; s < n_src; ++s) {
+  // Source side: shots [s0, s1) at once.
+  for (int s0 = 0; s0 < n_src; s0 += B) {
+    const int s1 = std::min(n_src, s0 + B), nv = s1 - s0;
+    const long long Nb = (long long)nv * N;
     int ib, ie;
-    range(P.items, s, ib, ie);
+    range(P.items, s0, s1, ib, ie);
     CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
     CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
     int done = 0;
+    auto flush = [&](int upto) -> int {  // DFT of samples [done, upto)
+      if (upto > done) {
+        CK(aux_count(ctx, launch_dft(V, Nb, upto - done, done, nf, (const int*)ctx->gnBins.p, nb,
+                                     (float2*)ctx->gnW.p, re, im, ctx->stream)));
+        done = upto;
+      }
+      return MAMUTE_OK;
+    };
     for (int n = 0; n < nt; ++n) {
       StepArgs a = fwd_args(ctx, P, n, wavelet, nullptr, MODE_FWD_STORE);
       a.items = (const WorkItem*)ctx->items.p + ib;
-      a.tstore = V + (size_t)(n % kT) * N - P.vols[s].toff;
+      a.tstore = V + (size_t)(n % kT) * Nb - (size_t)s0 * N;
       CK(step_launch(ctx, a, ie - ib, P.tx, P.ty, P.dens, MODE_FWD_STORE));
-      if ((n + 1) % kT == 0) TRY(flush(n + 1, done));
+      if ((n + 1) % kT == 0) TRY(flush(n + 1));
     }
-    TRY(flush(nt, done));
-    CK(aux_count(ctx, launch_power((long long)nb * N, re, im, (float*)ctx->gnS.p, ctx->stream)));
+    TRY(flush(nt));
+    CK(aux_count(ctx, launch_power(nb, N, nv, re, im, (float*)ctx->gnS.p, ctx->stream)));
   }
-  // Receiver side: shot 0's geometry, a unit data impulse at the last sample.
-  int ib, ie;
-  range(P.aitems, 0, ib, ie);
+  // Receiver side: receiver r0 + b of the common set in window b, a unit data
+  // impulse at the last sample.
   float* zero_row = (float*)ctx->gnRow.p;
   float* imp_row = zero_row + std::max(P.ncol, 1);
   CK(cudaMemsetAsync(ctx->gnRow.p, 0, (size_t)2 * std::max(P.ncol, 1) * 4, ctx->stream));
-  for (int r = rec_offset[0]; r < rec_offset[1]; ++r) {
-    int col = -1;
-    for (int c = 0; c < P.ncol; ++c)
-      if (P.acolmap[c] == r) col = c;
-    if (col < 0) return fail(ctx, MAMUTE_EINVAL, "receiver %d not planned", r);
-    const float one = 1.0f;
-    CK(cudaMemsetAsync(imp_row, 0, (size_t)std::max(P.ncol, 1) * 4, ctx->stream));
-    CK(cudaMemcpyAsync(imp_row + col, &one, 4, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int> col_of(P.ncol > 0 ? P.ncol : 1, -1);  // global receiver -> adjoint column
+  for (int c = 0; c < P.ncol; ++c) col_of[P.acolmap[c]] = c;
+  std::vector<float> row(std::max(P.ncol, 1));
+  for (int r0 = 0; r0 < nr0; r0 += B) {
+    const int nv = std::min(B, nr0 - r0);
+    const long long Nb = (long long)nv * N;
+    std::fill(row.begin(), row.end(), 0.0f);
+    for (int b = 0; b < nv; ++b) row[col_of[rec_offset[b] + r0 + b]] = 1.0f;
+    CK(cudaMemcpyAsync(imp_row, row.data(), row.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(ctx->psi[0].p, 0, pool, ctx->stream));
     CK(cudaMemsetAsync(ctx->psi[1].p, 0, pool, ctx->stream));
+    int ib, ie;
+    range(P.aitems, 0, nv, ib, ie);
     int done = 0;
+    auto flush = [&](int upto) -> int {
+      if (upto > done) {
+        CK(aux_count(ctx, launch_dft(V, Nb, upto - done, done, nf, (const int*)ctx->gnBins.p, nb,
+                                     (float2*)ctx->gnW.p, re, im, ctx->stream)));
+        done = upto;
+      }
+      return MAMUTE_OK;
+    };
     for (int j = 0; j < nt; ++j) {  // adjoint index k = nt - j holds G[j]
       const int k = nt - j;
       StepArgs a{};
@@ -1061,20 +1155,22 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
       a.gx = (const float*)ctx->gx.p;
       a.gy = (const float*)ctx->gy.p;
       a.gz = (const float*)ctx->gz.p;
-      a.fcur = (k + 1) & 1;
-      a.ucur = 0;
+      a.mF = shot_map(ctx, 4 + 2 * ((k + 1) & 1));  // psi^{k+1}, halo
+      a.mP = shot_map(ctx, 5 + 2 * (k & 1));        // psi^{k+2}, centre
+      a.mU = a.mF;
+      a.sF = a.sP = a.sU = kShotMapStride;
       a.fout = (float*)ctx->psi[k & 1].p;
-      a.tstore = V + (size_t)(j % kT) * N - P.vols[0].toff;
+      a.tstore = V + (size_t)(j % kT) * Nb;
       a.rec_ptr = (const int*)ctx->arecptr.p;
       a.rec = (const RecEntry*)ctx->arec.p;
       a.rin = (j == 0) ? imp_row : zero_row;
       a.status = ctx->status;
       CK(step_launch(ctx, a, ie - ib, P.atx, P.aty, P.dens, MODE_ADJ_TERM));
-      if ((j + 1) % kT == 0) TRY(flush(j + 1, done));
+      if ((j + 1) % kT == 0) TRY(flush(j + 1));
     }
-    TRY(flush(nt, done));
-    CK(aux_count(ctx, launch_power((long long)nb * N, re, im, (float*)ctx->gnR.p, ctx->stream)));
-    CK(cudaStreamSynchronize(ctx->stream));  // the host impulse value is reused
+    TRY(flush(nt));
+    CK(aux_count(ctx, launch_power(nb, N, nv, re, im, (float*)ctx->gnR.p, ctx->stream)));
+    CK(cudaStreamSynchronize(ctx->stream));  // the host impulse row is reused
   }
   CK(aux_count(ctx, launch_assemble(N, nb, (const float*)ctx->gnWts.p, (const float*)ctx->gnR.p,
                                     (const float*)ctx->gnS.p, vel, P.dt, nf, hdiag, ctx->stream)));
@@ -1165,7 +1261,8 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
                    &ctx->arec, &ctx->acolmap, &ctx->acells, &ctx->agvals, &ctx->hvel,
                    &ctx->hrho, &ctx->hseis, &ctx->hobs, &ctx->hgrad, &ctx->hphess,
                    &ctx->gnV, &ctx->gnRe, &ctx->gnIm, &ctx->gnS, &ctx->gnR, &ctx->gnW,
-                   &ctx->gnBins, &ctx->gnWts, &ctx->gnRow, &ctx->nnPartial, &ctx->nnLoss};
+                   &ctx->gnBins, &ctx->gnWts, &ctx->gnRow, &ctx->nnPartial, &ctx->nnLoss,
+                   &ctx->slotmaps};
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);

@@ -278,7 +278,7 @@ __global__ void adam_kernel(int n, float* __restrict__ p, float* __restrict__ m,
 
 // Network inputs: channel 0 = (c - v_ref) / v_scale, channel 1 =
 // max(log(P / Pmax), -lclip) / lclip, other channels 0 (BF16); target =
-// log(H / Pmax) when H is given.
+// log(H / P) when H is given.
 __global__ void features_kernel(long long N, const float* __restrict__ vel,
                                 const float* __restrict__ ph, const float* __restrict__ hd,
                                 const unsigned int* __restrict__ pmax_bits, float v_ref,
@@ -292,7 +292,7 @@ __global__ void features_kernel(long long N, const float* __restrict__ vel,
     uint4* xp = reinterpret_cast<uint4*>(x16 + p * kC);
     xp[0] = make_uint4((uint32_t)f2bf(c) | ((uint32_t)f2bf(lp) << 16), 0, 0, 0);
     xp[1] = make_uint4(0, 0, 0, 0);
-    if (hd && target) target[p] = logf(fmaxf(hd[p], 1e-30f) / pmax);
+    if (hd && target) target[p] = logf(fmaxf(hd[p], 1e-30f) / fmaxf(ph[p], 1e-30f));
   }
 }
 

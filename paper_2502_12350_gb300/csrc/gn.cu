@@ -72,15 +72,23 @@ __global__ void __launch_bounds__(512) dft_kernel(const float* __restrict__ V, l
   }
 }
 
-// pow[k][x] += re^2 + im^2; re = im = 0.
-__global__ void power_kernel(long long n, float* __restrict__ re, float* __restrict__ im,
-                             float* __restrict__ pw) {
+// pw[k][x] += sum_v re[k][v N + x]^2 + im[k][v N + x]^2 over the nv windows
+// of a batch (accumulators laid out [k][nv N]); then re = im = 0.
+__global__ void power_kernel(int nb, long long N, int nv, float* __restrict__ re,
+                             float* __restrict__ im, float* __restrict__ pw) {
+  const long long n = (long long)nb * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const float a = re[i], b = im[i];
-    pw[i] = fmaf(a, a, fmaf(b, b, pw[i]));
-    re[i] = 0.0f;
-    im[i] = 0.0f;
+    const long long k = i / N, x = i % N;
+    float acc = pw[i];
+    for (int v = 0; v < nv; ++v) {
+      const long long j = k * nv * N + v * N + x;
+      const float a = re[j], b = im[j];
+      acc = fmaf(a, a, fmaf(b, b, acc));
+      re[j] = 0.0f;
+      im[j] = 0.0f;
+    }
+    pw[i] = acc;
   }
 }
 
@@ -132,8 +140,9 @@ cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_power(long long n, float* re, float* im, float* pw, cudaStream_t s) {
-  power_kernel<<<blocks_for(n), 256, 0, s>>>(n, re, im, pw);
+cudaError_t launch_power(int nb, long long N, int nv, float* re, float* im, float* pw,
+                         cudaStream_t s) {
+  power_kernel<<<blocks_for((long long)nb * N), 256, 0, s>>>(nb, N, nv, re, im, pw);
   return cudaGetLastError();
 }
 

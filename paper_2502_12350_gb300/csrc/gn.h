@@ -11,8 +11,9 @@ int dft_max_bins();
 // scratch for T * nb twiddles.
 cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const int* bins, int nb,
                        float2* W, float* re, float* im, cudaStream_t s);
-// pw += re^2 + im^2, then re = im = 0 (n elements).
-cudaError_t launch_power(long long n, float* re, float* im, float* pw, cudaStream_t s);
+// pw[k][x] += sum over the nv windows of |acc[k][v N + x]|^2, then acc = 0.
+cudaError_t launch_power(int nb, long long N, int nv, float* re, float* im, float* pw,
+                         cudaStream_t s);
 // H[x] = 4 / (c^6 dt^4 nf) sum_k w[k] R[k][x] S[k][x].
 cudaError_t launch_assemble(long long N, int nb, const float* w, const float* R, const float* S,
                             const float* vel, double dt, int nf, float* H, cudaStream_t s);

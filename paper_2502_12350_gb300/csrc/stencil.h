@@ -24,8 +24,12 @@ struct StepArgs {
   const float* gx;        // x profiles of all shots
   const float* gy;        // y profiles of all shots
   const float* gz;        // z profile (shared)
-  int fcur;               // buffer holding the current level of the propagated field
-  int ucur;               // buffer holding u^{k-1} (adjoint imaging)
+  // Tensor maps of the buffers this step reads, for shot 0; shot v uses
+  // base + v * stride.
+  const CUtensorMap* mF;  // halo map of the current level of the propagated field
+  const CUtensorMap* mP;  // centre map of the previous level
+  const CUtensorMap* mU;  // halo map of u^{k-1} (adjoint imaging)
+  int sF, sP, sU;
   float wn;               // wavelet sample of this step (forward)
   float* fout;            // pool receiving the new level (buffer fcur ^ 1)
   float* acc;             // accumulator pool (pseudo-Hessian or imaging)

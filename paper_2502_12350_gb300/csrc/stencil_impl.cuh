@@ -198,12 +198,10 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
   }
   __syncthreads();
 
-  // Map indices (see ShotMaps): propagated field = buffer `fcur` (halo),
-  // previous level = buffer `fcur ^ 1` (centre).
-  const int fbase = ADJ ? 4 : 0;
-  const CUtensorMap* mapF = &sm->m[fbase + 2 * a.fcur + 0];
-  const CUtensorMap* mapP = &sm->m[fbase + 2 * (a.fcur ^ 1) + 1];
-  const CUtensorMap* mapU = &sm->m[9 + a.ucur];  // forward field for imaging
+  // Maps of the buffers this launch reads (chosen by the host per step).
+  const CUtensorMap* mapF = a.mF + (long long)it.vol * a.sF;
+  const CUtensorMap* mapP = a.mP + (long long)it.vol * a.sP;
+  const CUtensorMap* mapU = a.mU + (long long)it.vol * a.sU;  // forward field for imaging
   const CUtensorMap* mapAcc = &sm->m[ADJ ? 11 : 8];
   const CUtensorMap* mapT = &sm->m[12];
   const CUtensorMap* mapA = &a.cmaps->m[0];

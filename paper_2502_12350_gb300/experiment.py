@@ -23,7 +23,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--train-models", type=int, default=48)
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--epochs", type=int, default=150)
+    ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--nt", type=int, default=1500)
     ap.add_argument("--nx", type=int, default=160)
@@ -50,7 +51,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     report["label_seconds"] = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hist = learned.train(net, data, args.epochs, lr=2e-3, log=print)
+    hist = learned.train(net, data, args.epochs, lr=args.lr,
+                         log=lambda m: print(m) if m.split(":")[0].endswith("0") else None)
     torch.cuda.synchronize()
     report["train_seconds"] = time.perf_counter() - t0
     report["train_loss"] = hist

@@ -127,9 +127,9 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
         if kind == "pseudo":
             return _diag(ph.cpu().numpy())
         vt = torch.from_numpy(x.reshape(shape).astype(np.float32)).to(prob.dev)
-        x16, _, pmax = net.features(vt, ph)
-        out = net.forward(x16)
-        return _diag(pmax * np.exp(out.cpu().numpy().astype(np.float64)))
+        x16, _, _ = net.features(vt, ph)
+        out = net.forward(x16).cpu().numpy().astype(np.float64)
+        return _diag(ph.cpu().numpy().astype(np.float64) * np.exp(out + net.offset))
 
     def line_search(d, J, g, x, max_bt, alpha, expand):
         for _ in range(max_bt + 1):

@@ -4,7 +4,10 @@ Labels are the exact Gauss-Newton diagonal H (mamute_gn_diagonal) of
 seeded models of the layered family, each smoothed by a random Gaussian
 blur so that the inputs look like FWI iterates; the network input is the
 velocity and the source-side pseudo-Hessian P (mamute_model with the
-pseudo-Hessian output).  Everything numerical runs in libmamute.
+pseudo-Hessian output).  The network predicts the log-ratio log(H / P)
+minus its training-set mean (net.offset), i.e. the receiver-side factor the
+pseudo-Hessian lacks; the prediction is H^ = P exp(out + offset).  All
+propagation, label and network arithmetic runs in libmamute.
 """
 from __future__ import annotations
 
@@ -20,7 +23,7 @@ from . import cnn, mamute, synth
 @dataclasses.dataclass
 class Sample:
     x16: torch.Tensor      # network input [D][H][W][16] BF16 bits
-    target: torch.Tensor   # log(H / Pmax) [D][H][W]
+    target: torch.Tensor   # log(H / P) - offset [D][H][W]
     mask: torch.Tensor     # voxels used by the loss [D][H][W]
     n_mask: float
     pmax: float
@@ -52,14 +55,27 @@ def make_sample(ctx: mamute.Context, net: cnn.Net, w, vel: np.ndarray, band_rel:
     return Sample(x16, tgt, mask, float(mask.sum().item()), pmax, v, ph, hd)
 
 
-def dataset(ctx, net, workload_fn, model_ids, blur_max: float = 8.0, seed: int = 0):
-    """Samples for the given model ids; workload_fn(model_id) -> Workload."""
+def dataset(ctx, net, workload_fn, model_ids, blur_max: float = 8.0, seed: int = 0,
+            set_offset: bool = True):
+    """Samples for the given model ids; workload_fn(model_id) -> Workload.
+    With set_offset the network's offset becomes the mean masked log(H / P)
+    of these samples; the targets are centred by the network's offset."""
     rng = np.random.default_rng(seed)
     out = []
     for mid in model_ids:
         w = workload_fn(mid)
         vel = synth.gaussian_blur(w.vel, float(rng.uniform(0.0, blur_max)))
         out.append(make_sample(ctx, net, w, vel))
+    if set_offset:
+        tot, cnt = 0.0, 0.0
+        for s in out:  # host-side statistic of the label set
+            t = s.target.cpu().numpy().astype(np.float64)
+            m = s.mask.cpu().numpy() > 0
+            tot += t[m].sum()
+            cnt += m.sum()
+        net.offset = tot / max(cnt, 1.0)
+    for s in out:
+        s.target.sub_(net.offset)
     return out
 
 
@@ -78,18 +94,25 @@ def train(net: cnn.Net, data, epochs: int, lr: float = 2e-3, seed: int = 0, log=
     return hist
 
 
+def predict(net: cnn.Net, x16: torch.Tensor, phess: torch.Tensor) -> torch.Tensor:
+    """H^ = P exp(out + offset)."""
+    out = net.forward(x16).detach()
+    return phess * torch.exp(out + float(net.offset))
+
+
 def log_errors(net: cnn.Net, data):
-    """Masked RMS of log(H^ / H) for the network and for the best single
-    rescaling of the pseudo-Hessian, log(c P / H) (the method without it)."""
+    """Masked RMS of log(H^ / H) for the network and for the pseudo-Hessian,
+    each after removing its own mean over the model (the preconditioner is
+    insensitive to a global scale, which the L-BFGS scaling absorbs)."""
     res = []
     for s in data:
-        out = net.forward(s.x16).detach()
         m = s.mask > 0
         lh = torch.log(s.hdiag.clamp_min(1e-30))
-        ln = out + float(np.log(max(s.pmax, 1e-30)))
+        ln = torch.log(predict(net, s.x16, s.phess).clamp_min(1e-30))
         lp = torch.log(s.phess.clamp_min(1e-30))
         e_net = (ln - lh)[m]
         e_p = (lp - lh)[m]
-        e_p = e_p - e_p.mean()  # best constant rescaling of P
+        e_net = e_net - e_net.mean()
+        e_p = e_p - e_p.mean()
         res.append((float(torch.sqrt((e_net ** 2).mean())), float(torch.sqrt((e_p ** 2).mean()))))
     return res

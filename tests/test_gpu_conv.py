@@ -133,3 +133,29 @@ def test_training_reduces_loss(net_mod):
     xt, tt = torch.from_numpy(_bf16_bits(x)).to(dev), torch.from_numpy(t).to(dev)
     losses = [net.train_step(xt, tt, lr=3e-3) for _ in range(150)]
     assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+
+
+def test_network_features(net_mod):
+    """Input channels and log-ratio target against a float64 restatement:
+    channel 0 = (c - v_ref) / v_scale, channel 1 = clipped log(P / Pmax)
+    / clip (both rounded to BF16), channels 2..15 zero, target = log(H / P)."""
+    ctx, cnn = net_mod
+    rng = np.random.default_rng(11)
+    D, H, W = 5, 7, 9
+    vel = rng.uniform(1500.0, 4500.0, (D, H, W)).astype(np.float32)
+    ph = np.exp(rng.uniform(-30.0, 0.0, (D, H, W))).astype(np.float32) * 3.0
+    hd = np.exp(rng.uniform(-10.0, 2.0, (D, H, W))).astype(np.float32)
+    dev = torch.device("cuda:0")
+    net = cnn.Net(ctx, seed=0)
+    x16, tgt, pmax = net.features(torch.from_numpy(vel).to(dev), torch.from_numpy(ph).to(dev),
+                                  torch.from_numpy(hd).to(dev), 3000.0, 1000.0, 20.0)
+    assert pmax == float(ph.max())
+    x = _from_bits(x16).astype(np.float64)
+    c = (vel.astype(np.float64) - 3000.0) / 1000.0
+    lp = np.maximum(np.log(ph.astype(np.float64) / ph.max()), -20.0) / 20.0
+    # BF16 keeps 8 significant bits: half an ulp of rounding plus the FP32 log
+    np.testing.assert_allclose(x[..., 0], c, rtol=2.0 ** -8, atol=1e-6)
+    np.testing.assert_allclose(x[..., 1], lp, rtol=2.0 ** -8, atol=1e-6)
+    assert not x[..., 2:].any()
+    t = np.log(hd.astype(np.float64) / ph.astype(np.float64))
+    np.testing.assert_allclose(tgt.cpu().numpy(), t, rtol=0, atol=1e-4 * np.abs(t).max())
