@@ -74,11 +74,14 @@ typedef struct {
 } mamute_grid;
 
 /* Options (Table 4 check_mem; Sec. 3 zeroes_nplanes_gradient).
- *   check_mem       fraction (0,1] of free device memory that checkpoint
- *                   slots may use when n_snapshots == 0 (default 0.8).
- *   n_snapshots     0: as many revolve slots as check_mem allows;
- *                   >0: exactly that many slots; -1: keep the imaging term of
- *                   every step (no recomputation).
+ *   check_mem       fraction (0,1] of free device memory that the stored
+ *                   states may use when n_snapshots == 0 (default 0.8).
+ *   n_snapshots     0: automatic: keep the imaging term of every step when
+ *                   nt x (interior points) x 4 bytes fits in check_mem of
+ *                   the free memory and phess is NULL, else as many revolve
+ *                   slots as check_mem allows; >0: exactly that many revolve
+ *                   slots; -1: keep the imaging term of every step (no
+ *                   recomputation).
  *   zero_top_planes ZeroesNearSurface: gradient planes z < this are zeroed.
  *   aperture        host [n_src][4] or NULL: shot s propagates only over the
  *                   model columns x in [a0, a1), y in [a2, a3) plus the sponge

@@ -769,7 +769,24 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   CK(cudaMemsetAsync(ctx->misfit.p, 0, 8, ctx->stream));
   // Storage mode.
   const int nsnap = opts ? opts->n_snapshots : 0;
-  const bool all_mode = nsnap < 0;
+  const double frac = (opts && opts->check_mem > 0.f) ? opts->check_mem : 0.8;
+  bool all_mode = nsnap < 0;
+  if (nsnap == 0 && !ph) {
+    // Automatic: keep every step's imaging term (no recomputation) when the
+    // store fits in check_mem of the free memory, else revolve.
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    const size_t need = (size_t)P.nt * P.term_elems * 4;
+    const double avail = (double)fr + (double)ctx->tstore.bytes + (double)ctx->slots.bytes;
+    if ((double)need <= frac * avail) {
+      release(ctx->slots);
+      if (ensure(ctx->tstore, need) == cudaSuccess)
+        all_mode = true;
+      else
+        cudaGetLastError();
+    }
+  }
+  if (!all_mode && ctx->tstore.p) release(ctx->tstore);  // room for the slots
   int slots = 0;
   if (all_mode) {
     CK(ensure(ctx->tstore, (size_t)P.nt * P.term_elems * 4));
@@ -796,7 +813,6 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   } else {
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
-    const double frac = (opts && opts->check_mem > 0.f) ? opts->check_mem : 0.8;
     const double per = 2.0 * (double)pool;
     // Slots this context already holds count as available.
     const double avail = (double)fr + (double)ctx->slots.bytes;

@@ -47,7 +47,7 @@ def main(argv=None):
     train_ids = list(range(5000, 5000 + args.train_models))
     test_ids = list(range(5380, 5384))
     data = learned.dataset(ctx, net, wl, train_ids, seed=1)
-    held = learned.dataset(ctx, net, wl, test_ids, seed=2)
+    held = learned.dataset(ctx, net, wl, test_ids, seed=2, set_offset=False)
     torch.cuda.synchronize()
     report["label_seconds"] = time.perf_counter() - t0
     t0 = time.perf_counter()

@@ -27,7 +27,7 @@ def setup():
 
     net = cnn.Net(ctx, seed=1)
     train = learned.dataset(ctx, net, wl, list(range(5000, 5016)), seed=1)
-    held = learned.dataset(ctx, net, wl, list(range(5380, 5384)), seed=2)
+    held = learned.dataset(ctx, net, wl, list(range(5380, 5384)), seed=2, set_offset=False)
     yield ctx, net, learned, wl, train, held
     ctx.close()
 

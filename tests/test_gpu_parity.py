@@ -171,6 +171,36 @@ def test_gradient_bitwise_identical_across_snapshot_modes(ctx):
         np.testing.assert_array_equal(g, g0)
 
 
+def test_automatic_storage_keeps_every_term_when_it_fits(ctx):
+    """n_snapshots = 0 on a small grid keeps every imaging term: one forward
+    and one adjoint launch per step, and the all-states result."""
+    import ctypes
+    from paper_2502_12350_gb300 import mamute
+    lib = mamute.load()
+    lib.mamute_ctx_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mamute_ctx_last_timing.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_longlong)]
+    w = _grad_case(True, seed=12, nt=29)
+    dobs = np.zeros((int(w.rec_offset[-1]), w.nt), np.float32)
+    J0, g0 = gpu_gradient(ctx, w, dobs, n_snapshots=-1)
+    lib.mamute_ctx_set_timing(ctx._h, 1)
+    try:
+        J, g = gpu_gradient(ctx, w, dobs, n_snapshots=0)
+        sl = ctypes.c_longlong()
+        lib.mamute_ctx_last_timing(ctx._h, None, ctypes.byref(sl), None)
+        Jr, gr = gpu_gradient(ctx, w, dobs, n_snapshots=3)
+        slr = ctypes.c_longlong()
+        lib.mamute_ctx_last_timing(ctx._h, None, ctypes.byref(slr), None)
+    finally:
+        lib.mamute_ctx_set_timing(ctx._h, 0)
+    assert sl.value == 2 * w.nt
+    assert slr.value > 2 * w.nt  # revolve with 3 slots recomputes
+    assert J == J0 and Jr == J0
+    np.testing.assert_array_equal(g, g0)
+    np.testing.assert_array_equal(gr, g0)
+
+
 def test_adjoint_is_transpose_applied_to_data(ctx, oracle):
     """mamute_adjoint(d_res) equals the oracle gradient whose residual is d_res."""
     from paper_2502_12350_gb300 import mamute
