@@ -309,25 +309,50 @@ def run_gn_bench(args):
     build.build()
     dev = torch.device("cuda", 0)
     ctx = mamute.Context(0)
+    import ctypes
     w = synth.fwi_small(model_id=5000) if args.nt is None else synth.fwi_small(model_id=5000, nt=args.nt)
     g = mamute.grid_of(w)
     v = torch.from_numpy(w.vel).to(dev)
     hd = torch.empty_like(v)
+    lib = mamute.load()
+    lib.mamute_ctx_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    D, LL = ctypes.c_double, ctypes.c_longlong
+    lib.mamute_ctx_dft_timing.argtypes = [ctypes.c_void_p, ctypes.POINTER(D), ctypes.POINTER(LL),
+                                          ctypes.POINTER(D)]
+    lib.mamute_ctx_set_timing(ctx._h, 1)
     for _ in range(args.warmup):
         ctx.gn_diagonal(g, v, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, hd)
     torch.cuda.synchronize()
-    t0 = _t.perf_counter()
-    for _ in range(args.steps):
-        ctx.gn_diagonal(g, v, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, hd)
-    torch.cuda.synchronize()
-    sec = (_t.perf_counter() - t0) / args.steps
+    dft_ms, dft_n, macs = 0.0, 0, 0.0
+    with ClockSampler(0) as clk:
+        t0 = _t.perf_counter()
+        for _ in range(args.steps):
+            ctx.gn_diagonal(g, v, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, hd)
+            ms, n, m = D(), LL(), D()
+            lib.mamute_ctx_dft_timing(ctx._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(m))
+            dft_ms, dft_n, macs = dft_ms + ms.value, dft_n + n.value, macs + m.value
+        torch.cuda.synchronize()
+        sec = (_t.perf_counter() - t0) / args.steps
     props = w.n_src + int(w.rec_offset[1])
+    # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x max SM clock
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        mhz = json.load(f).get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = 4.0 * macs / (dft_ms * 1e-3) / 1e12 if dft_ms > 0 else None
     line = {"metric": "GN-diagonal labels/s", "value": 1.0 / sec, "unit": "models/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": w.name, "nt": w.nt, "propagations": props,
-                       "gpt_updates_per_s": props * w.n_padded * w.nt / sec / 1e9}}
+                       "gpt_updates_per_s": props * w.n_padded * w.nt / sec / 1e9},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak if achieved else None, "traffic": None,
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz",
+                         "kernel": "dft_kernel (with twiddles)",
+                         "flops_per_unit": 4, "unit_of_work": "point x sample x bin",
+                         "dft_share_of_step": dft_ms / args.steps / (sec * 1e3),
+                         "dft_launches_per_step": dft_n // max(args.steps, 1)},
+            "clocks": clk.summary()}
     ctx.close()
     print(json.dumps(line), flush=True)
     return 0

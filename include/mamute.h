@@ -269,6 +269,15 @@ int mamute_ctx_set_timing(mamute_ctx* ctx, int enable);
 int mamute_ctx_last_timing(const mamute_ctx* ctx, double* loop_ms, long long* step_launches,
                            long long* total_launches);
 
+/* For the last mamute_gn_diagonal call made with timing enabled: the summed
+ * device milliseconds of its DFT accumulations (an event pair on the
+ * context's stream around each twiddle + DFT launch), their number, and the
+ * complex multiply-adds they performed (points x samples x bins, each four
+ * FP32 flops).  NULL outputs are skipped; EINVAL for a NULL context.  No
+ * counterpart in the paper: it measures the labels' FP32 ALU roofline. */
+int mamute_ctx_dft_timing(const mamute_ctx* ctx, double* dft_ms, long long* dft_launches,
+                          double* complex_macs);
+
 /* Misfit J = 1/2 sum_i (d[i] - d_obs[i])^2 (FP64 sums of FP32 residuals)
  * for callers that cannot allocate device memory, e.g. because a host
  * framework's caching allocator already holds the device's memory, or because

@@ -87,6 +87,10 @@ struct mamute_ctx {
   bool ev0_set = false;
   double loop_ms = 0.0;
   long long step_launches = 0, launches = 0;
+  // event pairs around the DFT launches of mamute_gn_diagonal
+  std::vector<cudaEvent_t> dft_ev;
+  int dft_n = 0;
+  double dft_ms = 0.0, dft_macs = 0.0;
   int max_planes = 1;  // planes per work item of the current call
   // captured time loop of the last mamute_model call and its signature
   cudaGraphExec_t graph = nullptr;
@@ -572,6 +576,31 @@ cudaError_t step_launch(mamute_ctx* ctx, const StepArgs& a, int n_items, int tx,
   ++ctx->launches;
   cudaError_t e = launch_step(a, n_items, ctx->max_planes, tx, ty, dens, mode, ctx->stream);
   if (e == cudaSuccess && ctx->timing) e = cudaEventRecord(ctx->ev1, ctx->stream);
+  return e;
+}
+
+// One DFT accumulation (twiddles + dft_kernel), timed by an event pair
+// when the timing hook is on.
+cudaError_t dft_launch(mamute_ctx* ctx, const float* V, long long N, int T, int n0, int nf,
+                       const int* bins, int nb, float2* W, float* re, float* im) {
+  cudaError_t e = cudaSuccess;
+  if (ctx->timing) {
+    while (ctx->dft_ev.size() < (size_t)2 * ctx->dft_n + 2) {
+      cudaEvent_t ev = nullptr;
+      e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return e;
+      ctx->dft_ev.push_back(ev);
+    }
+    e = cudaEventRecord(ctx->dft_ev[2 * ctx->dft_n], ctx->stream);
+    if (e != cudaSuccess) return e;
+  }
+  ctx->launches += 2;
+  e = launch_dft(V, N, T, n0, nf, bins, nb, W, re, im, ctx->stream);
+  if (e == cudaSuccess && ctx->timing && T > 0) {
+    e = cudaEventRecord(ctx->dft_ev[2 * ctx->dft_n + 1], ctx->stream);
+    ++ctx->dft_n;
+    ctx->dft_macs += (double)N * T * nb;
+  }
   return e;
 }
 
@@ -1067,6 +1096,8 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
       wts.push_back((k == 0 || k == nt) ? 1.0f : 2.0f);
     }
   const int nb = (int)bins.size();
+  ctx->dft_n = 0;
+  ctx->dft_ms = ctx->dft_macs = 0.0;
   if (nb > dft_max_bins())
     return fail(ctx, MAMUTE_EINVAL, "%d frequency bins exceed the limit %d (raise band_rel)", nb,
                 dft_max_bins());
@@ -1082,6 +1113,8 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
     const double per_vol = ((double)2 * nb + kT) * (double)N * 4.0;
     const double fixed = 2.0 * nb * (double)N * 4.0;  // S and R
     B = (int)std::max(1.0, std::min((double)n_src, (0.6 * (double)fr - fixed) / per_vol));
+    const int cap = env_int("MAMUTE_GN_BATCH", 0);  // smaller batches (profiling)
+    if (cap > 0) B = std::min(B, cap);
   }
   CK(ensure(ctx->gnV, (size_t)kT * B * N * 4));
   CK(ensure(ctx->gnRe, (size_t)nb * B * N * 4));
@@ -1118,8 +1151,8 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
     int done = 0;
     auto flush = [&](int upto) -> int {  // DFT of samples [done, upto)
       if (upto > done) {
-        CK(aux_count(ctx, launch_dft(V, Nb, upto - done, done, nf, (const int*)ctx->gnBins.p, nb,
-                                     (float2*)ctx->gnW.p, re, im, ctx->stream)));
+        CK(dft_launch(ctx, V, Nb, upto - done, done, nf, (const int*)ctx->gnBins.p, nb,
+                      (float2*)ctx->gnW.p, re, im));
         done = upto;
       }
       return MAMUTE_OK;
@@ -1155,8 +1188,8 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
     int done = 0;
     auto flush = [&](int upto) -> int {
       if (upto > done) {
-        CK(aux_count(ctx, launch_dft(V, Nb, upto - done, done, nf, (const int*)ctx->gnBins.p, nb,
-                                     (float2*)ctx->gnW.p, re, im, ctx->stream)));
+        CK(dft_launch(ctx, V, Nb, upto - done, done, nf, (const int*)ctx->gnBins.p, nb,
+                      (float2*)ctx->gnW.p, re, im));
         done = upto;
       }
       return MAMUTE_OK;
@@ -1190,7 +1223,13 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   }
   CK(aux_count(ctx, launch_assemble(N, nb, (const float*)ctx->gnWts.p, (const float*)ctx->gnR.p,
                                     (const float*)ctx->gnS.p, vel, P.dt, nf, hdiag, ctx->stream)));
-  return finish(ctx);
+  TRY(finish(ctx));
+  for (int i = 0; i < ctx->dft_n; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->dft_ev[2 * i], ctx->dft_ev[2 * i + 1]));
+    ctx->dft_ms += ms;
+  }
+  return MAMUTE_OK;
 }
 
 }  // namespace
@@ -1231,6 +1270,15 @@ int mamute_ctx_last_timing(const mamute_ctx* ctx, double* loop_ms, long long* st
   if (loop_ms) *loop_ms = ctx->loop_ms;
   if (step_launches) *step_launches = ctx->step_launches;
   if (total_launches) *total_launches = ctx->launches;
+  return MAMUTE_OK;
+}
+
+int mamute_ctx_dft_timing(const mamute_ctx* ctx, double* dft_ms, long long* dft_launches,
+                          double* complex_macs) {
+  if (!ctx) return MAMUTE_EINVAL;
+  if (dft_ms) *dft_ms = ctx->dft_ms;
+  if (dft_launches) *dft_launches = ctx->dft_n;
+  if (complex_macs) *complex_macs = ctx->dft_macs;
   return MAMUTE_OK;
 }
 
@@ -1282,6 +1330,7 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);
+  for (cudaEvent_t ev : ctx->dft_ev) cudaEventDestroy(ev);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);

@@ -5,12 +5,16 @@
 // over the retained frequency bins k of an N_f = 2 nt zero-padded DFT.
 #include "gn.h"
 
+#include <cstdint>
+
 namespace mamute {
 
 namespace {
 
-constexpr int kPts = 64;    // points per CTA
+constexpr int kPts = 128;   // points per CTA
+constexpr int kPP = 4;      // consecutive points per thread
 constexpr int kChunk = 16;  // frequency bins per thread
+constexpr int kGroups = kPts / kPP;  // point groups: one warp
 
 // Twiddles W[t][k] = exp(-2 pi i bins[k] (n0 + t) / nf) for one time block.
 __global__ void twiddle_kernel(int T, int n0, int nf, const int* __restrict__ bins, int nb,
@@ -24,50 +28,85 @@ __global__ void twiddle_kernel(int T, int n0, int nf, const int* __restrict__ bi
   W[i] = make_float2(cs, -sn);
 }
 
-// acc[k][x] += sum_t V[t][x] W[t][k] for kPts points per CTA; thread
-// (p, c) owns point p and bins [c kChunk, (c+1) kChunk).
-__global__ void __launch_bounds__(512) dft_kernel(const float* __restrict__ V, long long N, int T, int nb,
-                           const float2* __restrict__ W, float* __restrict__ re,
-                           float* __restrict__ im) {
-  extern __shared__ float sm[];
-  float* Vs = sm;                                        // [T][kPts]
-  float2* Ws = reinterpret_cast<float2*>(sm + T * kPts);  // [T][nb]
+// acc[k][x] += sum_t V[t][x] W[t][k] for kPts points per CTA.  Warp c owns
+// bins [c kChunk, (c+1) kChunk); lane g owns points 4g..4g+3 of the CTA, so
+// per time sample a thread does 4 x 16 complex MACs from one 16-byte read of
+// V and eight broadcast 16-byte reads of W (FP32 FMA bound, not LSU bound).
+// VEC: N is a multiple of 4, so the accumulator rows take 16-byte accesses.
+template <bool VEC>
+__global__ void __launch_bounds__(256, 1)
+    dft_kernel(const float* __restrict__ V, long long N, int T, int nb,
+               const float2* __restrict__ W, float* __restrict__ re, float* __restrict__ im) {
+  extern __shared__ float4 sm4[];
+  float* Vs = reinterpret_cast<float*>(sm4);                // [T][kPts]
+  const int nbp = (blockDim.x / 32) * kChunk;             // bins padded to the warps
+  float2* Ws = reinterpret_cast<float2*>(Vs + T * kPts);  // [T][nbp], zero beyond nb
   const long long x0 = (long long)blockIdx.x * kPts;
-  for (int i = threadIdx.x; i < T * nb; i += blockDim.x) Ws[i] = W[i];
+  for (int i = threadIdx.x; i < T * nbp; i += blockDim.x) {
+    const int t = i / nbp, k = i % nbp;
+    Ws[i] = k < nb ? W[t * nb + k] : make_float2(0.0f, 0.0f);
+  }
   for (int i = threadIdx.x; i < T * kPts; i += blockDim.x) {
     const int t = i / kPts, p = i % kPts;
     const long long x = x0 + p;
     Vs[i] = x < N ? V[(long long)t * N + x] : 0.0f;
   }
   __syncthreads();
-  const int p = threadIdx.x % kPts, c = threadIdx.x / kPts;
-  const long long x = x0 + p;
-  if (x >= N) return;
-  float ar[kChunk], ai[kChunk];
+  const int g = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const long long xb = x0 + kPP * g;
+  if (xb >= N) return;
+  float ar[kPP][kChunk], ai[kPP][kChunk];
 #pragma unroll
   for (int j = 0; j < kChunk; ++j) {
     const int k = c * kChunk + j;
-    ar[j] = k < nb ? re[(long long)k * N + x] : 0.0f;
-    ai[j] = k < nb ? im[(long long)k * N + x] : 0.0f;
-  }
-  for (int t = 0; t < T; ++t) {
-    const float v = Vs[t * kPts + p];
-    const float2* wr = Ws + t * nb + c * kChunk;
+    if (VEC && k < nb) {  // xb + 3 < N as N is a multiple of 4
+      const float4 r = *reinterpret_cast<const float4*>(re + (long long)k * N + xb);
+      const float4 m = *reinterpret_cast<const float4*>(im + (long long)k * N + xb);
+      ar[0][j] = r.x; ar[1][j] = r.y; ar[2][j] = r.z; ar[3][j] = r.w;
+      ai[0][j] = m.x; ai[1][j] = m.y; ai[2][j] = m.z; ai[3][j] = m.w;
+    } else {
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) {
-      if (c * kChunk + j < nb) {
-        const float2 w = wr[j];
-        ar[j] = fmaf(v, w.x, ar[j]);
-        ai[j] = fmaf(v, w.y, ai[j]);
+      for (int q = 0; q < kPP; ++q) {
+        const bool ok = k < nb && xb + q < N;
+        ar[q][j] = ok ? re[(long long)k * N + xb + q] : 0.0f;
+        ai[q][j] = ok ? im[(long long)k * N + xb + q] : 0.0f;
+      }
+    }
+  }
+#pragma unroll 2
+  for (int t = 0; t < T; ++t) {
+    const float4 v = *reinterpret_cast<const float4*>(Vs + t * kPts + kPP * g);
+    const float vq[kPP] = {v.x, v.y, v.z, v.w};
+    const float4* w4 = reinterpret_cast<const float4*>(Ws + t * nbp + c * kChunk);
+#pragma unroll
+    for (int jj = 0; jj < kChunk / 2; ++jj) {
+      const float4 w = w4[jj];  // bins 2jj and 2jj + 1
+#pragma unroll
+      for (int q = 0; q < kPP; ++q) {
+        ar[q][2 * jj] = fmaf(vq[q], w.x, ar[q][2 * jj]);
+        ai[q][2 * jj] = fmaf(vq[q], w.y, ai[q][2 * jj]);
+        ar[q][2 * jj + 1] = fmaf(vq[q], w.z, ar[q][2 * jj + 1]);
+        ai[q][2 * jj + 1] = fmaf(vq[q], w.w, ai[q][2 * jj + 1]);
       }
     }
   }
 #pragma unroll
   for (int j = 0; j < kChunk; ++j) {
     const int k = c * kChunk + j;
-    if (k < nb) {
-      re[(long long)k * N + x] = ar[j];
-      im[(long long)k * N + x] = ai[j];
+    if (k >= nb) continue;
+    if (VEC) {
+      *reinterpret_cast<float4*>(re + (long long)k * N + xb) =
+          make_float4(ar[0][j], ar[1][j], ar[2][j], ar[3][j]);
+      *reinterpret_cast<float4*>(im + (long long)k * N + xb) =
+          make_float4(ai[0][j], ai[1][j], ai[2][j], ai[3][j]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kPP; ++q) {
+        if (xb + q < N) {
+          re[(long long)k * N + xb + q] = ar[q][j];
+          im[(long long)k * N + xb + q] = ai[q][j];
+        }
+      }
     }
   }
 }
@@ -118,25 +157,35 @@ int blocks_for(long long n) {
 
 }  // namespace
 
-size_t dft_smem_bytes(int T, int nb) { return sizeof(float) * T * kPts + sizeof(float2) * T * nb; }
+size_t dft_smem_bytes(int T, int nb) {
+  const int nbp = ((nb + kChunk - 1) / kChunk) * kChunk;
+  return sizeof(float) * T * kPts + sizeof(float2) * T * nbp;
+}
 
-int dft_max_bins() { return (512 / kPts) * kChunk; }
+int dft_max_bins() { return (256 / 32) * kChunk; }
 
 cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const int* bins, int nb,
                        float2* W, float* re, float* im, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
+  if (nb < 1 || nb > dft_max_bins()) return cudaErrorInvalidValue;
   twiddle_kernel<<<(T * nb + 255) / 256, 256, 0, s>>>(T, n0, nf, bins, nb, W);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t sm = dft_smem_bytes(T, nb);
-  static size_t attr = 0;
-  if (sm > attr) {
-    e = cudaFuncSetAttribute(dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const bool vec = (N % 4) == 0 && ((uintptr_t)re % 16) == 0 && ((uintptr_t)im % 16) == 0;
+  static size_t attr[2] = {0, 0};
+  if (sm > attr[vec]) {
+    e = vec ? cudaFuncSetAttribute(dft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+            : cudaFuncSetAttribute(dft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr = sm;
+    attr[vec] = sm;
   }
-  const int chunks = (nb + kChunk - 1) / kChunk;
-  dft_kernel<<<(int)((N + kPts - 1) / kPts), kPts * chunks, sm, s>>>(V, N, T, nb, W, re, im);
+  const int warps = (nb + kChunk - 1) / kChunk;
+  const unsigned grid = (unsigned)((N + kPts - 1) / kPts);
+  if (vec)
+    dft_kernel<true><<<grid, 32 * warps, sm, s>>>(V, N, T, nb, W, re, im);
+  else
+    dft_kernel<false><<<grid, 32 * warps, sm, s>>>(V, N, T, nb, W, re, im);
   return cudaGetLastError();
 }
 
