@@ -595,7 +595,7 @@ cudaError_t dft_launch(mamute_ctx* ctx, const float* V, long long N, int T, int 
     if (e != cudaSuccess) return e;
   }
   ctx->launches += 2;
-  e = launch_dft(V, N, T, n0, nf, bins, nb, W, re, im, ctx->stream);
+  e = launch_dft(V, N, T, n0, nf, bins, nb, W, re, im, ctx->status, ctx->stream);
   if (e == cudaSuccess && ctx->timing && T > 0) {
     e = cudaEventRecord(ctx->dft_ev[2 * ctx->dft_n + 1], ctx->stream);
     ++ctx->dft_n;
@@ -1121,7 +1121,7 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   CK(ensure(ctx->gnIm, (size_t)nb * B * N * 4));
   CK(ensure(ctx->gnS, (size_t)nb * N * 4));
   CK(ensure(ctx->gnR, (size_t)nb * N * 4));
-  CK(ensure(ctx->gnW, (size_t)kT * nb * 8));
+  CK(ensure(ctx->gnW, (size_t)kT * dft_max_bins() * 8));
   CK(upload(ctx->gnBins, bins, ctx->stream));
   CK(upload(ctx->gnWts, wts, ctx->stream));
   CK(ensure(ctx->gnRow, (size_t)2 * std::max(P.ncol, 1) * 4));
@@ -1440,15 +1440,45 @@ static int nn_end(mamute_ctx* ctx) {
   return MAMUTE_OK;
 }
 
+// TMA map over a [D][H][W][16] BF16 activation (innermost first: channels,
+// x, y, z) with the 32-byte swizzle and zero fill outside.
+static CUresult encode_act(mamute_ctx* ctx, CUtensorMap* m, const void* p, int D, int H, int W,
+                           const unsigned (&box)[4]) {
+  cuuint64_t dims[4] = {16, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
+  cuuint64_t strides[3] = {32, (cuuint64_t)W * 32, (cuuint64_t)W * H * 32};
+  cuuint32_t cbox[4] = {box[0], box[1], box[2], box[3]};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return ctx->encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(p), dims, strides,
+                     cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+// As nn_end, for kernels with bounded device-side waits.
+static int nn_end_status(mamute_ctx* ctx) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st & kErrTimeout) return fail(ctx, MAMUTE_ETIMEOUT, "a device-side wait ran out");
+  return MAMUTE_OK;
+}
+
 int mamute_conv3d(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
                   const unsigned short* w, const float* bias, int relu,
                   const unsigned short* mask, float* y32, unsigned short* y16) {
   TRY(nn_begin(ctx));
   if (D < 1 || H < 1 || W < 1 || !x || !w || (!y32 && !y16))
     return fail(ctx, MAMUTE_EINVAL, "conv3d: bad arguments");
+  if ((uintptr_t)x % 16)
+    return fail(ctx, MAMUTE_EINVAL, "conv3d: x must be 16-byte aligned");
   ConvArgs a{x, w, bias, relu, mask, y32, y16, D, H, W};
-  CK(launch_conv(a, ctx->stream));
-  return nn_end(ctx);
+  CUtensorMap xmap;
+  unsigned box[4];
+  conv_halo_box(box);
+  if (encode_act(ctx, &xmap, x, D, H, W, box))
+    return fail(ctx, MAMUTE_ECUDA, "conv3d: cuTensorMapEncodeTiled failed");
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  CK(launch_conv(a, xmap, ctx->status, ctx->stream));
+  return nn_end_status(ctx);
 }
 
 int mamute_conv3d_wgrad(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
@@ -1456,10 +1486,19 @@ int mamute_conv3d_wgrad(mamute_ctx* ctx, int D, int H, int W, const unsigned sho
   TRY(nn_begin(ctx));
   if (D < 1 || H < 1 || W < 1 || !x || !gy || !gw || !gb)
     return fail(ctx, MAMUTE_EINVAL, "conv3d_wgrad: bad arguments");
+  if ((uintptr_t)x % 16 || (uintptr_t)gy % 16)
+    return fail(ctx, MAMUTE_EINVAL, "conv3d_wgrad: x and gy must be 16-byte aligned");
   CK(ensure(ctx->nnPartial, wgrad_partial_floats() * 4));
   WgradArgs a{x, gy, (float*)ctx->nnPartial.p, D, H, W};
-  CK(launch_wgrad(a, gw, gb, ctx->stream));
-  return nn_end(ctx);
+  CUtensorMap xmap, gmap;
+  unsigned hbox[4], gbox[4];
+  conv_halo_box(hbox);
+  conv_gy_box(gbox);
+  if (encode_act(ctx, &xmap, x, D, H, W, hbox) || encode_act(ctx, &gmap, gy, D, H, W, gbox))
+    return fail(ctx, MAMUTE_ECUDA, "conv3d_wgrad: cuTensorMapEncodeTiled failed");
+  CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+  CK(launch_wgrad(a, xmap, gmap, ctx->status, gw, gb, ctx->stream));
+  return nn_end_status(ctx);
 }
 
 int mamute_conv3d_pack(mamute_ctx* ctx, const float* w, unsigned short* fwd,

@@ -68,71 +68,196 @@ __device__ __forceinline__ void load_halo(uint4* halo, const uint16_t* __restric
   }
 }
 
-__global__ void __launch_bounds__(256) conv_fwd_kernel(ConvArgs a) {
-  __shared__ __align__(128) uint4 halo[kHZ * kHY * kHX * 2];
+// Forward / input-gradient convolution, persistent: a CTA walks tiles of
+// 16 (x) x 8 (y) x 4 (z) output voxels.  The 18 x 10 x 6 input halo of a
+// tile (34,560 B, zero outside the volume) arrives by one 4-D TMA load with
+// the 32-byte swizzle (16-byte channel halves of voxel v swap when bit 2 of
+// v is set, so ldmatrix rows of consecutive voxels hit distinct banks), into
+// a double buffer: the next tile's load overlaps this tile's products.
+// Warp w owns the 2 x 2 output rows y = 2 (w & 3) + {0, 1},
+// z = 2 (w >> 2) + {0, 1}; every A fragment it loads (16 halo voxels x 16
+// channels of one halo row, shifted by dx) feeds each output row it
+// reaches (up to 4 x 2 products), and the 27 taps' B fragments live in
+// registers for the whole kernel.
+constexpr int kFZ = 4;                                  // output planes per tile
+constexpr int kFHZ = kFZ + 2;                           // halo planes
+constexpr int kFHalo = kFHZ * kHY * kHX * kC * 2;       // bytes per halo buffer
+static_assert(kFHalo % 256 == 0, "halo buffers must stay 256-byte aligned");
+
+__device__ __forceinline__ int swz(int v, int half) { return 2 * v + (half ^ ((v >> 2) & 1)); }
+
+__global__ void __launch_bounds__(256, 1)
+    conv_fwd_kernel(const __grid_constant__ CUtensorMap xmap, ConvArgs a, int* status) {
+  extern __shared__ unsigned char dsm_raw[];
+  // The swizzle acts on address bits 4 and 7: buffers start on 256 bytes.
+  unsigned char* dsm = dsm_raw + ((256 - (smem_u32(dsm_raw) & 255)) & 255);
   __shared__ __align__(128) uint4 wsm[kTaps * kC * 2];
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z = blockIdx.z;
-  load_halo(halo, a.x, a.D, a.H, a.W, z, y0, x0);
+  __shared__ uint64_t bar[2];
+  __shared__ int abort_flag;
+  const int tiles_x = (a.W + kTX - 1) / kTX, tiles_y = (a.H + kTY - 1) / kTY;
+  const int tiles_z = (a.D + kFZ - 1) / kFZ;
+  const long long n_tiles = (long long)tiles_x * tiles_y * tiles_z;
+  auto origin = [&](long long t, int& x0, int& y0, int& z0) {
+    x0 = (int)(t % tiles_x) * kTX;
+    y0 = (int)((t / tiles_x) % tiles_y) * kTY;
+    z0 = (int)(t / ((long long)tiles_x * tiles_y)) * kFZ;
+  };
+  auto issue = [&](int b, long long t) {
+    int x0, y0, z0;
+    origin(t, x0, y0, z0);
+    mbar_arrive_expect_tx(&bar[b], kFHalo);
+    tma_load_4d(dsm + b * kFHalo, &xmap, 0, x0 - 1, y0 - 1, z0 - 1, &bar[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    abort_flag = 0;
+  }
   for (int i = threadIdx.x; i < kTaps * kC * 2; i += blockDim.x)
     wsm[i] = reinterpret_cast<const uint4*>(a.w)[i];
   __syncthreads();
+  if (threadIdx.x == 0 && (long long)blockIdx.x < n_tiles) issue(0, blockIdx.x);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mat = lane >> 3, r = lane & 7;
-  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  const char* hb = reinterpret_cast<const char*>(halo);
-  const char* wb = reinterpret_cast<const char*>(wsm);
-  // A rows: voxel r + 8 (mat & 1), channel half (mat >> 1).
-  const int avox = r + 8 * (mat & 1), ahalf = mat >> 1;
-  // B rows: out channel r + 8 (mat >> 1), input-channel half (mat & 1).
-  const int bco = r + 8 * (mat >> 1), bhalf = mat & 1;
-#pragma unroll 3
-  for (int tap = 0; tap < kTaps; ++tap) {
-    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-    uint32_t af[4], bf[4];
-    const int hv = (dz * kHY + warp + dy) * kHX + dx + avox;
-    ldsm_x4(af, hb + hv * 32 + ahalf * 16);
-    ldsm_x4(bf, wb + (tap * kC + bco) * 32 + bhalf * 16);
-    mma16816(acc[0], af, bf[0], bf[1]);
-    mma16816(acc[1], af, bf[2], bf[3]);
+  // B fragments of every tap: rows out channel r + 8 (mat >> 1), input half (mat & 1).
+  uint32_t bw[kTaps][4];
+  {
+    const char* wb = reinterpret_cast<const char*>(wsm);
+    const int bco = r + 8 * (mat >> 1), bhalf = mat & 1;
+#pragma unroll
+    for (int tap = 0; tap < kTaps; ++tap) ldsm_x4(bw[tap], wb + (tap * kC + bco) * 32 + bhalf * 16);
   }
-  // Epilogue: thread holds voxels g, g + 8 and channels nt*8 + 2t, +1.
+  const int wy = 2 * (warp & 3), wz = 2 * (warp >> 2);
+  // A rows: voxel r + 8 (mat & 1) of the shifted halo row, channel half (mat >> 1).
+  const int avox = r + 8 * (mat & 1), ahalf = mat >> 1;
   const int g = lane >> 2, t = lane & 3;
-  const int y = y0 + warp;
-  if (y >= a.H) return;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int xx = x0 + g + 8 * h;
-    if (xx >= a.W) continue;
-    const long long vox = ((long long)z * a.H + y) * a.W + xx;
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const int co = nt * 8 + 2 * t;
-      float v0 = acc[nt][2 * h] + (a.bias ? a.bias[co] : 0.f);
-      float v1 = acc[nt][2 * h + 1] + (a.bias ? a.bias[co + 1] : 0.f);
-      if (a.relu) {
-        v0 = fmaxf(v0, 0.f);
-        v1 = fmaxf(v1, 0.f);
-      }
-      if (a.mask) {
-        if (!(bf2f(a.mask[vox * kC + co]) > 0.f)) v0 = 0.f;
-        if (!(bf2f(a.mask[vox * kC + co + 1]) > 0.f)) v1 = 0.f;
-      }
-      if (a.y32) *reinterpret_cast<float2*>(a.y32 + vox * kC + co) = make_float2(v0, v1);
-      if (a.y16)
-        *reinterpret_cast<uint32_t*>(a.y16 + vox * kC + co) =
-            (uint32_t)f2bf(v0) | ((uint32_t)f2bf(v1) << 16);
+  int it = 0;
+  bool issued_next = false;  // thread 0: a load into the other buffer is in flight
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    issued_next = threadIdx.x == 0 && tile + gridDim.x < n_tiles;
+    if (issued_next) issue(b ^ 1, tile + gridDim.x);
+    if (!mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), status)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) {
+      // Let the load still in flight land before the CTA exits (bounded).
+      if (issued_next) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), status);
+      return;
     }
+    const unsigned char* hb = dsm + b * kFHalo;
+    float acc[2][2][2][4];  // [oz][oy][n half][fragment]
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[i][j][n][e] = 0.f;
+#pragma unroll
+    for (int hz = 0; hz < 4; ++hz)
+#pragma unroll
+      for (int hy = 0; hy < 4; ++hy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          uint32_t af[4];
+          const int v = ((wz + hz) * kHY + wy + hy) * kHX + dx + avox;
+          ldsm_x4(af, hb + swz(v, ahalf) * 16);
+#pragma unroll
+          for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+            for (int oy = 0; oy < 2; ++oy) {
+              const int dz = hz - oz, dy = hy - oy;
+              if (dz < 0 || dz > 2 || dy < 0 || dy > 2) continue;
+              const int tap = (dz * 3 + dy) * 3 + dx;
+              mma16816(acc[oz][oy][0], af, bw[tap][0], bw[tap][1]);
+              mma16816(acc[oz][oy][1], af, bw[tap][2], bw[tap][3]);
+            }
+        }
+    int x0, y0, z0;
+    origin(tile, x0, y0, z0);
+    // Epilogue: the thread holds voxels g, g + 8 and channels n*8 + 2t, +1.
+#pragma unroll
+    for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy) {
+        const int z = z0 + wz + oz, y = y0 + wy + oy;
+        if (z >= a.D || y >= a.H) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int xx = x0 + g + 8 * h;
+          if (xx >= a.W) continue;
+          const long long vox = ((long long)z * a.H + y) * a.W + xx;
+#pragma unroll
+          for (int n = 0; n < 2; ++n) {
+            const int co = n * 8 + 2 * t;
+            float v0 = acc[oz][oy][n][2 * h] + (a.bias ? a.bias[co] : 0.f);
+            float v1 = acc[oz][oy][n][2 * h + 1] + (a.bias ? a.bias[co + 1] : 0.f);
+            if (a.relu) {
+              v0 = fmaxf(v0, 0.f);
+              v1 = fmaxf(v1, 0.f);
+            }
+            if (a.mask) {
+              if (!(bf2f(a.mask[vox * kC + co]) > 0.f)) v0 = 0.f;
+              if (!(bf2f(a.mask[vox * kC + co + 1]) > 0.f)) v1 = 0.f;
+            }
+            if (a.y32) *reinterpret_cast<float2*>(a.y32 + vox * kC + co) = make_float2(v0, v1);
+            if (a.y16)
+              *reinterpret_cast<uint32_t*>(a.y16 + vox * kC + co) =
+                  (uint32_t)f2bf(v0) | ((uint32_t)f2bf(v1) << 16);
+          }
+        }
+      }
+    __syncthreads();  // buffer b is free for the load issued next iteration
   }
 }
 
 // Weight gradient: per CTA partial sums over its tiles of
 // gw[tap][o][i] = sum_p gy[p][o] x[p + tap - 1][i] and gb[o] = sum_p gy[p][o].
-__global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a) {
-  __shared__ __align__(128) uint4 halo[kHZ * kHY * kHX * 2];
-  __shared__ __align__(128) uint4 gys[kTY * kTX * 2];
+// Persistent like the forward kernel: per 16 x 8 x 4 tile one TMA load
+// brings the 18 x 10 x 6 halo of x and one the 16 x 8 x 4 tile of gy (both
+// with the 32-byte swizzle) into a double buffer.  Warp w accumulates taps
+// w, w + 8, w + 16, w + 24; per output row the A fragment is gy^T (16 out
+// channels x 16 voxels) and the B fragment the shifted x row.  Warp 0 also
+// sums gy for the bias from its A fragments.
+constexpr int kGTile = kFZ * kTY * kTX * kC * 2;  // bytes of a gy tile
+static_assert(kGTile % 256 == 0, "gy tiles must stay 256-byte aligned");
+constexpr int kWStage = kFHalo + kGTile;
+
+__device__ __forceinline__ float2 bf2x2(uint32_t v) {
+  return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+}
+
+__global__ void __launch_bounds__(256, 2)
+    conv_wgrad_kernel(const __grid_constant__ CUtensorMap xmap,
+                      const __grid_constant__ CUtensorMap gmap, WgradArgs a, int* status) {
+  extern __shared__ unsigned char wsm_raw[];
+  unsigned char* dsm = wsm_raw + ((256 - (smem_u32(wsm_raw) & 255)) & 255);
+  __shared__ uint64_t bar[2];
+  __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mat = lane >> 3, r = lane & 7;
-  // Taps of this warp: warp, warp + 8, warp + 16, warp + 24 (< 27).
+  const int tiles_x = (a.W + kTX - 1) / kTX, tiles_y = (a.H + kTY - 1) / kTY;
+  const int tiles_z = (a.D + kFZ - 1) / kFZ;
+  const long long n_tiles = (long long)tiles_x * tiles_y * tiles_z;
+  auto issue = [&](int b, long long t) {
+    const int x0 = (int)(t % tiles_x) * kTX;
+    const int y0 = (int)((t / tiles_x) % tiles_y) * kTY;
+    const int z0 = (int)(t / ((long long)tiles_x * tiles_y)) * kFZ;
+    unsigned char* st = dsm + b * kWStage;
+    mbar_arrive_expect_tx(&bar[b], kWStage);
+    tma_load_4d(st, &xmap, 0, x0 - 1, y0 - 1, z0 - 1, &bar[b]);
+    tma_load_4d(st + kFHalo, &gmap, 0, x0, y0, z0, &bar[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (long long)blockIdx.x < n_tiles) issue(0, blockIdx.x);
   float acc[4][2][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -140,34 +265,32 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a) {
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-  float bacc = 0.f;
-  const int tiles_x = (a.W + kTX - 1) / kTX, tiles_y = (a.H + kTY - 1) / kTY;
-  const long long n_tiles = (long long)tiles_x * tiles_y * a.D;
-  const char* hb = reinterpret_cast<const char*>(halo);
-  const char* gb = reinterpret_cast<const char*>(gys);
-  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int tx = (int)(tile % tiles_x), ty = (int)((tile / tiles_x) % tiles_y);
-    const int z = (int)(tile / ((long long)tiles_x * tiles_y));
-    const int x0 = tx * kTX, y0 = ty * kTY;
+  float bsum[2] = {0.f, 0.f};  // warp 0: out channels g and g + 8
+  int it = 0;
+  bool issued_next = false;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    issued_next = threadIdx.x == 0 && tile + gridDim.x < n_tiles;
+    if (issued_next) issue(b ^ 1, tile + gridDim.x);
+    if (!mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), status)) abort_flag = 1;
     __syncthreads();
-    load_halo(halo, a.x, a.D, a.H, a.W, z, y0, x0);
-    for (int i = threadIdx.x; i < kTY * kTX * 2; i += blockDim.x) {
-      const int half = i & 1, v = i >> 1, vx = v % kTX, vy = v / kTX;
-      const int xx = x0 + vx, yy = y0 + vy;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (xx < a.W && yy < a.H)
-        val = reinterpret_cast<const uint4*>(a.gy + (((long long)z * a.H + yy) * a.W + xx) * kC)[half];
-      gys[i] = val;
+    if (abort_flag) {
+      if (issued_next) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), status);
+      return;
     }
-    __syncthreads();
-    if (threadIdx.x < kC) {
-      const uint16_t* g16 = reinterpret_cast<const uint16_t*>(gys);
-      for (int v = 0; v < kTY * kTX; ++v) bacc += bf2f(g16[v * kC + threadIdx.x]);
-    }
-    for (int row = 0; row < kTY; ++row) {  // k step: the 16 voxels of one row
+    const unsigned char* hb = dsm + b * kWStage;
+    const unsigned char* gb = hb + kFHalo;
+#pragma unroll 2
+    for (int row = 0; row < kFZ * kTY; ++row) {  // k step: the 16 voxels of one output row
+      const int oz = row / kTY, oy = row % kTY;
       uint32_t af[4];
       // A = gy^T: rows voxel r + 8 (mat >> 1), channel half (mat & 1), transposed.
-      ldsm_x4_t(af, gb + (row * kTX + r + 8 * (mat >> 1)) * 32 + (mat & 1) * 16);
+      ldsm_x4_t(af, gb + swz(row * kTX + r + 8 * (mat >> 1), mat & 1) * 16);
+      if (warp == 0) {
+        const float2 p0 = bf2x2(af[0]), p1 = bf2x2(af[1]), p2 = bf2x2(af[2]), p3 = bf2x2(af[3]);
+        bsum[0] += (p0.x + p0.y) + (p2.x + p2.y);
+        bsum[1] += (p1.x + p1.y) + (p3.x + p3.y);
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int tap = warp + 8 * i;
@@ -175,13 +298,14 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a) {
           const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
           uint32_t bf[4];
           // B = shifted x: rows voxel r + 8 (mat & 1), channel half (mat >> 1), transposed.
-          const int hv = (dz * kHY + row + dy) * kHX + dx + r + 8 * (mat & 1);
-          ldsm_x4_t(bf, hb + hv * 32 + (mat >> 1) * 16);
+          const int hv = ((oz + dz) * kHY + oy + dy) * kHX + dx + r + 8 * (mat & 1);
+          ldsm_x4_t(bf, hb + swz(hv, mat >> 1) * 16);
           mma16816(acc[i][0], af, bf[0], bf[1]);
           mma16816(acc[i][1], af, bf[2], bf[3]);
         }
       }
     }
+    __syncthreads();  // stage b is free for the load issued next iteration
   }
   // Partial sums: d0 = (o = g, i = nt*8 + 2t), d1 = (g, +1), d2/d3 rows g + 8.
   const int g = lane >> 2, t = lane & 3;
@@ -200,7 +324,17 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(WgradArgs a) {
       p[(g + 8) * kC + ci + 1] = acc[i][nt][3];
     }
   }
-  if (threadIdx.x < kC) part[kTaps * kC * kC + threadIdx.x] = bacc;
+  if (warp == 0) {
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      bsum[0] += __shfl_xor_sync(0xffffffffu, bsum[0], o);
+      bsum[1] += __shfl_xor_sync(0xffffffffu, bsum[1], o);
+    }
+    if (t == 0) {
+      part[kTaps * kC * kC + g] = bsum[0];
+      part[kTaps * kC * kC + g + 8] = bsum[1];
+    }
+  }
 }
 
 // Fixed-order sum of the per-CTA partials: gw [27][16][16], gb [16].
@@ -319,22 +453,58 @@ cudaError_t launch_features(long long N, const float* vel, const float* ph, cons
   return cudaGetLastError();
 }
 
-int wgrad_blocks() { return 152 * 4; }
+int wgrad_blocks() { return 152 * 2; }
 size_t wgrad_partial_floats() { return (size_t)wgrad_blocks() * (kTaps * kC * kC + kC); }
 int mse_blocks() { return 152 * 4; }
 
-cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
-  dim3 grid((a.W + kTX - 1) / kTX, (a.H + kTY - 1) / kTY, a.D);
-  conv_fwd_kernel<<<grid, 256, 0, s>>>(a);
+size_t conv_halo_box_bytes() { return kFHalo; }
+
+void conv_halo_box(unsigned (&box)[4]) {
+  box[0] = kC;
+  box[1] = kHX;
+  box[2] = kHY;
+  box[3] = kFHZ;
+}
+
+void conv_gy_box(unsigned (&box)[4]) {
+  box[0] = kC;
+  box[1] = kTX;
+  box[2] = kTY;
+  box[3] = kFZ;
+}
+
+cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& xmap, int* status, cudaStream_t s) {
+  const long long n_tiles = (long long)((a.W + kTX - 1) / kTX) * ((a.H + kTY - 1) / kTY) *
+                            ((a.D + kFZ - 1) / kFZ);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(conv_fwd_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kFHalo + 256);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int grid = (int)std::min<long long>(n_tiles, 152);
+  conv_fwd_kernel<<<grid, 256, 2 * kFHalo + 256, s>>>(xmap, a, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_wgrad(const WgradArgs& a, float* gw, float* gb, cudaStream_t s) {
-  conv_wgrad_kernel<<<wgrad_blocks(), 256, 0, s>>>(a);
+cudaError_t launch_wgrad(const WgradArgs& a, const CUtensorMap& xmap, const CUtensorMap& gmap,
+                         int* status, float* gw, float* gb, cudaStream_t s) {
+  const long long n_tiles = (long long)((a.W + kTX - 1) / kTX) * ((a.H + kTY - 1) / kTY) *
+                            ((a.D + kFZ - 1) / kFZ);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(conv_wgrad_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * kWStage + 256);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int grid = (int)std::min<long long>(n_tiles, wgrad_blocks());
+  conv_wgrad_kernel<<<grid, 256, 2 * kWStage + 256, s>>>(xmap, gmap, a, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  wgrad_reduce_kernel<<<(kTaps * kC * kC + kC + 255) / 256, 256, 0, s>>>(a.partial, wgrad_blocks(),
-                                                                         gw, gb);
+  wgrad_reduce_kernel<<<(kTaps * kC * kC + kC + 255) / 256, 256, 0, s>>>(a.partial, grid, gw, gb);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Launch interface of the network kernels (internal).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,8 +28,17 @@ struct WgradArgs {
 int wgrad_blocks();
 size_t wgrad_partial_floats();
 int mse_blocks();
-cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s);
-cudaError_t launch_wgrad(const WgradArgs& a, float* gw, float* gb, cudaStream_t s);
+// Input halo box of the forward kernel's TMA map over x viewed as
+// [D][H][W][16] BF16 (dims innermost first: channels, x, y, z), 32-byte
+// swizzle, zero fill outside.
+size_t conv_halo_box_bytes();
+void conv_halo_box(unsigned (&box)[4]);
+cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& xmap, int* status, cudaStream_t s);
+// gy tile box of the weight-gradient kernel's TMA map over gy (same layout
+// and swizzle as x; no halo).
+void conv_gy_box(unsigned (&box)[4]);
+cudaError_t launch_wgrad(const WgradArgs& a, const CUtensorMap& xmap, const CUtensorMap& gmap,
+                         int* status, float* gw, float* gb, cudaStream_t s);
 cudaError_t launch_pack(const float* w, uint16_t* fwd, uint16_t* bwd, cudaStream_t s);
 cudaError_t launch_mse(long long N, const float* out, const float* tgt, const float* mask,
                        double n_mask, uint16_t* gy, double* partial, double* loss, cudaStream_t s);

@@ -5,109 +5,173 @@
 // over the retained frequency bins k of an N_f = 2 nt zero-padded DFT.
 #include "gn.h"
 
+#include <algorithm>
 #include <cstdint>
+
+#include "common.cuh"
 
 namespace mamute {
 
 namespace {
 
-constexpr int kPts = 128;   // points per CTA
-constexpr int kPP = 4;      // consecutive points per thread
-constexpr int kChunk = 16;  // frequency bins per thread
-constexpr int kGroups = kPts / kPP;  // point groups: one warp
+constexpr int kPts = 128;     // points per block
+constexpr int kPP = 4;        // consecutive points per thread
+constexpr int kChunk = 8;     // frequency bins per warp
+constexpr int kMaxWarps = 16;
 
-// Twiddles W[t][k] = exp(-2 pi i bins[k] (n0 + t) / nf) for one time block.
-__global__ void twiddle_kernel(int T, int n0, int nf, const int* __restrict__ bins, int nb,
+// Twiddles W[t][k] = exp(-2 pi i bins[k] (n0 + t) / nf) for one time block,
+// rows padded to nbp bins with zeros.
+__global__ void twiddle_kernel(int T, int n0, int nf, const int* __restrict__ bins, int nb, int nbp,
                                float2* __restrict__ W) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= T * nb) return;
-  const int t = i / nb, k = i % nb;
+  if (i >= T * nbp) return;
+  const int t = i / nbp, k = i % nbp;
+  if (k >= nb) {
+    W[i] = make_float2(0.0f, 0.0f);
+    return;
+  }
   const long long m = ((long long)bins[k] * (long long)(n0 + t)) % nf;
   float sn, cs;
   sincospif(2.0f * (float)m / (float)nf, &sn, &cs);
   W[i] = make_float2(cs, -sn);
 }
 
-// acc[k][x] += sum_t V[t][x] W[t][k] for kPts points per CTA.  Warp c owns
-// bins [c kChunk, (c+1) kChunk); lane g owns points 4g..4g+3 of the CTA, so
-// per time sample a thread does 4 x 16 complex MACs from one 16-byte read of
-// V and eight broadcast 16-byte reads of W (FP32 FMA bound, not LSU bound).
-// VEC: N is a multiple of 4, so the accumulator rows take 16-byte accesses.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// acc[k][x] += sum_t V[t][x] W[t][k], persistent over blocks of kPts points.
+// The T x nbp twiddles are loaded once per CTA; the T x kPts samples of the
+// next block arrive by bulk copies (one per sample row) into the other half
+// of a double buffer while this block is accumulated.  Warp c owns bins
+// [c kChunk, (c+1) kChunk) and lane g points 4g..4g+3, so per sample a
+// thread does 4 x 8 complex MACs from one 16-byte read of V and four
+// broadcast 16-byte reads of W.  VEC (N a multiple of 4): bulk copies and
+// 16-byte accumulator accesses; otherwise plain loads.
 template <bool VEC>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kMaxWarps * 32, 1)
     dft_kernel(const float* __restrict__ V, long long N, int T, int nb,
-               const float2* __restrict__ W, float* __restrict__ re, float* __restrict__ im) {
+               const float2* __restrict__ W, float* __restrict__ re, float* __restrict__ im,
+               int* status) {
   extern __shared__ float4 sm4[];
-  float* Vs = reinterpret_cast<float*>(sm4);                // [T][kPts]
-  const int nbp = (blockDim.x / 32) * kChunk;             // bins padded to the warps
-  float2* Ws = reinterpret_cast<float2*>(Vs + T * kPts);  // [T][nbp], zero beyond nb
-  const long long x0 = (long long)blockIdx.x * kPts;
-  for (int i = threadIdx.x; i < T * nbp; i += blockDim.x) {
-    const int t = i / nbp, k = i % nbp;
-    Ws[i] = k < nb ? W[t * nb + k] : make_float2(0.0f, 0.0f);
-  }
-  for (int i = threadIdx.x; i < T * kPts; i += blockDim.x) {
-    const int t = i / kPts, p = i % kPts;
-    const long long x = x0 + p;
-    Vs[i] = x < N ? V[(long long)t * N + x] : 0.0f;
+  __shared__ uint64_t bar[3];  // [0] twiddles, [1 + b] samples of buffer b
+  __shared__ int abort_flag;
+  const int nbp = (blockDim.x / 32) * kChunk;
+  float2* Ws = reinterpret_cast<float2*>(sm4);   // [T][nbp]
+  float* Vs = reinterpret_cast<float*>(Ws + T * nbp);  // [2][T][kPts]
+  const long long nblk = (N + kPts - 1) / kPts;
+  auto issue = [&](int b, long long blk) {
+    const long long x0 = blk * kPts;
+    const uint32_t bytes = (uint32_t)(min((long long)kPts, N - x0) * 4);
+    mbar_arrive_expect_tx(&bar[1 + b], (uint32_t)T * bytes);
+    for (int t = 0; t < T; ++t)
+      bulk_load(Vs + ((size_t)b * T + t) * kPts, V + (long long)t * N + x0, bytes, &bar[1 + b]);
+  };
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&bar[i], 1);
+    fence_barrier_init();
+    abort_flag = 0;
   }
   __syncthreads();
+  bool issued_next = false;  // thread 0: a sample copy into the other buffer is in flight
+  if (VEC) {
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(&bar[0], (uint32_t)(T * nbp * 8));
+      bulk_load(Ws, W, (uint32_t)(T * nbp * 8), &bar[0]);
+      issue(0, blockIdx.x);
+    }
+    if (!mbar_wait(&bar[0], 0, status)) abort_flag = 1;
+  } else {
+    for (int i = threadIdx.x; i < T * nbp; i += blockDim.x) Ws[i] = W[i];
+  }
   const int g = threadIdx.x & 31, c = threadIdx.x >> 5;
-  const long long xb = x0 + kPP * g;
-  if (xb >= N) return;
-  float ar[kPP][kChunk], ai[kPP][kChunk];
-#pragma unroll
-  for (int j = 0; j < kChunk; ++j) {
-    const int k = c * kChunk + j;
-    if (VEC && k < nb) {  // xb + 3 < N as N is a multiple of 4
-      const float4 r = *reinterpret_cast<const float4*>(re + (long long)k * N + xb);
-      const float4 m = *reinterpret_cast<const float4*>(im + (long long)k * N + xb);
-      ar[0][j] = r.x; ar[1][j] = r.y; ar[2][j] = r.z; ar[3][j] = r.w;
-      ai[0][j] = m.x; ai[1][j] = m.y; ai[2][j] = m.z; ai[3][j] = m.w;
-    } else {
-#pragma unroll
-      for (int q = 0; q < kPP; ++q) {
-        const bool ok = k < nb && xb + q < N;
-        ar[q][j] = ok ? re[(long long)k * N + xb + q] : 0.0f;
-        ai[q][j] = ok ? im[(long long)k * N + xb + q] : 0.0f;
-      }
-    }
-  }
-#pragma unroll 2
-  for (int t = 0; t < T; ++t) {
-    const float4 v = *reinterpret_cast<const float4*>(Vs + t * kPts + kPP * g);
-    const float vq[kPP] = {v.x, v.y, v.z, v.w};
-    const float4* w4 = reinterpret_cast<const float4*>(Ws + t * nbp + c * kChunk);
-#pragma unroll
-    for (int jj = 0; jj < kChunk / 2; ++jj) {
-      const float4 w = w4[jj];  // bins 2jj and 2jj + 1
-#pragma unroll
-      for (int q = 0; q < kPP; ++q) {
-        ar[q][2 * jj] = fmaf(vq[q], w.x, ar[q][2 * jj]);
-        ai[q][2 * jj] = fmaf(vq[q], w.y, ai[q][2 * jj]);
-        ar[q][2 * jj + 1] = fmaf(vq[q], w.z, ar[q][2 * jj + 1]);
-        ai[q][2 * jj + 1] = fmaf(vq[q], w.w, ai[q][2 * jj + 1]);
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kChunk; ++j) {
-    const int k = c * kChunk + j;
-    if (k >= nb) continue;
+  int it = 0;
+  for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x, ++it) {
+    const int b = it & 1;
+    float* Vb = Vs + (size_t)b * T * kPts;
+    const long long x0 = blk * kPts;
     if (VEC) {
-      *reinterpret_cast<float4*>(re + (long long)k * N + xb) =
-          make_float4(ar[0][j], ar[1][j], ar[2][j], ar[3][j]);
-      *reinterpret_cast<float4*>(im + (long long)k * N + xb) =
-          make_float4(ai[0][j], ai[1][j], ai[2][j], ai[3][j]);
+      issued_next = threadIdx.x == 0 && blk + gridDim.x < nblk;
+      if (issued_next) issue(b ^ 1, blk + gridDim.x);
     } else {
+      for (int i = threadIdx.x; i < T * kPts; i += blockDim.x) {
+        const int t = i / kPts, p = i % kPts;
+        Vb[i] = x0 + p < N ? V[(long long)t * N + x0 + p] : 0.0f;
+      }
+    }
+    const long long xb = x0 + kPP * g;
+    const bool live = xb < N;
+    float ar[kPP][kChunk], ai[kPP][kChunk];
 #pragma unroll
-      for (int q = 0; q < kPP; ++q) {
-        if (xb + q < N) {
-          re[(long long)k * N + xb + q] = ar[q][j];
-          im[(long long)k * N + xb + q] = ai[q][j];
+    for (int j = 0; j < kChunk; ++j) {
+      const int k = c * kChunk + j;
+      if (VEC) {
+        float4 rv = make_float4(0.f, 0.f, 0.f, 0.f), mv = rv;
+        if (live && k < nb) {  // xb + 3 < N as N is a multiple of 4
+          rv = *reinterpret_cast<const float4*>(re + (long long)k * N + xb);
+          mv = *reinterpret_cast<const float4*>(im + (long long)k * N + xb);
+        }
+        ar[0][j] = rv.x; ar[1][j] = rv.y; ar[2][j] = rv.z; ar[3][j] = rv.w;
+        ai[0][j] = mv.x; ai[1][j] = mv.y; ai[2][j] = mv.z; ai[3][j] = mv.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < kPP; ++q) {
+          const bool ok = k < nb && xb + q < N;
+          ar[q][j] = ok ? re[(long long)k * N + xb + q] : 0.0f;
+          ai[q][j] = ok ? im[(long long)k * N + xb + q] : 0.0f;
         }
       }
     }
+    if (VEC && !mbar_wait(&bar[1 + b], (uint32_t)((it >> 1) & 1), status)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) {
+      if (issued_next) mbar_wait(&bar[1 + (b ^ 1)], (uint32_t)(((it + 1) >> 1) & 1), status);
+      return;
+    }
+#pragma unroll 2
+    for (int t = 0; t < T; ++t) {
+      const float4 v = *reinterpret_cast<const float4*>(Vb + t * kPts + kPP * g);
+      const float vq[kPP] = {v.x, v.y, v.z, v.w};
+      const float4* w4 = reinterpret_cast<const float4*>(Ws + t * nbp + c * kChunk);
+#pragma unroll
+      for (int jj = 0; jj < kChunk / 2; ++jj) {
+        const float4 w = w4[jj];  // bins 2jj and 2jj + 1
+#pragma unroll
+        for (int q = 0; q < kPP; ++q) {
+          ar[q][2 * jj] = fmaf(vq[q], w.x, ar[q][2 * jj]);
+          ai[q][2 * jj] = fmaf(vq[q], w.y, ai[q][2 * jj]);
+          ar[q][2 * jj + 1] = fmaf(vq[q], w.z, ar[q][2 * jj + 1]);
+          ai[q][2 * jj + 1] = fmaf(vq[q], w.w, ai[q][2 * jj + 1]);
+        }
+      }
+    }
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        const int k = c * kChunk + j;
+        if (k >= nb) continue;
+        if (VEC) {
+          *reinterpret_cast<float4*>(re + (long long)k * N + xb) =
+              make_float4(ar[0][j], ar[1][j], ar[2][j], ar[3][j]);
+          *reinterpret_cast<float4*>(im + (long long)k * N + xb) =
+              make_float4(ai[0][j], ai[1][j], ai[2][j], ai[3][j]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < kPP; ++q) {
+            if (xb + q < N) {
+              re[(long long)k * N + xb + q] = ar[q][j];
+              im[(long long)k * N + xb + q] = ai[q][j];
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // buffer b is free for the copy issued next iteration
   }
 }
 
@@ -157,22 +221,25 @@ int blocks_for(long long n) {
 
 }  // namespace
 
+int dft_padded_bins(int nb) { return ((nb + kChunk - 1) / kChunk) * kChunk; }
+
 size_t dft_smem_bytes(int T, int nb) {
-  const int nbp = ((nb + kChunk - 1) / kChunk) * kChunk;
-  return sizeof(float) * T * kPts + sizeof(float2) * T * nbp;
+  return sizeof(float2) * T * dft_padded_bins(nb) + sizeof(float) * 2 * T * kPts;
 }
 
-int dft_max_bins() { return (256 / 32) * kChunk; }
+int dft_max_bins() { return kMaxWarps * kChunk; }
 
 cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const int* bins, int nb,
-                       float2* W, float* re, float* im, cudaStream_t s) {
-  if (T <= 0) return cudaSuccess;
+                       float2* W, float* re, float* im, int* status, cudaStream_t s) {
+  if (T <= 0 || N <= 0) return cudaSuccess;
   if (nb < 1 || nb > dft_max_bins()) return cudaErrorInvalidValue;
-  twiddle_kernel<<<(T * nb + 255) / 256, 256, 0, s>>>(T, n0, nf, bins, nb, W);
+  const int nbp = dft_padded_bins(nb);
+  twiddle_kernel<<<(T * nbp + 255) / 256, 256, 0, s>>>(T, n0, nf, bins, nb, nbp, W);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t sm = dft_smem_bytes(T, nb);
-  const bool vec = (N % 4) == 0 && ((uintptr_t)re % 16) == 0 && ((uintptr_t)im % 16) == 0;
+  const bool vec = (N % 4) == 0 && ((uintptr_t)V % 16) == 0 && ((uintptr_t)W % 16) == 0 &&
+                   ((uintptr_t)re % 16) == 0 && ((uintptr_t)im % 16) == 0;
   static size_t attr[2] = {0, 0};
   if (sm > attr[vec]) {
     e = vec ? cudaFuncSetAttribute(dft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
@@ -180,12 +247,17 @@ cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const
     if (e != cudaSuccess) return e;
     attr[vec] = sm;
   }
-  const int warps = (nb + kChunk - 1) / kChunk;
-  const unsigned grid = (unsigned)((N + kPts - 1) / kPts);
+  const int threads = 32 * (nbp / kChunk);
+  int per_sm = 1;
+  e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_kernel<true>, threads, sm)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_kernel<false>, threads, sm);
+  if (e != cudaSuccess) return e;
+  const long long nblk = (N + kPts - 1) / kPts;
+  const unsigned grid = (unsigned)std::min<long long>(nblk, 152LL * std::max(per_sm, 1));
   if (vec)
-    dft_kernel<true><<<grid, 32 * warps, sm, s>>>(V, N, T, nb, W, re, im);
+    dft_kernel<true><<<grid, threads, sm, s>>>(V, N, T, nb, W, re, im, status);
   else
-    dft_kernel<false><<<grid, 32 * warps, sm, s>>>(V, N, T, nb, W, re, im);
+    dft_kernel<false><<<grid, threads, sm, s>>>(V, N, T, nb, W, re, im, status);
   return cudaGetLastError();
 }
 

@@ -8,9 +8,9 @@ namespace mamute {
 size_t dft_smem_bytes(int T, int nb);
 int dft_max_bins();
 // acc (re, im)[nb][N] += sum_{t<T} V[t][N] exp(-2 pi i bins[k] (n0 + t) / nf); W is
-// scratch for T * nb twiddles.
+// scratch for T * dft_max_bins() twiddles; status collects bounded-wait timeouts.
 cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const int* bins, int nb,
-                       float2* W, float* re, float* im, cudaStream_t s);
+                       float2* W, float* re, float* im, int* status, cudaStream_t s);
 // pw[k][x] += sum over the nv windows of |acc[k][v N + x]|^2, then acc = 0.
 cudaError_t launch_power(int nb, long long N, int nv, float* re, float* im, float* pw,
                          cudaStream_t s);
