@@ -343,7 +343,15 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int n_par
   const int n = kTaps * kC * kC + kC;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int p = 0; p < n_parts; ++p) s += partial[(long long)p * n + i];
+    int p = 0;
+    for (; p + 8 <= n_parts; p += 8) {  // 8 loads in flight, summed in order
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = partial[(long long)(p + j) * n + i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s += v[j];
+    }
+    for (; p < n_parts; ++p) s += partial[(long long)p * n + i];
     if (i < kTaps * kC * kC) gw[i] = (float)s;
     else gb[i - kTaps * kC * kC] = (float)s;
   }
@@ -504,7 +512,7 @@ cudaError_t launch_wgrad(const WgradArgs& a, const CUtensorMap& xmap, const CUte
   conv_wgrad_kernel<<<grid, 256, 2 * kWStage + 256, s>>>(xmap, gmap, a, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  wgrad_reduce_kernel<<<(kTaps * kC * kC + kC + 255) / 256, 256, 0, s>>>(a.partial, grid, gw, gb);
+  wgrad_reduce_kernel<<<(kTaps * kC * kC + kC + 63) / 64, 64, 0, s>>>(a.partial, grid, gw, gb);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,9 @@ Preconditioners:
              (velocity, P); a learned step is accepted only if Armijo holds
              within `learned_backtracks` backtracks, otherwise the iteration
              falls back to the 'pseudo' step.
+  'exact'    h = H, the exact Gauss-Newton diagonal of the current model
+             (mamute_gn_diagonal; what the network approximates, at the cost
+             of 2 + n_rec / n_src propagations per shot).
 """
 from __future__ import annotations
 
@@ -126,6 +129,13 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
             return np.ones_like(x)
         if kind == "pseudo":
             return _diag(ph.cpu().numpy())
+        if kind == "exact":
+            vt = torch.from_numpy(x.reshape(shape).astype(np.float32)).to(prob.dev)
+            hd = torch.empty_like(vt)
+            w = prob.w
+            prob.ctx.gn_diagonal(prob.grid, vt, None, w.src_xyz, w.wavelet, w.rec_offset,
+                                 w.rec_xyz, hd)
+            return _diag(hd.cpu().numpy())
         vt = torch.from_numpy(x.reshape(shape).astype(np.float32)).to(prob.dev)
         x16, _, _ = net.features(vt, ph)
         out = net.forward(x16).cpu().numpy().astype(np.float64)
@@ -151,10 +161,11 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
         kinds = ["learned", "pseudo"] if precond == "learned" else [precond]
         accepted = None
         for kind in kinds:
-            d = two_loop(g, pairs, diag_for(kind, x, ph))
+            dg = diag_for(kind, x, ph)
+            d = two_loop(g, pairs, dg)
             if np.dot(d, g) >= 0:  # not a descent direction: restart the memory
                 pairs = []
-                d = two_loop(g, pairs, diag_for(kind, x, ph))
+                d = two_loop(g, pairs, dg)
             alpha = first_step / max(np.abs(d).max(), 1e-30) if not pairs else 1.0
             nb = learned_backtracks if (kind == "learned") else max_backtracks
             xn, Jn = line_search(d, J, g, x, nb, alpha, expand=not pairs)
