@@ -163,7 +163,9 @@ int mamute_adjoint(mamute_ctx* ctx, const mamute_grid* grid, const float* vel, c
 
 /* As mamute_model and mamute_gradient, but vel, rho, seis, d_obs, grad and
  * opts->phess are HOST pointers; the call stages them through context
- * buffers (host->device before, device->host after). */
+ * buffers (host->device before, device->host after).  mamute_model_host
+ * copies the seismograms to seis in 8 time segments while the later
+ * segments propagate (page-locked seis makes the copies asynchronous). */
 int mamute_model_host(mamute_ctx* ctx, const mamute_grid* grid, const float* vel,
                       const float* rho, int n_src, const float* src_xyz, const float* wavelet,
                       const int* rec_offset, const float* rec_xyz, const mamute_opts* opts,
@@ -201,8 +203,9 @@ int mamute_gn_diagonal(mamute_ctx* ctx, const mamute_grid* grid, const float* ve
  * padded); weights are FP32 masters [27 taps][16 out][16 in] with taps in
  * (dz, dy, dx) order, packed to BF16 for the products; products are BF16 x
  * BF16 with FP32 accumulation on the tensor cores.  Every call synchronises
- * the context's stream.  Errors: EINVAL for bad sizes or NULL pointers,
- * ECUDA, ENOMEM. */
+ * the context's stream.  Errors: EINVAL for bad sizes, NULL pointers or
+ * activation pointers that are not 16-byte aligned, ECUDA, ENOMEM, ETIMEOUT
+ * (a bounded device-side wait ran out). */
 
 /* y = act(conv(x, w) + bias) with zero padding; act = ReLU if relu != 0;
  * if mask is given, outputs where mask <= 0 are zeroed (ReLU derivative of

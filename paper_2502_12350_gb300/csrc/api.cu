@@ -96,6 +96,8 @@ struct mamute_ctx {
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned long long> graph_key;
   cudaStream_t capture = nullptr;  // private stream the time loop is captured on
+  cudaStream_t copy = nullptr;     // seismogram transposes and copies to the host
+  std::vector<cudaEvent_t> seg_ev;  // ends of the time-loop segments
   std::vector<ShotMaps> hmaps;     // host copy of the uploaded shot maps
 };
 
@@ -669,9 +671,12 @@ int check_common(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     if (rc_ != MAMUTE_OK) return rc_; \
   } while (0)
 
+// host_seis (host, may be NULL): the seismograms also go to this host array,
+// segment by segment while later segments of the time loop run.
 int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* rho,
               int n_src, const float* src_xyz, const float* wavelet, const int* rec_offset,
-              const float* rec_xyz, const mamute_opts* opts, float* seis) {
+              const float* rec_xyz, const mamute_opts* opts, float* seis,
+              float* host_seis = nullptr) {
   TRY(check_common(ctx, g, vel, wavelet));
   Plan P;
   TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz,
@@ -690,7 +695,8 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   // The time loop is captured into a CUDA graph and replayed while the plan,
   // the buffers and the wavelet stay the same (MAMUTE_GRAPHS=0 disables).
   std::vector<unsigned long long> key;
-  const bool use_graph = env_int("MAMUTE_GRAPHS", 1) != 0 && P.nt >= 8;
+  const bool stream_out = host_seis != nullptr && P.ncol > 0;
+  const bool use_graph = env_int("MAMUTE_GRAPHS", 1) != 0 && P.nt >= 8 && !stream_out;
   if (use_graph) {
     auto push = [&](const void* p) { key.push_back((unsigned long long)(uintptr_t)p); };
     key.push_back((unsigned long long)P.nt);
@@ -716,7 +722,35 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
     }
     return MAMUTE_OK;
   };
-  if (!use_graph) {
+  if (stream_out) {
+    // In 8 segments: after each, the copy stream transposes that segment's
+    // samples and copies them to the host while the next segment runs.
+    if (!ctx->copy) CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    const int nseg = std::min(P.nt, 8);
+    while ((int)ctx->seg_ev.size() < nseg + 1) {
+      cudaEvent_t ev = nullptr;
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      ctx->seg_ev.push_back(ev);
+    }
+    int t0 = 0;
+    for (int k = 0; k < nseg; ++k) {
+      const int t1 = (int)((long long)P.nt * (k + 1) / nseg);
+      for (int n = t0; n < t1; ++n) {
+        StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
+        CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+      }
+      CK(cudaEventRecord(ctx->seg_ev[k], ctx->stream));
+      CK(cudaStreamWaitEvent(ctx->copy, ctx->seg_ev[k], 0));
+      CK(aux_count(ctx, launch_data_out_range((const float*)ctx->dint.p, (const int*)ctx->colmap.p,
+                                              t0, t1, P.nt, P.ncol, seis, ctx->copy)));
+      CK(cudaMemcpy2DAsync(host_seis + t0, (size_t)P.nt * 4, seis + t0, (size_t)P.nt * 4,
+                           (size_t)(t1 - t0) * 4, (size_t)P.ncol, cudaMemcpyDeviceToHost,
+                           ctx->copy));
+      t0 = t1;
+    }
+    CK(cudaEventRecord(ctx->seg_ev[nseg], ctx->copy));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->seg_ev[nseg], 0));
+  } else if (!use_graph) {
     TRY(launch_all());
   } else {
     if (!ctx->graph || ctx->graph_key != key) {
@@ -760,8 +794,9 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
     ctx->step_launches = P.nt;
     ctx->launches += P.nt;
   }
-  CK(aux_count(ctx, launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol, seis,
-                     ctx->stream)));
+  if (!stream_out)
+    CK(aux_count(ctx, launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt,
+                                      P.ncol, seis, ctx->stream)));
   if (ph) {
     FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
                     P.nx, P.ny, P.nz, P.b, P.dt, 1, 0, opts->phess};
@@ -1335,6 +1370,8 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  if (ctx->copy) cudaStreamDestroy(ctx->copy);
+  for (cudaEvent_t ev : ctx->seg_ev) cudaEventDestroy(ev);
   delete ctx;
 }
 
@@ -1379,9 +1416,10 @@ int mamute_model_host(mamute_ctx* ctx, const mamute_grid* g, const float* vel, c
     CK(ensure(ctx->hphess, nm));
     o.phess = (float*)ctx->hphess.p;
   }
+  if (ns && !seis) return fail(ctx, MAMUTE_EINVAL, "seis is NULL");
   TRY(run_model(ctx, g, (const float*)ctx->hvel.p, rho ? (const float*)ctx->hrho.p : nullptr, n_src,
-                src_xyz, wavelet, rec_offset, rec_xyz, opts ? &o : nullptr, (float*)ctx->hseis.p));
-  if (seis && ns) CK(cudaMemcpyAsync(seis, ctx->hseis.p, ns, cudaMemcpyDeviceToHost, ctx->stream));
+                src_xyz, wavelet, rec_offset, rec_xyz, opts ? &o : nullptr, (float*)ctx->hseis.p,
+                seis));
   if (opts && opts->phess)
     CK(cudaMemcpyAsync(opts->phess, ctx->hphess.p, nm, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1453,6 +1491,20 @@ static CUresult encode_act(mamute_ctx* ctx, CUtensorMap* m, const void* p, int D
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
+// TMA map over 8 channels (16 bytes) of every voxel of a [D][H][W][16] BF16
+// activation starting at p (channel 0 or 8): innermost first (8 channels,
+// x, y, z), no swizzle, zero fill outside.
+static CUresult encode_half(mamute_ctx* ctx, CUtensorMap* m, const void* p, int D, int H, int W,
+                            const unsigned (&box)[4]) {
+  cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
+  cuuint64_t strides[3] = {32, (cuuint64_t)W * 32, (cuuint64_t)W * H * 32};
+  cuuint32_t cbox[4] = {box[0], box[1], box[2], box[3]};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return ctx->encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(p), dims, strides,
+                     cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
 // As nn_end, for kernels with bounded device-side waits.
 static int nn_end_status(mamute_ctx* ctx) {
   int st = 0;
@@ -1471,13 +1523,15 @@ int mamute_conv3d(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
   if ((uintptr_t)x % 16)
     return fail(ctx, MAMUTE_EINVAL, "conv3d: x must be 16-byte aligned");
   ConvArgs a{x, w, bias, relu, mask, y32, y16, D, H, W};
-  CUtensorMap xmap;
+  // Two maps over x, one per 16-byte channel half, so the halo lands as
+  // [half][row][x][8 channels] (the tensor cores' K-major layout).
+  CUtensorMap mlo, mhi;
   unsigned box[4];
-  conv_halo_box(box);
-  if (encode_act(ctx, &xmap, x, D, H, W, box))
+  conv_halo_box(D, H, W, box);
+  if (encode_half(ctx, &mlo, x, D, H, W, box) || encode_half(ctx, &mhi, x + 8, D, H, W, box))
     return fail(ctx, MAMUTE_ECUDA, "conv3d: cuTensorMapEncodeTiled failed");
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
-  CK(launch_conv(a, xmap, ctx->status, ctx->stream));
+  CK(launch_conv(a, mlo, mhi, ctx->status, ctx->stream));
   return nn_end_status(ctx);
 }
 
@@ -1492,7 +1546,7 @@ int mamute_conv3d_wgrad(mamute_ctx* ctx, int D, int H, int W, const unsigned sho
   WgradArgs a{x, gy, (float*)ctx->nnPartial.p, D, H, W};
   CUtensorMap xmap, gmap;
   unsigned hbox[4], gbox[4];
-  conv_halo_box(hbox);
+  conv_wgrad_halo_box(hbox);
   conv_gy_box(gbox);
   if (encode_act(ctx, &xmap, x, D, H, W, hbox) || encode_act(ctx, &gmap, gy, D, H, W, gbox))
     return fail(ctx, MAMUTE_ECUDA, "conv3d_wgrad: cuTensorMapEncodeTiled failed");

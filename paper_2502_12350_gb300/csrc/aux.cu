@@ -91,7 +91,7 @@ __global__ void geometry_kernel(GeomArgs a) {
 
 // seis[colmap[c]][n] = d_int[n][c] (32x32 tiles through shared memory).
 __global__ void data_out_kernel(const float* __restrict__ d_int, const int* __restrict__ colmap,
-                                int nt, int ncol, float* __restrict__ seis) {
+                                int nt, int ncol, long long pitch, float* __restrict__ seis) {
   __shared__ float tile[32][33];
   const int c0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -101,7 +101,7 @@ __global__ void data_out_kernel(const float* __restrict__ d_int, const int* __re
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int c = c0 + r, n = n0 + threadIdx.x;
-    if (c < ncol && n < nt) seis[(long long)colmap[c] * nt + n] = tile[threadIdx.x][r];
+    if (c < ncol && n < nt) seis[(long long)colmap[c] * pitch + n] = tile[threadIdx.x][r];
   }
 }
 
@@ -211,7 +211,16 @@ cudaError_t launch_data_out(const float* d_int, const int* colmap, int nt, int n
                             cudaStream_t s) {
   if (ncol == 0) return cudaSuccess;
   dim3 g((ncol + 31) / 32, (nt + 31) / 32), b(32, 8);
-  data_out_kernel<<<g, b, 0, s>>>(d_int, colmap, nt, ncol, seis);
+  data_out_kernel<<<g, b, 0, s>>>(d_int, colmap, nt, ncol, nt, seis);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_data_out_range(const float* d_int, const int* colmap, int n0, int n1, int nt,
+                                  int ncol, float* seis, cudaStream_t s) {
+  if (ncol == 0 || n1 <= n0) return cudaSuccess;
+  dim3 g((ncol + 31) / 32, (n1 - n0 + 31) / 32), b(32, 8);
+  data_out_kernel<<<g, b, 0, s>>>(d_int + (long long)n0 * ncol, colmap, n1 - n0, ncol, nt,
+                                  seis + n0);
   return cudaGetLastError();
 }
 

@@ -47,6 +47,9 @@ cudaError_t launch_max(const float* v, long long n, unsigned int* out, cudaStrea
 cudaError_t launch_geometry(const GeomArgs& a, cudaStream_t s);
 cudaError_t launch_data_out(const float* d_int, const int* colmap, int nt, int ncol, float* seis,
                             cudaStream_t s);
+// Samples [n0, n1) of the same transpose into seis rows of length nt.
+cudaError_t launch_data_out_range(const float* d_int, const int* colmap, int n0, int n1, int nt,
+                                  int ncol, float* seis, cudaStream_t s);
 int data_in_blocks(int nt, int ncol);
 cudaError_t launch_data_in(const float* src, const int* colmap, int nt, int ncol,
                            const float* d_int, float sign, float* r_int, double* partial,

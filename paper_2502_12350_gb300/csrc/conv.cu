@@ -1,13 +1,11 @@
 // 3x3x3 'same' convolutions of the preconditioner network, BF16 in, FP32
-// accumulate, on the tensor cores (mma.sync m16n8k16), with the loss and
-// optimizer kernels that train it.
+// accumulate, with the loss and optimizer kernels that train it.  Forward
+// and input-gradient convolutions run on tcgen05 (conv_tc.cuh); the weight
+// gradient, a reduction over voxels, on mma.sync m16n8k16.
 //
 // Activations are channels-last [D][H][W][16] BF16 (fewer channels are
 // zero-padded to 16); weights are [27 taps][16 out][16 in] BF16 for the
 // forward product, with a flipped, transposed copy for the input gradient.
-// A CTA owns a 16 (x) x 8 (y) tile of one z plane; each warp one row of 16
-// voxels.  Per tap the 16 voxels x 16 input channels A fragment and the
-// 16 x 16 weight B fragments come from shared memory through ldmatrix.
 #include "conv.h"
 
 #include <algorithm>
@@ -53,32 +51,10 @@ __device__ __forceinline__ uint16_t f2bf(float f) {  // round to nearest even
   return (uint16_t)(u >> 16);
 }
 
-// Loads the (3, kHY, kHX) x 16-channel halo tile around (z, y0 - 1, x0 - 1)
-// (zero outside the volume) as 16-byte halves.
-__device__ __forceinline__ void load_halo(uint4* halo, const uint16_t* __restrict__ x, int D, int H,
-                                          int W, int z, int y0, int x0) {
-  for (int i = threadIdx.x; i < kHZ * kHY * kHX * 2; i += blockDim.x) {
-    const int half = i & 1, v = i >> 1;
-    const int hx = v % kHX, hy = (v / kHX) % kHY, hz = v / (kHX * kHY);
-    const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z + hz - 1;
-    uint4 val = make_uint4(0, 0, 0, 0);
-    if (gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D)
-      val = reinterpret_cast<const uint4*>(x + (((long long)gz * H + gy) * W + gx) * kC)[half];
-    halo[i] = val;
-  }
-}
-
-// Forward / input-gradient convolution, persistent: a CTA walks tiles of
-// 16 (x) x 8 (y) x 4 (z) output voxels.  The 18 x 10 x 6 input halo of a
-// tile (34,560 B, zero outside the volume) arrives by one 4-D TMA load with
-// the 32-byte swizzle (16-byte channel halves of voxel v swap when bit 2 of
-// v is set, so ldmatrix rows of consecutive voxels hit distinct banks), into
-// a double buffer: the next tile's load overlaps this tile's products.
-// Warp w owns the 2 x 2 output rows y = 2 (w & 3) + {0, 1},
-// z = 2 (w >> 2) + {0, 1}; every A fragment it loads (16 halo voxels x 16
-// channels of one halo row, shifted by dx) feeds each output row it
-// reaches (up to 4 x 2 products), and the 27 taps' B fragments live in
-// registers for the whole kernel.
+// Tiles of the weight-gradient kernel: 16 (x) x 8 (y) x 4 (z) output
+// voxels, the 18 x 10 x 6 input halo and the gy tile stored with the
+// 32-byte TMA swizzle (the 16-byte channel halves of voxel v swap when bit 2
+// of v is set, so ldmatrix rows of consecutive voxels hit distinct banks).
 constexpr int kFZ = 4;                                  // output planes per tile
 constexpr int kFHZ = kFZ + 2;                           // halo planes
 constexpr int kFHalo = kFHZ * kHY * kHX * kC * 2;       // bytes per halo buffer
@@ -86,132 +62,7 @@ static_assert(kFHalo % 256 == 0, "halo buffers must stay 256-byte aligned");
 
 __device__ __forceinline__ int swz(int v, int half) { return 2 * v + (half ^ ((v >> 2) & 1)); }
 
-__global__ void __launch_bounds__(256, 1)
-    conv_fwd_kernel(const __grid_constant__ CUtensorMap xmap, ConvArgs a, int* status) {
-  extern __shared__ unsigned char dsm_raw[];
-  // The swizzle acts on address bits 4 and 7: buffers start on 256 bytes.
-  unsigned char* dsm = dsm_raw + ((256 - (smem_u32(dsm_raw) & 255)) & 255);
-  __shared__ __align__(128) uint4 wsm[kTaps * kC * 2];
-  __shared__ uint64_t bar[2];
-  __shared__ int abort_flag;
-  const int tiles_x = (a.W + kTX - 1) / kTX, tiles_y = (a.H + kTY - 1) / kTY;
-  const int tiles_z = (a.D + kFZ - 1) / kFZ;
-  const long long n_tiles = (long long)tiles_x * tiles_y * tiles_z;
-  auto origin = [&](long long t, int& x0, int& y0, int& z0) {
-    x0 = (int)(t % tiles_x) * kTX;
-    y0 = (int)((t / tiles_x) % tiles_y) * kTY;
-    z0 = (int)(t / ((long long)tiles_x * tiles_y)) * kFZ;
-  };
-  auto issue = [&](int b, long long t) {
-    int x0, y0, z0;
-    origin(t, x0, y0, z0);
-    mbar_arrive_expect_tx(&bar[b], kFHalo);
-    tma_load_4d(dsm + b * kFHalo, &xmap, 0, x0 - 1, y0 - 1, z0 - 1, &bar[b]);
-  };
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_barrier_init();
-    abort_flag = 0;
-  }
-  for (int i = threadIdx.x; i < kTaps * kC * 2; i += blockDim.x)
-    wsm[i] = reinterpret_cast<const uint4*>(a.w)[i];
-  __syncthreads();
-  if (threadIdx.x == 0 && (long long)blockIdx.x < n_tiles) issue(0, blockIdx.x);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mat = lane >> 3, r = lane & 7;
-  // B fragments of every tap: rows out channel r + 8 (mat >> 1), input half (mat & 1).
-  uint32_t bw[kTaps][4];
-  {
-    const char* wb = reinterpret_cast<const char*>(wsm);
-    const int bco = r + 8 * (mat >> 1), bhalf = mat & 1;
-#pragma unroll
-    for (int tap = 0; tap < kTaps; ++tap) ldsm_x4(bw[tap], wb + (tap * kC + bco) * 32 + bhalf * 16);
-  }
-  const int wy = 2 * (warp & 3), wz = 2 * (warp >> 2);
-  // A rows: voxel r + 8 (mat & 1) of the shifted halo row, channel half (mat >> 1).
-  const int avox = r + 8 * (mat & 1), ahalf = mat >> 1;
-  const int g = lane >> 2, t = lane & 3;
-  int it = 0;
-  bool issued_next = false;  // thread 0: a load into the other buffer is in flight
-  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
-    const int b = it & 1;
-    issued_next = threadIdx.x == 0 && tile + gridDim.x < n_tiles;
-    if (issued_next) issue(b ^ 1, tile + gridDim.x);
-    if (!mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), status)) abort_flag = 1;
-    __syncthreads();
-    if (abort_flag) {
-      // Let the load still in flight land before the CTA exits (bounded).
-      if (issued_next) mbar_wait(&bar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), status);
-      return;
-    }
-    const unsigned char* hb = dsm + b * kFHalo;
-    float acc[2][2][2][4];  // [oz][oy][n half][fragment]
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int n = 0; n < 2; ++n)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[i][j][n][e] = 0.f;
-#pragma unroll
-    for (int hz = 0; hz < 4; ++hz)
-#pragma unroll
-      for (int hy = 0; hy < 4; ++hy)
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          uint32_t af[4];
-          const int v = ((wz + hz) * kHY + wy + hy) * kHX + dx + avox;
-          ldsm_x4(af, hb + swz(v, ahalf) * 16);
-#pragma unroll
-          for (int oz = 0; oz < 2; ++oz)
-#pragma unroll
-            for (int oy = 0; oy < 2; ++oy) {
-              const int dz = hz - oz, dy = hy - oy;
-              if (dz < 0 || dz > 2 || dy < 0 || dy > 2) continue;
-              const int tap = (dz * 3 + dy) * 3 + dx;
-              mma16816(acc[oz][oy][0], af, bw[tap][0], bw[tap][1]);
-              mma16816(acc[oz][oy][1], af, bw[tap][2], bw[tap][3]);
-            }
-        }
-    int x0, y0, z0;
-    origin(tile, x0, y0, z0);
-    // Epilogue: the thread holds voxels g, g + 8 and channels n*8 + 2t, +1.
-#pragma unroll
-    for (int oz = 0; oz < 2; ++oz)
-#pragma unroll
-      for (int oy = 0; oy < 2; ++oy) {
-        const int z = z0 + wz + oz, y = y0 + wy + oy;
-        if (z >= a.D || y >= a.H) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int xx = x0 + g + 8 * h;
-          if (xx >= a.W) continue;
-          const long long vox = ((long long)z * a.H + y) * a.W + xx;
-#pragma unroll
-          for (int n = 0; n < 2; ++n) {
-            const int co = n * 8 + 2 * t;
-            float v0 = acc[oz][oy][n][2 * h] + (a.bias ? a.bias[co] : 0.f);
-            float v1 = acc[oz][oy][n][2 * h + 1] + (a.bias ? a.bias[co + 1] : 0.f);
-            if (a.relu) {
-              v0 = fmaxf(v0, 0.f);
-              v1 = fmaxf(v1, 0.f);
-            }
-            if (a.mask) {
-              if (!(bf2f(a.mask[vox * kC + co]) > 0.f)) v0 = 0.f;
-              if (!(bf2f(a.mask[vox * kC + co + 1]) > 0.f)) v1 = 0.f;
-            }
-            if (a.y32) *reinterpret_cast<float2*>(a.y32 + vox * kC + co) = make_float2(v0, v1);
-            if (a.y16)
-              *reinterpret_cast<uint32_t*>(a.y16 + vox * kC + co) =
-                  (uint32_t)f2bf(v0) | ((uint32_t)f2bf(v1) << 16);
-          }
-        }
-      }
-    __syncthreads();  // buffer b is free for the load issued next iteration
-  }
-}
+#include "conv_tc.cuh"
 
 // Weight gradient: per CTA partial sums over its tiles of
 // gw[tap][o][i] = sum_p gy[p][o] x[p + tap - 1][i] and gb[o] = sum_p gy[p][o].
@@ -465,9 +316,7 @@ int wgrad_blocks() { return 152 * 2; }
 size_t wgrad_partial_floats() { return (size_t)wgrad_blocks() * (kTaps * kC * kC + kC); }
 int mse_blocks() { return 152 * 4; }
 
-size_t conv_halo_box_bytes() { return kFHalo; }
-
-void conv_halo_box(unsigned (&box)[4]) {
+void conv_wgrad_halo_box(unsigned (&box)[4]) {
   box[0] = kC;
   box[1] = kHX;
   box[2] = kHY;
@@ -481,18 +330,65 @@ void conv_gy_box(unsigned (&box)[4]) {
   box[3] = kFZ;
 }
 
-cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& xmap, int* status, cudaStream_t s) {
-  const long long n_tiles = (long long)((a.W + kTX - 1) / kTX) * ((a.H + kTY - 1) / kTY) *
-                            ((a.D + kFZ - 1) / kFZ);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(conv_fwd_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kFHalo + 256);
-    if (e != cudaSuccess) return e;
-    attr = true;
+// Blocking of the tensor-core convolution for a D x H x W volume.
+static TcPlan tc_plan(int D, int H, int W) {
+  TcPlan p{};
+  p.SW = std::min(W, kTcMaxP - 2);
+  p.P = p.SW + 2;
+  p.nxs = (W + p.SW - 1) / p.SW;
+  p.RY = std::max(1, std::min(H, (kTcMaxChunks * 128) / p.P));
+  for (;;) {  // the halo box must cover the last chunk's reach and fit a TMA box
+    p.NCH = (p.RY * p.P + 127) / 128;
+    p.rows = (p.NCH * 128 + 2 * p.P + 2 + p.P - 1) / p.P;
+    if (p.rows <= 256 || p.RY == 1) break;
+    --p.RY;
   }
-  const int grid = (int)std::min<long long>(n_tiles, 152);
-  conv_fwd_kernel<<<grid, 256, 2 * kFHalo + 256, s>>>(xmap, a, status);
+  p.nyb = (H + p.RY - 1) / p.RY;
+  // z chunk: fewest rounds of 152 persistent CTAs x planes per item; ties
+  // go to longer chunks (fewer re-loaded halo planes).
+  long long best = -1;
+  for (int zc = 1; zc <= std::min(D, 32); ++zc) {
+    const long long items = (long long)p.nxs * p.nyb * ((D + zc - 1) / zc);
+    const long long cost = ((items + 151) / 152) * zc;
+    if (best < 0 || cost <= best) {
+      best = cost;
+      p.ZC = zc;
+    }
+  }
+  p.nzc = (D + p.ZC - 1) / p.ZC;
+  p.items = (long long)p.nxs * p.nyb * p.nzc;
+  p.half_bytes = ((p.rows * p.P * 16 + 127) / 128) * 128;
+  p.slot_bytes = 2 * p.half_bytes;
+  return p;
+}
+
+static size_t tc_smem_bytes(const TcPlan& p) {
+  return (size_t)kTcRing * p.slot_bytes + (size_t)kTaps * 512 + 128;
+}
+
+void conv_halo_box(int D, int H, int W, unsigned (&box)[4]) {
+  const TcPlan p = tc_plan(D, H, W);
+  box[0] = 8;  // one channel half (16 bytes)
+  box[1] = (unsigned)p.P;
+  box[2] = (unsigned)p.rows;
+  box[3] = 1;
+}
+
+cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& mlo, const CUtensorMap& mhi,
+                        int* status, cudaStream_t s) {
+  const TcPlan p = tc_plan(a.D, a.H, a.W);
+  // At least 116 KB so that one CTA runs per SM and TMEM allocation never
+  // waits for another CTA of this kernel.
+  const size_t sm = std::max<size_t>(tc_smem_bytes(p), 116 * 1024);
+  static size_t attr = 0;
+  if (sm > attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = sm;
+  }
+  const int grid = (int)std::min<long long>(p.items, 152);
+  conv_tc_kernel<<<grid, 192, sm, s>>>(mlo, mhi, a, p, status);
   return cudaGetLastError();
 }
 

@@ -28,14 +28,17 @@ struct WgradArgs {
 int wgrad_blocks();
 size_t wgrad_partial_floats();
 int mse_blocks();
-// Input halo box of the forward kernel's TMA map over x viewed as
-// [D][H][W][16] BF16 (dims innermost first: channels, x, y, z), 32-byte
-// swizzle, zero fill outside.
-size_t conv_halo_box_bytes();
-void conv_halo_box(unsigned (&box)[4]);
-cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& xmap, int* status, cudaStream_t s);
-// gy tile box of the weight-gradient kernel's TMA map over gy (same layout
-// and swizzle as x; no halo).
+// TMA box of the tensor-core convolution's input maps for a D x H x W
+// volume: the activation viewed as [D][H][W][16] BF16 with only 8 channels
+// (one 16-byte half) per voxel in the box, innermost first (8 channels, x,
+// y, z); one map starts at channel 0, the other at channel 8.  No swizzle,
+// zero fill outside.
+void conv_halo_box(int D, int H, int W, unsigned (&box)[4]);
+cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& mlo, const CUtensorMap& mhi,
+                        int* status, cudaStream_t s);
+// Boxes of the weight-gradient kernel's maps over x (halo) and gy (tile),
+// [D][H][W][16] BF16, 32-byte swizzle.
+void conv_wgrad_halo_box(unsigned (&box)[4]);
 void conv_gy_box(unsigned (&box)[4]);
 cudaError_t launch_wgrad(const WgradArgs& a, const CUtensorMap& xmap, const CUtensorMap& gmap,
                          int* status, float* gw, float* gb, cudaStream_t s);

@@ -1,0 +1,312 @@
+// 3x3x3 convolution (forward and input gradient) on the 5th-generation
+// tensor cores: tcgen05.mma with the accumulators in tensor memory, operands
+// staged in shared memory by TMA.  Included by conv.cu inside its anonymous
+// namespace (shares bf2f / f2bf and the constants there).
+//
+// Formulation.  A CTA owns a block of RY output rows (y) of an x segment of
+// SW voxels and marches over a chunk of z planes.  Each halo plane of the
+// block (rows y0-1 .. , x from xs-1, width P = SW + 2) is stored as two
+// "channel-half planes" [half][row][x][8 channels], 16 bytes per voxel and
+// half, which is exactly the K-major no-swizzle canonical layout of a
+// tcgen05 operand: 8 consecutive voxels x 16 bytes form one core matrix.
+// Output voxels are numbered f = ry * P + xx over the block (xx in [0, P):
+// the last two columns of every row are junk and never stored), so the A
+// rows of tap (dz, dy, dx) for the 128 outputs f0 .. f0+127 are the 128
+// consecutive halo voxels starting at f0 + dy P + dx of halo plane z + dz:
+// one shared-memory descriptor (start, K stride = half-plane bytes, M stride
+// = 128 bytes) per tap and chunk, no data movement.  Per output plane:
+// NCH chunks x 27 taps of tcgen05.mma.kind::f16 M=128 N=16 K=16 (bf16 in,
+// f32 accumulate) into NCH x 16 TMEM columns; the epilogue warps read one
+// voxel's 16 output channels per thread with tcgen05.ld and store 32 (bf16)
+// or 64 (f32) contiguous bytes.
+//
+// Warp roles (192 threads): warp 0 lane 0 issues the TMA loads of halo
+// planes into a ring of 4 slots; warp 1 allocates TMEM and lane 0 issues
+// the MMAs; warps 2-5 (TMEM lane quarters 2, 3, 0, 1) run the epilogue from
+// a double-buffered accumulator.  Every wait is bounded; a timeout sets the
+// status flag and a CTA-wide abort flag that ends every role's loop.
+
+constexpr int kTcRing = 4;           // halo plane slots
+constexpr int kTcCols = 256;         // TMEM columns: 2 buffers x 8 chunks x 16
+constexpr int kTcMaxChunks = 8;
+constexpr int kTcMaxP = 200;         // halo row width (x segment + 2)
+
+struct TcPlan {
+  int P, SW, RY, NCH, rows, ZC;
+  int nxs, nyb, nzc;
+  long long items;
+  int half_bytes, slot_bytes;  // shared memory of one channel half / slot
+};
+
+__device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem desc] x B[smem desc]^T, kind::f16 (bf16 operands, f32 D).
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrives on the mbarrier once every MMA this thread issued so far is done.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading
+// (K-direction core-matrix) byte offset, stride (M/N-direction 8-row group)
+// byte offset, descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+// Bounded wait that also ends when another role has aborted.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* status,
+                                        volatile int* abort_flag) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && *abort_flag) return false;
+  }
+  atomicOr(status, kErrTimeout);
+  *abort_flag = 1;
+  return false;
+}
+
+__global__ void __launch_bounds__(192, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap mlo, const __grid_constant__ CUtensorMap mhi,
+                   ConvArgs a, TcPlan pl, int* status) {
+  extern __shared__ unsigned char tc_raw[];
+  unsigned char* sm = tc_raw + ((128 - (smem_u32(tc_raw) & 127)) & 127);
+  unsigned char* slots = sm;                               // kTcRing x slot_bytes
+  unsigned char* wts = sm + kTcRing * pl.slot_bytes;       // [27][k half][16 out][8 in] bf16
+  __shared__ uint64_t full[kTcRing], empty[kTcRing], tfull[2], tempty[2], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  volatile int* ab = &abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // B operand: weights w[tap][o][i] in the K-major canonical layout (core
+  // matrix = 8 out channels x 8 in channels; out groups 128 B apart, in
+  // halves 256 B apart).
+  for (int e = threadIdx.x; e < kTaps * kC * kC; e += blockDim.x) {
+    const int tap = e / (kC * kC), o = (e / kC) % kC, i = e % kC;
+    reinterpret_cast<uint16_t*>(wts)[(tap * 2 + (i >> 3)) * 128 + o * 8 + (i & 7)] = a.w[e];
+  }
+  fence_async_smem();  // visible to the tensor cores (async proxy)
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kTcRing; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_init(&done_bar, 1);
+    fence_barrier_init();
+    abort_flag = 0;
+  }
+  if (warp == 1) {
+    tc_alloc(&tmem_base, kTcCols);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  auto geom = [&](long long it, int& xs, int& y0, int& z0, int& nz) {
+    xs = (int)(it % pl.nxs) * pl.SW;
+    y0 = (int)((it / pl.nxs) % pl.nyb) * pl.RY;
+    z0 = (int)(it / ((long long)pl.nxs * pl.nyb)) * pl.ZC;
+    nz = min(pl.ZC, a.D - z0);
+  };
+
+  if (warp == 0) {
+    // ---- producer: halo planes z0 - 1 .. z0 + nz of each item, in order
+    if (lane == 0) {
+      const uint32_t tx = 2u * 16u * (uint32_t)pl.P * (uint32_t)pl.rows;
+      uint32_t q = 0;
+      for (long long it = blockIdx.x; it < pl.items && !*ab; it += gridDim.x) {
+        int xs, y0, z0, nz;
+        geom(it, xs, y0, z0, nz);
+        for (int h = 0; h < nz + 2; ++h, ++q) {
+          const int s = (int)(q % kTcRing);
+          if (!tc_wait(&empty[s], ((q / kTcRing) & 1) ^ 1, status, ab)) break;
+          unsigned char* dst = slots + (size_t)s * pl.slot_bytes;
+          mbar_arrive_expect_tx(&full[s], tx);
+          tma_load_4d(dst, &mlo, 0, xs - 1, y0 - 1, z0 - 1 + h, &full[s]);
+          tma_load_4d(dst + pl.half_bytes, &mhi, 0, xs - 1, y0 - 1, z0 - 1 + h, &full[s]);
+        }
+      }
+      if (*ab)  // let issued loads land before the CTA exits
+        for (uint32_t k = 0; k < kTcRing && k < q; ++k) {
+          const uint32_t qq = q - 1 - k;
+          mbar_wait(&full[qq % kTcRing], (qq / kTcRing) & 1, status);
+        }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t wbase = smem_u32(wts), sbase = smem_u32(slots);
+      uint32_t q0 = 0, p = 0;
+      for (long long it = blockIdx.x; it < pl.items && !*ab; it += gridDim.x) {
+        int xs, y0, z0, nz;
+        geom(it, xs, y0, z0, nz);
+        for (int j = 0; j < nz; ++j, ++p) {
+          const int buf = (int)(p & 1);
+          if (!tc_wait(&tempty[buf], ((p >> 1) & 1) ^ 1, status, ab)) break;
+          bool ok = true;
+          for (int dz = 0; dz < 3 && ok; ++dz) {
+            const uint32_t q = q0 + j + dz;
+            ok = tc_wait(&full[q % kTcRing], (q / kTcRing) & 1, status, ab);
+          }
+          if (!ok) break;
+          tc_fence_after();
+          for (int c = 0; c < pl.NCH; ++c) {
+            const uint32_t d = tmem + (uint32_t)(buf * 128 + c * 16);
+#pragma unroll 1
+            for (int tap = 0; tap < kTaps; ++tap) {
+              const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+              const uint32_t q = q0 + j + dz;
+              const uint32_t aaddr = sbase + (q % kTcRing) * (uint32_t)pl.slot_bytes +
+                                     (uint32_t)(c * 128 + dy * pl.P + dx) * 16u;
+              tc_mma(d, tc_sdesc(aaddr, (uint32_t)pl.half_bytes, 128u),
+                     tc_sdesc(wbase + (uint32_t)tap * 512u, 256u, 128u), kTcIdesc, tap > 0);
+            }
+          }
+          tc_commit(&tfull[buf]);
+          tc_commit(&empty[(q0 + j) % kTcRing]);
+          if (j == nz - 1) {
+            tc_commit(&empty[(q0 + j + 1) % kTcRing]);
+            tc_commit(&empty[(q0 + j + 2) % kTcRing]);
+          }
+        }
+        q0 += nz + 2;
+      }
+      tc_commit(&done_bar);  // every MMA issued above has completed
+      mbar_wait(&done_bar, 0, status);
+    }
+  } else {
+    // ---- epilogue: one output voxel (16 channels) per thread and chunk
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    float bias[kC];
+#pragma unroll
+    for (int o = 0; o < kC; ++o) bias[o] = a.bias ? a.bias[o] : 0.f;
+    uint32_t p = 0;
+    for (long long it = blockIdx.x; it < pl.items && !*ab; it += gridDim.x) {
+      int xs, y0, z0, nz;
+      geom(it, xs, y0, z0, nz);
+      for (int j = 0; j < nz; ++j, ++p) {
+        const int buf = (int)(p & 1);
+        if (!tc_wait(&tfull[buf], (p >> 1) & 1, status, ab)) break;
+        tc_fence_after();
+        const int z = z0 + j;
+        for (int c = 0; c < pl.NCH; ++c) {
+          uint32_t r[16];
+          tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + c * 16), r);
+          tc_wait_ld();
+          const int f = c * 128 + row;
+          const int ry = f / pl.P, xx = f % pl.P;
+          const int y = y0 + ry, x = xs + xx;
+          if (ry < pl.RY && xx < pl.SW && y < a.H && x < a.W) {
+            const long long vox = ((long long)z * a.H + y) * a.W + x;
+            float v[kC];
+#pragma unroll
+            for (int o = 0; o < kC; ++o) {
+              v[o] = __uint_as_float(r[o]) + bias[o];
+              if (a.relu) v[o] = fmaxf(v[o], 0.f);
+            }
+            if (a.mask) {
+              const uint4* mp = reinterpret_cast<const uint4*>(a.mask + vox * kC);
+              const uint4 m0 = mp[0], m1 = mp[1];
+              const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+              for (int o = 0; o < kC; ++o) {
+                const uint16_t mb = (uint16_t)(mw[o >> 1] >> (16 * (o & 1)));
+                if (!(bf2f(mb) > 0.f)) v[o] = 0.f;
+              }
+            }
+            if (a.y32) {
+              float4* yp = reinterpret_cast<float4*>(a.y32 + vox * kC);
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                yp[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            }
+            if (a.y16) {
+              uint32_t pk[8];
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                pk[k] = (uint32_t)f2bf(v[2 * k]) | ((uint32_t)f2bf(v[2 * k + 1]) << 16);
+              uint4* yp = reinterpret_cast<uint4*>(a.y16 + vox * kC);
+              yp[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              yp[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tc_dealloc(tmem, kTcCols);
+  }
+}

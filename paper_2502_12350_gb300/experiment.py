@@ -34,7 +34,12 @@ def main(argv=None):
     ap.add_argument("--nx", type=int, default=160)
     ap.add_argument("--ny", type=int, default=160)
     ap.add_argument("--nz", type=int, default=80)
-    ap.add_argument("--test-model", type=int, default=5400)
+    ap.add_argument("--test-model", type=int, default=5420)
+    ap.add_argument("--water", type=float, default=0.05,
+                    help="water level of the preconditioning diagonals (fraction of the max)")
+    ap.add_argument("--save-net", default=None, help="write the trained network (.npz)")
+    ap.add_argument("--load-net", default=None,
+                    help="use a trained network (.npz) instead of labelling and training")
     ap.add_argument("--arms", default="none,pseudo,learned,exact")
     args = ap.parse_args(argv)
 
@@ -48,26 +53,42 @@ def main(argv=None):
         return synth.fwi_small(model_id=mid, nt=args.nt, nx=args.nx, ny=args.ny, nz=args.nz)
 
     net = cnn.Net(ctx, seed=1)
-    t0 = time.perf_counter()
+    # training models 5000 .. 5000+n-1, held-out models right after them,
+    # the inverted model after those
     train_ids = list(range(5000, 5000 + args.train_models))
-    test_ids = list(range(5400 - args.heldout_models, 5400))
-    data = learned.dataset(ctx, net, wl, train_ids, seed=1)
-    held = learned.dataset(ctx, net, wl, test_ids, seed=2, set_offset=False)
-    report["offset"] = net.offset
-    torch.cuda.synchronize()
-    report["label_seconds"] = time.perf_counter() - t0
-    report["label_seconds_per_model"] = report["label_seconds"] / (len(train_ids) + len(test_ids))
-    t0 = time.perf_counter()
-    hist = learned.train(net, data, args.epochs, lr=args.lr,
-                         log=lambda m: print(m) if m.split(":")[0].endswith("0") else None)
-    torch.cuda.synchronize()
-    report["train_seconds"] = time.perf_counter() - t0
-    report["train_loss"] = hist
-    errs = learned.log_errors(net, held)
-    report["heldout_log_rms"] = {"network": [e[0] for e in errs],
-                                 "pseudo_hessian_rescaled": [e[1] for e in errs]}
-    print("held-out RMS log error (network, rescaled P): %.3f %.3f" %
-          (np.mean([e[0] for e in errs]), np.mean([e[1] for e in errs])))
+    test_ids = list(range(5000 + args.train_models, 5000 + args.train_models + args.heldout_models))
+    assert args.test_model not in train_ids + test_ids
+    if args.load_net:
+        z = np.load(args.load_net)
+        ws = [z[f"w{l}"] for l in range(cnn.LAYERS)]
+        bs = [z[f"b{l}"] for l in range(cnn.LAYERS)]
+        net = cnn.Net(ctx, weights=(ws, bs))
+        net.offset = float(z["offset"])
+        report["loaded_net"] = args.load_net
+    else:
+        t0 = time.perf_counter()
+        data = learned.dataset(ctx, net, wl, train_ids, seed=1)
+        held = learned.dataset(ctx, net, wl, test_ids, seed=2, set_offset=False)
+        report["offset"] = net.offset
+        torch.cuda.synchronize()
+        report["label_seconds"] = time.perf_counter() - t0
+        report["label_seconds_per_model"] = report["label_seconds"] / (len(train_ids) + len(test_ids))
+        t0 = time.perf_counter()
+        hist = learned.train(net, data, args.epochs, lr=args.lr,
+                             log=lambda m: print(m) if m.split(":")[0].endswith("0") else None)
+        torch.cuda.synchronize()
+        report["train_seconds"] = time.perf_counter() - t0
+        report["train_loss"] = hist
+        errs = learned.log_errors(net, held)
+        report["heldout_log_rms"] = {"network": [e[0] for e in errs],
+                                     "pseudo_hessian_rescaled": [e[1] for e in errs]}
+        print("held-out RMS log error (network, rescaled P): %.3f %.3f" %
+              (np.mean([e[0] for e in errs]), np.mean([e[1] for e in errs])))
+        del data, held
+        if args.save_net:
+            ws, bs = net.weights()
+            np.savez(args.save_net, offset=net.offset, **{f"w{l}": ws[l] for l in range(cnn.LAYERS)},
+                     **{f"b{l}": bs[l] for l in range(cnn.LAYERS)})
 
     w = wl(args.test_model)
     g = mamute.grid_of(w)
@@ -79,7 +100,8 @@ def main(argv=None):
     runs = {}
     for kind in args.arms.split(","):
         prob = fwi.Problem(ctx, w, dobs, vmin, vmax)
-        res = fwi.run(prob, w.vel_init.astype(np.float64), args.iters, precond=kind, net=net)
+        res = fwi.run(prob, w.vel_init.astype(np.float64), args.iters, precond=kind, net=net,
+                      water=args.water)
         err = float(np.sqrt(np.mean((res.vel - w.vel) ** 2)))
         runs[kind] = {"history": [(t, J, k) for t, J, k in res.history],
                       "model_rms_error": err, "gradients": res.n_gradients,

@@ -114,7 +114,7 @@ def _diag(h, water=0.05):
 
 def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net=None,
         memory: int = 5, first_step: float = 40.0, learned_backtracks: int = 4,
-        max_backtracks: int = 8, c1: float = 1e-4) -> Result:
+        max_backtracks: int = 8, c1: float = 1e-4, water: float = 0.05) -> Result:
     """Projected L-BFGS on the misfit.  first_step (m/s) scales the first
     direction; later iterations try the unit L-BFGS step first."""
     shape = v0.shape
@@ -128,18 +128,18 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
         if kind == "none":
             return np.ones_like(x)
         if kind == "pseudo":
-            return _diag(ph.cpu().numpy())
+            return _diag(ph.cpu().numpy(), water)
         if kind == "exact":
             vt = torch.from_numpy(x.reshape(shape).astype(np.float32)).to(prob.dev)
             hd = torch.empty_like(vt)
             w = prob.w
             prob.ctx.gn_diagonal(prob.grid, vt, None, w.src_xyz, w.wavelet, w.rec_offset,
                                  w.rec_xyz, hd)
-            return _diag(hd.cpu().numpy())
+            return _diag(hd.cpu().numpy(), water)
         vt = torch.from_numpy(x.reshape(shape).astype(np.float32)).to(prob.dev)
         x16, _, _ = net.features(vt, ph)
         out = net.forward(x16).cpu().numpy().astype(np.float64)
-        return _diag(ph.cpu().numpy().astype(np.float64) * np.exp(out + net.offset))
+        return _diag(ph.cpu().numpy().astype(np.float64) * np.exp(out + net.offset), water)
 
     def line_search(d, J, g, x, max_bt, alpha, expand):
         for _ in range(max_bt + 1):

@@ -37,7 +37,9 @@ def _rand_act(rng, D, H, W, ch):
     return conv.bf16_round(x)
 
 
-SHAPES = [(3, 8, 16), (5, 11, 21), (2, 9, 33)]
+# ragged tiles in every axis; two x segments (W > 198); many row blocks with
+# z chunks of 3 planes per persistent CTA item
+SHAPES = [(3, 8, 16), (5, 11, 21), (2, 9, 33), (2, 3, 205), (8, 200, 198)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
