@@ -308,7 +308,7 @@ def run_cnn_bench(args):
             "data": "synthetic", "config": {"workload": "cnn_4x3^3_16ch_80x160x160"},
             "roofline": {"bound": "tensor", "achieved": conv_tf, "peak": peak, "unit": "TFLOP/s",
                          "frac": conv_tf / peak, "traffic": None, "peak_kind": "measured",
-                         "kernel": "conv_fwd_kernel (16 -> 16, 3x3x3)",
+                         "kernel": "conv_tc_kernel (16 -> 16, 3x3x3, tcgen05)",
                          "flops_per_voxel": 2 * 27 * 16 * 16, "kernel_ms": conv_ms,
                          "training_step_tflops": tf}}
     ctx.close()

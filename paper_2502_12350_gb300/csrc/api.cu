@@ -696,7 +696,7 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   // the buffers and the wavelet stay the same (MAMUTE_GRAPHS=0 disables).
   std::vector<unsigned long long> key;
   const bool stream_out = host_seis != nullptr && P.ncol > 0;
-  const bool use_graph = env_int("MAMUTE_GRAPHS", 1) != 0 && P.nt >= 8 && !stream_out;
+  const bool use_graph = env_int("MAMUTE_GRAPHS", 1) != 0 && P.nt >= 8;
   if (use_graph) {
     auto push = [&](const void* p) { key.push_back((unsigned long long)(uintptr_t)p); };
     key.push_back((unsigned long long)P.nt);
@@ -714,24 +714,23 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
       std::memcpy(&u, &wavelet[n], 4);
       key.push_back(u);
     }
+    key.push_back(stream_out ? 1 : 0);
+    if (stream_out) {
+      push(seis);
+      push(host_seis);
+    }
   }
   auto launch_all = [&]() -> int {
-    for (int n = 0; n < P.nt; ++n) {
-      StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
-      CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+    if (!stream_out) {
+      for (int n = 0; n < P.nt; ++n) {
+        StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
+        CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+      }
+      return MAMUTE_OK;
     }
-    return MAMUTE_OK;
-  };
-  if (stream_out) {
     // In 8 segments: after each, the copy stream transposes that segment's
     // samples and copies them to the host while the next segment runs.
-    if (!ctx->copy) CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
     const int nseg = std::min(P.nt, 8);
-    while ((int)ctx->seg_ev.size() < nseg + 1) {
-      cudaEvent_t ev = nullptr;
-      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      ctx->seg_ev.push_back(ev);
-    }
     int t0 = 0;
     for (int k = 0; k < nseg; ++k) {
       const int t1 = (int)((long long)P.nt * (k + 1) / nseg);
@@ -750,7 +749,17 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
     }
     CK(cudaEventRecord(ctx->seg_ev[nseg], ctx->copy));
     CK(cudaStreamWaitEvent(ctx->stream, ctx->seg_ev[nseg], 0));
-  } else if (!use_graph) {
+    return MAMUTE_OK;
+  };
+  if (stream_out) {
+    if (!ctx->copy) CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    while ((int)ctx->seg_ev.size() < 9) {
+      cudaEvent_t ev = nullptr;
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      ctx->seg_ev.push_back(ev);
+    }
+  }
+  if (!use_graph) {
     TRY(launch_all());
   } else {
     if (!ctx->graph || ctx->graph_key != key) {
@@ -792,7 +801,7 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
       ctx->ev0_set = true;
     }
     ctx->step_launches = P.nt;
-    ctx->launches += P.nt;
+    ctx->launches += P.nt + (stream_out ? std::min(P.nt, 8) : 0);
   }
   if (!stream_out)
     CK(aux_count(ctx, launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt,

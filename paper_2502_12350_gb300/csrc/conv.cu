@@ -330,19 +330,37 @@ void conv_gy_box(unsigned (&box)[4]) {
   box[3] = kFZ;
 }
 
-// Blocking of the tensor-core convolution for a D x H x W volume.
+// Blocking of the tensor-core convolution for a D x H x W volume: the
+// tallest row block (at most 8 chunks of 128 outputs) whose halo slots leave
+// room for a ring of 5 (lookahead of 2 planes), else the tallest with 4.
+constexpr int kTcSmemMax = 232448;                  // dynamic shared memory per CTA
+constexpr int kTcSlotBudget = kTcSmemMax - kTaps * 512 - 128;
+
 static TcPlan tc_plan(int D, int H, int W) {
   TcPlan p{};
   p.SW = std::min(W, kTcMaxP - 2);
   p.P = p.SW + 2;
   p.nxs = (W + p.SW - 1) / p.SW;
-  p.RY = std::max(1, std::min(H, (kTcMaxChunks * 128) / p.P));
-  for (;;) {  // the halo box must cover the last chunk's reach and fit a TMA box
+  auto shape = [&](int ry) {
+    p.RY = ry;
     p.NCH = (p.RY * p.P + 127) / 128;
+    // the halo box must cover the last chunk's reach
     p.rows = (p.NCH * 128 + 2 * p.P + 2 + p.P - 1) / p.P;
-    if (p.rows <= 256 || p.RY == 1) break;
-    --p.RY;
-  }
+    p.half_bytes = ((p.rows * p.P * 16 + 127) / 128) * 128;
+    p.slot_bytes = 2 * p.half_bytes;
+    p.ring = std::min(kTcMaxRing, kTcSlotBudget / p.slot_bytes);
+  };
+  const int ry_max = std::max(1, std::min(H, (kTcMaxChunks * 128) / p.P));
+  int pick = 0;
+  for (int want = 5; want >= 3 && !pick; --want)
+    for (int ry = ry_max; ry >= 1; --ry) {
+      shape(ry);
+      if (p.rows <= 256 && p.ring >= want) {
+        pick = ry;
+        break;
+      }
+    }
+  shape(pick > 0 ? pick : 1);
   p.nyb = (H + p.RY - 1) / p.RY;
   // z chunk: fewest rounds of 152 persistent CTAs x planes per item; ties
   // go to longer chunks (fewer re-loaded halo planes).
@@ -357,13 +375,11 @@ static TcPlan tc_plan(int D, int H, int W) {
   }
   p.nzc = (D + p.ZC - 1) / p.ZC;
   p.items = (long long)p.nxs * p.nyb * p.nzc;
-  p.half_bytes = ((p.rows * p.P * 16 + 127) / 128) * 128;
-  p.slot_bytes = 2 * p.half_bytes;
   return p;
 }
 
 static size_t tc_smem_bytes(const TcPlan& p) {
-  return (size_t)kTcRing * p.slot_bytes + (size_t)kTaps * 512 + 128;
+  return (size_t)p.ring * p.slot_bytes + (size_t)kTaps * 512 + 128;
 }
 
 void conv_halo_box(int D, int H, int W, unsigned (&box)[4]) {

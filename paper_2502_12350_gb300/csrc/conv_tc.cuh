@@ -26,13 +26,13 @@
 // a double-buffered accumulator.  Every wait is bounded; a timeout sets the
 // status flag and a CTA-wide abort flag that ends every role's loop.
 
-constexpr int kTcRing = 4;           // halo plane slots
+constexpr int kTcMaxRing = 6;        // halo plane slots (at most)
 constexpr int kTcCols = 256;         // TMEM columns: 2 buffers x 8 chunks x 16
 constexpr int kTcMaxChunks = 8;
 constexpr int kTcMaxP = 200;         // halo row width (x segment + 2)
 
 struct TcPlan {
-  int P, SW, RY, NCH, rows, ZC;
+  int P, SW, RY, NCH, rows, ZC, ring;
   int nxs, nyb, nzc;
   long long items;
   int half_bytes, slot_bytes;  // shared memory of one channel half / slot
@@ -80,13 +80,18 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 64 consecutive f32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, uint32_t (&r)[64]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
       : "r"(taddr));
 }
 
@@ -129,9 +134,9 @@ __global__ void __launch_bounds__(192, 1)
                    ConvArgs a, TcPlan pl, int* status) {
   extern __shared__ unsigned char tc_raw[];
   unsigned char* sm = tc_raw + ((128 - (smem_u32(tc_raw) & 127)) & 127);
-  unsigned char* slots = sm;                               // kTcRing x slot_bytes
-  unsigned char* wts = sm + kTcRing * pl.slot_bytes;       // [27][k half][16 out][8 in] bf16
-  __shared__ uint64_t full[kTcRing], empty[kTcRing], tfull[2], tempty[2], done_bar;
+  unsigned char* slots = sm;                               // ring x slot_bytes
+  unsigned char* wts = sm + pl.ring * pl.slot_bytes;       // [27][k half][16 out][8 in] bf16
+  __shared__ uint64_t full[kTcMaxRing], empty[kTcMaxRing], tfull[2], tempty[2], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   volatile int* ab = &abort_flag;
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   fence_async_smem();  // visible to the tensor cores (async proxy)
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kTcRing; ++i) {
+    for (int i = 0; i < kTcMaxRing; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
@@ -183,8 +188,8 @@ __global__ void __launch_bounds__(192, 1)
         int xs, y0, z0, nz;
         geom(it, xs, y0, z0, nz);
         for (int h = 0; h < nz + 2; ++h, ++q) {
-          const int s = (int)(q % kTcRing);
-          if (!tc_wait(&empty[s], ((q / kTcRing) & 1) ^ 1, status, ab)) break;
+          const int s = (int)(q % pl.ring);
+          if (!tc_wait(&empty[s], ((q / pl.ring) & 1) ^ 1, status, ab)) break;
           unsigned char* dst = slots + (size_t)s * pl.slot_bytes;
           mbar_arrive_expect_tx(&full[s], tx);
           tma_load_4d(dst, &mlo, 0, xs - 1, y0 - 1, z0 - 1 + h, &full[s]);
@@ -192,9 +197,9 @@ __global__ void __launch_bounds__(192, 1)
         }
       }
       if (*ab)  // let issued loads land before the CTA exits
-        for (uint32_t k = 0; k < kTcRing && k < q; ++k) {
+        for (uint32_t k = 0; k < (uint32_t)pl.ring && k < q; ++k) {
           const uint32_t qq = q - 1 - k;
-          mbar_wait(&full[qq % kTcRing], (qq / kTcRing) & 1, status);
+          mbar_wait(&full[qq % pl.ring], (qq / pl.ring) & 1, status);
         }
     }
   } else if (warp == 1) {
@@ -208,30 +213,38 @@ __global__ void __launch_bounds__(192, 1)
         for (int j = 0; j < nz; ++j, ++p) {
           const int buf = (int)(p & 1);
           if (!tc_wait(&tempty[buf], ((p >> 1) & 1) ^ 1, status, ab)) break;
+          // Taps in dz order: the oldest halo plane (dz = 0) is released as soon
+          // as its products are done, so its slot refills while the newer
+          // planes' products run, and the newest plane is needed last.
+          const uint64_t b0 = tc_sdesc(wbase, 256u, 128u);
+          const uint64_t rowoff[3] = {0ull, (uint64_t)pl.P, 2ull * (uint64_t)pl.P};
           bool ok = true;
-          for (int dz = 0; dz < 3 && ok; ++dz) {
+#pragma unroll
+          for (int dz = 0; dz < 3; ++dz) {
             const uint32_t q = q0 + j + dz;
-            ok = tc_wait(&full[q % kTcRing], (q / kTcRing) & 1, status, ab);
+            if (!(ok = tc_wait(&full[q % pl.ring], (q / pl.ring) & 1, status, ab))) break;
+            tc_fence_after();
+            // start-address field (address >> 4) advanced by
+            // chunk * 128 + dy * P + dx voxels of 16 bytes
+            const uint64_t a0 = tc_sdesc(sbase + (q % pl.ring) * (uint32_t)pl.slot_bytes,
+                                         (uint32_t)pl.half_bytes, 128u);
+            for (int c = 0; c < pl.NCH; ++c) {
+              const uint32_t d = tmem + (uint32_t)(buf * 128 + c * 16);
+              const uint64_t ac = a0 + (uint64_t)c * 128u;
+#pragma unroll
+              for (int t9 = 0; t9 < 9; ++t9) {
+                const int dy = t9 / 3, dx = t9 % 3;
+                tc_mma(d, ac + rowoff[dy] + (uint64_t)dx, b0 + (uint64_t)(dz * 9 + t9) * 32u,
+                       kTcIdesc, (dz | t9) != 0);
+              }
+            }
+            if (dz == 0) tc_commit(&empty[(q0 + j) % pl.ring]);
           }
           if (!ok) break;
-          tc_fence_after();
-          for (int c = 0; c < pl.NCH; ++c) {
-            const uint32_t d = tmem + (uint32_t)(buf * 128 + c * 16);
-#pragma unroll 1
-            for (int tap = 0; tap < kTaps; ++tap) {
-              const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-              const uint32_t q = q0 + j + dz;
-              const uint32_t aaddr = sbase + (q % kTcRing) * (uint32_t)pl.slot_bytes +
-                                     (uint32_t)(c * 128 + dy * pl.P + dx) * 16u;
-              tc_mma(d, tc_sdesc(aaddr, (uint32_t)pl.half_bytes, 128u),
-                     tc_sdesc(wbase + (uint32_t)tap * 512u, 256u, 128u), kTcIdesc, tap > 0);
-            }
-          }
           tc_commit(&tfull[buf]);
-          tc_commit(&empty[(q0 + j) % kTcRing]);
           if (j == nz - 1) {
-            tc_commit(&empty[(q0 + j + 1) % kTcRing]);
-            tc_commit(&empty[(q0 + j + 2) % kTcRing]);
+            tc_commit(&empty[(q0 + j + 1) % pl.ring]);
+            tc_commit(&empty[(q0 + j + 2) % pl.ring]);
           }
         }
         q0 += nz + 2;
@@ -255,19 +268,21 @@ __global__ void __launch_bounds__(192, 1)
         if (!tc_wait(&tfull[buf], (p >> 1) & 1, status, ab)) break;
         tc_fence_after();
         const int z = z0 + j;
-        for (int c = 0; c < pl.NCH; ++c) {
-          uint32_t r[16];
-          tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + c * 16), r);
+        for (int c0 = 0; c0 < pl.NCH; c0 += 4) {  // 4 chunks (64 columns) per TMEM load
+          uint32_t r[64];
+          tc_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + c0 * 16), r);
           tc_wait_ld();
-          const int f = c * 128 + row;
-          const int ry = f / pl.P, xx = f % pl.P;
-          const int y = y0 + ry, x = xs + xx;
-          if (ry < pl.RY && xx < pl.SW && y < a.H && x < a.W) {
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const int f = (c0 + cc) * 128 + row;
+            const int ry = f / pl.P, xx = f % pl.P;
+            const int y = y0 + ry, x = xs + xx;
+            if (c0 + cc >= pl.NCH || ry >= pl.RY || xx >= pl.SW || y >= a.H || x >= a.W) continue;
             const long long vox = ((long long)z * a.H + y) * a.W + x;
             float v[kC];
 #pragma unroll
             for (int o = 0; o < kC; ++o) {
-              v[o] = __uint_as_float(r[o]) + bias[o];
+              v[o] = __uint_as_float(r[cc * 16 + o]) + bias[o];
               if (a.relu) v[o] = fmaxf(v[o], 0.f);
             }
             if (a.mask) {

@@ -101,7 +101,7 @@ def test_gradient_256cube_storage_modes_and_descent(ctx):
     """The 256^3 single-shot gradient: automatic storage (every imaging term
     kept, the benchmark's configuration) equals 16-slot binomial
     checkpointing bit for bit, and a small step along -grad lowers the
-    misfit."""
+    misfit by the amount the gradient predicts."""
     from paper_2502_12350_gb300 import mamute
     w = synth.gradient_single()
     dev = torch.device("cuda:0")
@@ -119,10 +119,17 @@ def test_gradient_256cube_storage_modes_and_descent(ctx):
     assert J0 == J1 and J0 > 0
     assert bool(torch.equal(g0, g1))
     assert bool(torch.isfinite(g0).all()) and float(g0.abs().max()) > 0
-    step = 5.0 / float(g0.abs().max())  # at most 5 m/s
-    seis = run_model(ctx, dataclasses.replace(wi, vel=(wi.vel - step * g0.cpu().numpy())))
-    J_new = 0.5 * float(((seis.double() - dobs.double()) ** 2).sum())
-    assert J_new < J0
+    # First-order check along -grad, away from the acquisition layer and the
+    # outer model layer (whose edge replication into the sponge the gradient
+    # leaves out): J(c + eps d) - J(c) ~ eps <grad, d> for a 0.5 m/s step.
+    gn = g0.cpu().numpy().astype(np.float64)
+    d = np.zeros_like(gn)
+    d[16:-1, 1:-1, 1:-1] = -gn[16:-1, 1:-1, 1:-1]
+    eps = 0.5 / np.abs(d).max()
+    pred = eps * float(np.sum(gn * d))
+    seis = run_model(ctx, dataclasses.replace(wi, vel=(wi.vel + eps * d).astype(np.float32)))
+    dJ = 0.5 * float(((seis.double() - dobs.double()) ** 2).sum()) - J0
+    assert dJ < 0 and 0.5 < dJ / pred < 1.5, (dJ, pred)
 
 
 def test_batched_shots_match_single_shots_and_oracle(ctx, oracle):
