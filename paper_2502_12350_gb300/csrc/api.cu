@@ -1500,20 +1500,6 @@ static CUresult encode_act(mamute_ctx* ctx, CUtensorMap* m, const void* p, int D
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-// TMA map over 8 channels (16 bytes) of every voxel of a [D][H][W][16] BF16
-// activation starting at p (channel 0 or 8): innermost first (8 channels,
-// x, y, z), no swizzle, zero fill outside.
-static CUresult encode_half(mamute_ctx* ctx, CUtensorMap* m, const void* p, int D, int H, int W,
-                            const unsigned (&box)[4]) {
-  cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
-  cuuint64_t strides[3] = {32, (cuuint64_t)W * 32, (cuuint64_t)W * H * 32};
-  cuuint32_t cbox[4] = {box[0], box[1], box[2], box[3]};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  return ctx->encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(p), dims, strides,
-                     cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-}
-
 // As nn_end, for kernels with bounded device-side waits.
 static int nn_end_status(mamute_ctx* ctx) {
   int st = 0;
@@ -1532,15 +1518,15 @@ int mamute_conv3d(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
   if ((uintptr_t)x % 16)
     return fail(ctx, MAMUTE_EINVAL, "conv3d: x must be 16-byte aligned");
   ConvArgs a{x, w, bias, relu, mask, y32, y16, D, H, W};
-  // Two maps over x, one per 16-byte channel half, so the halo lands as
-  // [half][row][x][8 channels] (the tensor cores' K-major layout).
-  CUtensorMap mlo, mhi;
+  if ((uintptr_t)mask % 16 || (uintptr_t)y32 % 16 || (uintptr_t)y16 % 16)
+    return fail(ctx, MAMUTE_EINVAL, "conv3d: mask and outputs must be 16-byte aligned");
+  CUtensorMap xmap;
   unsigned box[4];
   conv_halo_box(D, H, W, box);
-  if (encode_half(ctx, &mlo, x, D, H, W, box) || encode_half(ctx, &mhi, x + 8, D, H, W, box))
+  if (encode_act(ctx, &xmap, x, D, H, W, box))
     return fail(ctx, MAMUTE_ECUDA, "conv3d: cuTensorMapEncodeTiled failed");
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
-  CK(launch_conv(a, mlo, mhi, ctx->status, ctx->stream));
+  CK(launch_conv(a, xmap, ctx->status, ctx->stream));
   return nn_end_status(ctx);
 }
 

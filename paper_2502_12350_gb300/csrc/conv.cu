@@ -334,7 +334,7 @@ void conv_gy_box(unsigned (&box)[4]) {
 // tallest row block (at most 8 chunks of 128 outputs) whose halo slots leave
 // room for a ring of 5 (lookahead of 2 planes), else the tallest with 4.
 constexpr int kTcSmemMax = 232448;                  // dynamic shared memory per CTA
-constexpr int kTcSlotBudget = kTcSmemMax - kTaps * 512 - 128;
+constexpr int kTcSlotBudget = kTcSmemMax - kTaps * 512 - 1024;
 
 static TcPlan tc_plan(int D, int H, int W) {
   TcPlan p{};
@@ -346,8 +346,7 @@ static TcPlan tc_plan(int D, int H, int W) {
     p.NCH = (p.RY * p.P + 127) / 128;
     // the halo box must cover the last chunk's reach
     p.rows = (p.NCH * 128 + 2 * p.P + 2 + p.P - 1) / p.P;
-    p.half_bytes = ((p.rows * p.P * 16 + 127) / 128) * 128;
-    p.slot_bytes = 2 * p.half_bytes;
+    p.slot_bytes = ((p.rows * p.P * 32 + 1023) / 1024) * 1024;
     p.ring = std::min(kTcMaxRing, kTcSlotBudget / p.slot_bytes);
   };
   const int ry_max = std::max(1, std::min(H, (kTcMaxChunks * 128) / p.P));
@@ -379,19 +378,18 @@ static TcPlan tc_plan(int D, int H, int W) {
 }
 
 static size_t tc_smem_bytes(const TcPlan& p) {
-  return (size_t)p.ring * p.slot_bytes + (size_t)kTaps * 512 + 128;
+  return (size_t)p.ring * p.slot_bytes + (size_t)kTaps * 512 + 1024;
 }
 
 void conv_halo_box(int D, int H, int W, unsigned (&box)[4]) {
   const TcPlan p = tc_plan(D, H, W);
-  box[0] = 8;  // one channel half (16 bytes)
+  box[0] = 16;  // one voxel (32 bytes, the swizzle span)
   box[1] = (unsigned)p.P;
   box[2] = (unsigned)p.rows;
   box[3] = 1;
 }
 
-cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& mlo, const CUtensorMap& mhi,
-                        int* status, cudaStream_t s) {
+cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& xmap, int* status, cudaStream_t s) {
   const TcPlan p = tc_plan(a.D, a.H, a.W);
   // At least 116 KB so that one CTA runs per SM and TMEM allocation never
   // waits for another CTA of this kernel.
@@ -404,7 +402,7 @@ cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& mlo, const CUtenso
     attr = sm;
   }
   const int grid = (int)std::min<long long>(p.items, 152);
-  conv_tc_kernel<<<grid, 192, sm, s>>>(mlo, mhi, a, p, status);
+  conv_tc_kernel<<<grid, 192, sm, s>>>(xmap, a, p, status);
   return cudaGetLastError();
 }
 

@@ -28,14 +28,12 @@ struct WgradArgs {
 int wgrad_blocks();
 size_t wgrad_partial_floats();
 int mse_blocks();
-// TMA box of the tensor-core convolution's input maps for a D x H x W
-// volume: the activation viewed as [D][H][W][16] BF16 with only 8 channels
-// (one 16-byte half) per voxel in the box, innermost first (8 channels, x,
-// y, z); one map starts at channel 0, the other at channel 8.  No swizzle,
-// zero fill outside.
+// TMA box of the tensor-core convolution's input map for a D x H x W
+// volume: one halo plane of a row block, the activation viewed as
+// [D][H][W][16] BF16 (innermost first: 16 channels, x, y, z), 32-byte
+// swizzle, zero fill outside.
 void conv_halo_box(int D, int H, int W, unsigned (&box)[4]);
-cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& mlo, const CUtensorMap& mhi,
-                        int* status, cudaStream_t s);
+cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& xmap, int* status, cudaStream_t s);
 // Boxes of the weight-gradient kernel's maps over x (halo) and gy (tile),
 // [D][H][W][16] BF16, 32-byte swizzle.
 void conv_wgrad_halo_box(unsigned (&box)[4]);

@@ -5,23 +5,25 @@
 //
 // Formulation.  A CTA owns a block of RY output rows (y) of an x segment of
 // SW voxels and marches over a chunk of z planes.  Each halo plane of the
-// block (rows y0-1 .. , x from xs-1, width P = SW + 2) is stored as two
-// "channel-half planes" [half][row][x][8 channels], 16 bytes per voxel and
-// half, which is exactly the K-major no-swizzle canonical layout of a
-// tcgen05 operand: 8 consecutive voxels x 16 bytes form one core matrix.
-// Output voxels are numbered f = ry * P + xx over the block (xx in [0, P):
-// the last two columns of every row are junk and never stored), so the A
-// rows of tap (dz, dy, dx) for the 128 outputs f0 .. f0+127 are the 128
-// consecutive halo voxels starting at f0 + dy P + dx of halo plane z + dz:
-// one shared-memory descriptor (start, K stride = half-plane bytes, M stride
-// = 128 bytes) per tap and chunk, no data movement.  Per output plane:
-// NCH chunks x 27 taps of tcgen05.mma.kind::f16 M=128 N=16 K=16 (bf16 in,
-// f32 accumulate) into NCH x 16 TMEM columns; the epilogue warps read one
-// voxel's 16 output channels per thread with tcgen05.ld and store 32 (bf16)
-// or 64 (f32) contiguous bytes.
+// block (rows y0-1 .., x from xs-1, width P = SW + 2) arrives by one TMA
+// load with the 32-byte swizzle: 32 bytes (16 channels) per voxel, the two
+// 16-byte channel halves of a voxel swapped when bit 7 of its shared-memory
+// address is set.  That is the K-major SWIZZLE_32B operand layout of
+// tcgen05 (one 32-byte row per M row, 8-row groups 256 bytes apart), with
+// the swizzle taken on absolute shared-memory addresses by both the copy
+// and the tensor core.  Output voxels are numbered f = ry * P + xx over the
+// block (xx in [0, P): the last two columns of every row are junk and never
+// stored), so the A rows of tap (dz, dy, dx) for the 128 outputs
+// f0 .. f0+127 are the 128 consecutive halo voxels starting at
+// f0 + dy P + dx of halo plane z + dz: one descriptor per tap and chunk, no
+// data movement.  Per output plane: NCH chunks x 27 taps of
+// tcgen05.mma.kind::f16 M=128 N=16 K=16 (bf16 in, f32 accumulate) into
+// NCH x 16 TMEM columns; the epilogue warps read one voxel's 16 output
+// channels per thread with tcgen05.ld and store 32 (bf16) or 64 (f32)
+// contiguous bytes.
 //
 // Warp roles (192 threads): warp 0 lane 0 issues the TMA loads of halo
-// planes into a ring of 4 slots; warp 1 allocates TMEM and lane 0 issues
+// planes into a ring of slots; warp 1 allocates TMEM and lane 0 issues
 // the MMAs; warps 2-5 (TMEM lane quarters 2, 3, 0, 1) run the epilogue from
 // a double-buffered accumulator.  Every wait is bounded; a timeout sets the
 // status flag and a CTA-wide abort flag that ends every role's loop.
@@ -35,7 +37,7 @@ struct TcPlan {
   int P, SW, RY, NCH, rows, ZC, ring;
   int nxs, nyb, nzc;
   long long items;
-  int half_bytes, slot_bytes;  // shared memory of one channel half / slot
+  int slot_bytes;  // shared memory of one halo plane (multiple of 1024)
 };
 
 __device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols) {
@@ -103,12 +105,15 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor, no swizzle: start address, leading
-// (K-direction core-matrix) byte offset, stride (M/N-direction 8-row group)
-// byte offset, descriptor version 1 (bits 46-47).
-__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor: start address (bits 0-13, address >> 4),
+// leading byte offset (bits 16-29, >> 4; unused when K fits one swizzle
+// row), stride byte offset between 8-row groups (bits 32-45, >> 4),
+// descriptor version 1 (bits 46-47), layout (bits 61-63: 0 none, 6 32-byte
+// swizzle).
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo,
+                                             uint32_t layout = 0) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
 }
 
 // Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16
@@ -130,10 +135,10 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* sta
 }
 
 __global__ void __launch_bounds__(192, 1)
-    conv_tc_kernel(const __grid_constant__ CUtensorMap mlo, const __grid_constant__ CUtensorMap mhi,
-                   ConvArgs a, TcPlan pl, int* status) {
+    conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, ConvArgs a, TcPlan pl, int* status) {
   extern __shared__ unsigned char tc_raw[];
-  unsigned char* sm = tc_raw + ((128 - (smem_u32(tc_raw) & 127)) & 127);
+  // the 32-byte swizzle acts on address bits 4 and 7: slots on 1024 bytes
+  unsigned char* sm = tc_raw + ((1024 - (smem_u32(tc_raw) & 1023)) & 1023);
   unsigned char* slots = sm;                               // ring x slot_bytes
   unsigned char* wts = sm + pl.ring * pl.slot_bytes;       // [27][k half][16 out][8 in] bf16
   __shared__ uint64_t full[kTcMaxRing], empty[kTcMaxRing], tfull[2], tempty[2], done_bar;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) {
     // ---- producer: halo planes z0 - 1 .. z0 + nz of each item, in order
     if (lane == 0) {
-      const uint32_t tx = 2u * 16u * (uint32_t)pl.P * (uint32_t)pl.rows;
+      const uint32_t tx = 32u * (uint32_t)pl.P * (uint32_t)pl.rows;
       uint32_t q = 0;
       for (long long it = blockIdx.x; it < pl.items && !*ab; it += gridDim.x) {
         int xs, y0, z0, nz;
@@ -192,8 +197,7 @@ __global__ void __launch_bounds__(192, 1)
           if (!tc_wait(&empty[s], ((q / pl.ring) & 1) ^ 1, status, ab)) break;
           unsigned char* dst = slots + (size_t)s * pl.slot_bytes;
           mbar_arrive_expect_tx(&full[s], tx);
-          tma_load_4d(dst, &mlo, 0, xs - 1, y0 - 1, z0 - 1 + h, &full[s]);
-          tma_load_4d(dst + pl.half_bytes, &mhi, 0, xs - 1, y0 - 1, z0 - 1 + h, &full[s]);
+          tma_load_4d(dst, &xmap, 0, xs - 1, y0 - 1, z0 - 1 + h, &full[s]);
         }
       }
       if (*ab)  // let issued loads land before the CTA exits
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(192, 1)
           // as its products are done, so its slot refills while the newer
           // planes' products run, and the newest plane is needed last.
           const uint64_t b0 = tc_sdesc(wbase, 256u, 128u);
-          const uint64_t rowoff[3] = {0ull, (uint64_t)pl.P, 2ull * (uint64_t)pl.P};
+          const uint64_t rowoff[3] = {0ull, 2ull * (uint64_t)pl.P, 4ull * (uint64_t)pl.P};
           bool ok = true;
 #pragma unroll
           for (int dz = 0; dz < 3; ++dz) {
@@ -225,16 +229,16 @@ __global__ void __launch_bounds__(192, 1)
             if (!(ok = tc_wait(&full[q % pl.ring], (q / pl.ring) & 1, status, ab))) break;
             tc_fence_after();
             // start-address field (address >> 4) advanced by
-            // chunk * 128 + dy * P + dx voxels of 16 bytes
-            const uint64_t a0 = tc_sdesc(sbase + (q % pl.ring) * (uint32_t)pl.slot_bytes,
-                                         (uint32_t)pl.half_bytes, 128u);
+            // chunk * 128 + dy * P + dx voxels of 32 bytes (2 units each)
+            const uint64_t a0 = tc_sdesc(sbase + (q % pl.ring) * (uint32_t)pl.slot_bytes, 16u,
+                                         256u, 6u);
             for (int c = 0; c < pl.NCH; ++c) {
               const uint32_t d = tmem + (uint32_t)(buf * 128 + c * 16);
-              const uint64_t ac = a0 + (uint64_t)c * 128u;
+              const uint64_t ac = a0 + (uint64_t)c * 256u;
 #pragma unroll
               for (int t9 = 0; t9 < 9; ++t9) {
                 const int dy = t9 / 3, dx = t9 % 3;
-                tc_mma(d, ac + rowoff[dy] + (uint64_t)dx, b0 + (uint64_t)(dz * 9 + t9) * 32u,
+                tc_mma(d, ac + rowoff[dy] + 2ull * (uint64_t)dx, b0 + (uint64_t)(dz * 9 + t9) * 32u,
                        kTcIdesc, (dz | t9) != 0);
               }
             }
