@@ -19,13 +19,13 @@ constexpr int kPP = 4;        // consecutive points per thread
 constexpr int kChunk = 8;     // frequency bins per warp
 constexpr int kMaxWarps = 16;
 
-// Twiddles W[t][k] = exp(-2 pi i bins[k] (n0 + t) / nf) for one time block,
-// rows padded to nbp bins with zeros.
-__global__ void twiddle_kernel(int T, int n0, int nf, const int* __restrict__ bins, int nb, int nbp,
-                               float2* __restrict__ W) {
+// Twiddles exp(-2 pi i bins[k] (n0 + t) / nf) for one time block, laid out
+// [group][t][k'] with k = group * nbh + k' (zeros beyond nb).
+__global__ void twiddle_kernel(int T, int n0, int nf, const int* __restrict__ bins, int nb,
+                               int groups, int nbh, float2* __restrict__ W) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= T * nbp) return;
-  const int t = i / nbp, k = i % nbp;
+  if (i >= groups * T * nbh) return;
+  const int grp = i / (T * nbh), t = (i / nbh) % T, k = grp * nbh + i % nbh;
   if (k >= nb) {
     W[i] = make_float2(0.0f, 0.0f);
     return;
@@ -45,8 +45,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
-// acc[k][x] += sum_t V[t][x] W[t][k], persistent over blocks of kPts points.
-// The T x nbp twiddles are loaded once per CTA; the T x kPts samples of the
+// acc[k][x] += sum_t V[t][x] W[t][k], persistent over blocks of kPts points;
+// blockIdx.y selects a group of bins (the bins are split over 1 or 2 CTAs
+// per block of points so that two CTAs fit on an SM and one computes while
+// the other loads or stores its accumulators).
+// The T x nbh twiddles of the group are loaded once per CTA; the T x kPts samples of the
 // next block arrive by bulk copies (one per sample row) into the other half
 // of a double buffer while this block is accumulated.  Warp c owns bins
 // [c kChunk, (c+1) kChunk) and lane g points 4g..4g+3, so per sample a
@@ -61,7 +64,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
   extern __shared__ float4 sm4[];
   __shared__ uint64_t bar[3];  // [0] twiddles, [1 + b] samples of buffer b
   __shared__ int abort_flag;
-  const int nbp = (blockDim.x / 32) * kChunk;
+  const int nbp = (blockDim.x / 32) * kChunk;     // bins of this CTA's group
+  const int kbase = blockIdx.y * nbp;
+  W += (size_t)blockIdx.y * T * nbp;
   float2* Ws = reinterpret_cast<float2*>(sm4);   // [T][nbp]
   float* Vs = reinterpret_cast<float*>(Ws + T * nbp);  // [2][T][kPts]
   const long long nblk = (N + kPts - 1) / kPts;
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
     float ar[kPP][kChunk], ai[kPP][kChunk];
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) {
-      const int k = c * kChunk + j;
+      const int k = kbase + c * kChunk + j;
       if (VEC) {
         float4 rv = make_float4(0.f, 0.f, 0.f, 0.f), mv = rv;
         if (live && k < nb) {  // xb + 3 < N as N is a multiple of 4
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
     if (live) {
 #pragma unroll
       for (int j = 0; j < kChunk; ++j) {
-        const int k = c * kChunk + j;
+        const int k = kbase + c * kChunk + j;
         if (k >= nb) continue;
         if (VEC) {
           *reinterpret_cast<float4*>(re + (long long)k * N + xb) =
@@ -223,8 +228,18 @@ int blocks_for(long long n) {
 
 int dft_padded_bins(int nb) { return ((nb + kChunk - 1) / kChunk) * kChunk; }
 
+// Bins split over groups of CTAs: 2 groups above 64 bins, so that a CTA
+// needs at most 8 warps and two CTAs fit on an SM.
+static void dft_groups(int nb, int& groups, int& nbh) {
+  const int nbp = dft_padded_bins(nb);
+  groups = nbp > 64 ? 2 : 1;
+  nbh = dft_padded_bins((nbp + groups - 1) / groups);
+}
+
 size_t dft_smem_bytes(int T, int nb) {
-  return sizeof(float2) * T * dft_padded_bins(nb) + sizeof(float) * 2 * T * kPts;
+  int groups, nbh;
+  dft_groups(nb, groups, nbh);
+  return sizeof(float2) * T * nbh + sizeof(float) * 2 * T * kPts;
 }
 
 int dft_max_bins() { return kMaxWarps * kChunk; }
@@ -233,8 +248,10 @@ cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const
                        float2* W, float* re, float* im, int* status, cudaStream_t s) {
   if (T <= 0 || N <= 0) return cudaSuccess;
   if (nb < 1 || nb > dft_max_bins()) return cudaErrorInvalidValue;
-  const int nbp = dft_padded_bins(nb);
-  twiddle_kernel<<<(T * nbp + 255) / 256, 256, 0, s>>>(T, n0, nf, bins, nb, nbp, W);
+  int groups, nbh;
+  dft_groups(nb, groups, nbh);  // groups * nbh <= dft_max_bins()
+  twiddle_kernel<<<(groups * T * nbh + 255) / 256, 256, 0, s>>>(T, n0, nf, bins, nb, groups, nbh,
+                                                                W);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t sm = dft_smem_bytes(T, nb);
@@ -247,13 +264,15 @@ cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const
     if (e != cudaSuccess) return e;
     attr[vec] = sm;
   }
-  const int threads = 32 * (nbp / kChunk);
+  const int threads = 32 * (nbh / kChunk);
   int per_sm = 1;
   e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_kernel<true>, threads, sm)
           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_kernel<false>, threads, sm);
   if (e != cudaSuccess) return e;
   const long long nblk = (N + kPts - 1) / kPts;
-  const unsigned grid = (unsigned)std::min<long long>(nblk, 152LL * std::max(per_sm, 1));
+  const dim3 grid(
+      (unsigned)std::min<long long>(nblk, std::max(1LL, 152LL * std::max(per_sm, 1) / groups)),
+      (unsigned)groups);
   if (vec)
     dft_kernel<true><<<grid, threads, sm, s>>>(V, N, T, nb, W, re, im, status);
   else
