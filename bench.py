@@ -211,9 +211,19 @@ def run_gradient_bench(args):
               aperture=w.aperture)
     grad = torch.empty_like(vinit)
 
+    tiles = None
+    if args.autotune:  # measured adjoint decomposition (outside the timed region)
+        from paper_2502_12350_gb300 import autotune
+        # tune with the storage mode the full run takes: every term kept for
+        # the single shot (134 GB fits), checkpointing for the 64-shot batch
+        ns = args.snapshots if args.snapshots != 0 else (
+            -1 if args.workload == "gradient_single" else 16)
+        tiles = autotune.tune_gradient(ctx, g, vinit, None, w.src_xyz, w.wavelet, w.rec_offset,
+                                       w.rec_xyz, dobs, aperture=w.aperture, n_snapshots=ns)
+
     def step():
         return ctx.gradient(g, vinit, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs,
-                            grad, aperture=w.aperture, n_snapshots=args.snapshots)
+                            grad, aperture=w.aperture, n_snapshots=args.snapshots, tiles=tiles)
 
     for _ in range(args.warmup):
         step()
@@ -242,6 +252,7 @@ def run_gradient_bench(args):
             "data": "synthetic",
             "config": {"workload": w.name, "shots": w.n_src, "nt": w.nt,
                        "points_per_step": int(sum(pts_shot)), "snapshots": args.snapshots,
+                       "tiles": tiles if tiles is not None else "cost model",
                        "step_launches_per_gradient": steps_per_call},
             "gpt_updates_per_s": sum(pts_shot) * steps_per_call / (ms / 1e3) / 1e9,
             "misfit": J, "gpu_launches": int(launches), "clocks": clk.summary()}
@@ -389,6 +400,8 @@ def main():
                              "gn_labels"],
                     help="model: the headline modelling benchmark; gradient_*: FWI gradient "
                          "shots/s on the 256^3 single-shot or the 64-shot aperture workload")
+    ap.add_argument("--autotune", action="store_true",
+                    help="gradient workloads: measured adjoint decomposition (autotune.py)")
     ap.add_argument("--snapshots", type=int, default=0,
                     help="gradient workloads: revolve slots (0 = from free memory, -1 = all)")
     args = ap.parse_args()

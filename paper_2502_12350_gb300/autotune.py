@@ -1,9 +1,9 @@
 """Measured choice of the time-step kernels' work decomposition.
 
 For a problem shape the autotuner times candidate (tile width, height,
-z blocks) decompositions of the forward (and, for gradients, adjoint)
-kernels with the library's own CUDA-event timing hook over a short run, and
-keeps the fastest.  Results are cached in a JSON file (MAMUTE_AUTOTUNE_CACHE,
+z blocks) decompositions of the forward kernel (tune_model) or of the
+adjoint kernel (tune_gradient) with the library's own CUDA-event timing
+hook over a short run, and keeps the fastest.  Results are cached in a JSON file (MAMUTE_AUTOTUNE_CACHE,
 default ~/.cache/mamute/tiles.json) keyed by the padded window shape, the
 number of shots, density and the kernel, and passed to the library through
 the `tiles` option (the numerical result does not depend on the choice).
@@ -92,5 +92,47 @@ def tune_model(ctx, grid, vel, rho, src_xyz, wavelet, rec_offset, rec_xyz, seis,
                 best = (t, tiles)
     c = _load()
     c[k] = {"tiles": best[1], "ms_per_step": best[0]}
+    _store(c)
+    return best[1]
+
+
+def tune_gradient(ctx, grid, vel, rho, src_xyz, wavelet, rec_offset, rec_xyz, d_obs, aperture=None,
+                  n_snapshots=-1, steps=24, candidates=None):
+    """Fastest adjoint decomposition for mamute_gradient on this problem
+    (forward left to the library's cost model), timed over whole gradients
+    of `steps` steps with the given storage mode, cached; returns the
+    `tiles` option to pass."""
+    c = _load()
+    k = key(grid, len(src_xyz), rho is not None, f"adj{n_snapshots}", aperture)
+    if k in c:
+        return c[k]["tiles"]
+    lib = ctx.lib
+    lib.mamute_ctx_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mamute_ctx_last_timing.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_longlong)]
+    lib.mamute_ctx_set_timing(ctx._h, 1)
+    short = mamute.make_grid(grid.nx, grid.ny, grid.nz, grid.border, grid.h, grid.dt, steps,
+                             (grid.ox, grid.oy, grid.oz), grid.cerjan)
+    import torch
+    dobs = d_obs[:, :steps].contiguous()
+    grad = torch.empty_like(vel)
+    best = None
+    for tx, ty in (candidates or SHAPES):
+        for zs in ZSPLITS:
+            tiles = [0, 0, 0, tx, ty, zs]
+            try:
+                for _ in range(2):
+                    ctx.gradient(short, vel, rho, src_xyz, wavelet[:steps], rec_offset, rec_xyz,
+                                 dobs, grad, aperture=aperture, n_snapshots=n_snapshots,
+                                 tiles=tiles)
+            except mamute.MamuteError:
+                continue
+            ms = ctypes.c_double()
+            lib.mamute_ctx_last_timing(ctx._h, ctypes.byref(ms), None, None)
+            if best is None or ms.value < best[0]:
+                best = (ms.value, tiles)
+    c = _load()
+    c[k] = {"tiles": best[1], "ms_per_gradient": best[0]}
     _store(c)
     return best[1]
