@@ -188,24 +188,37 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
-// Fixed-order sum of the per-CTA partials: gw [27][16][16], gb [16].
-__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int n_parts,
-                                    float* __restrict__ gw, float* __restrict__ gb) {
+// Fixed-order sum of the per-CTA partials in two stages: groups of
+// kRedGroup partials (in order, FP64) into stage[g][i], then the groups (in
+// order) into gw [27][16][16] and gb [16].
+constexpr int kRedGroup = 16;
+
+__global__ void wgrad_reduce1_kernel(const float* __restrict__ partial, int n_parts,
+                                     double* __restrict__ stage) {
   const int n = kTaps * kC * kC + kC;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    int p = 0;
-    for (; p + 8 <= n_parts; p += 8) {  // 8 loads in flight, summed in order
-      float v[8];
+  const int g = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p0 = g * kRedGroup, p1 = min(n_parts, p0 + kRedGroup);
+  float v[kRedGroup];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = partial[(long long)(p + j) * n + i];
+  for (int j = 0; j < kRedGroup; ++j)
+    v[j] = p0 + j < p1 ? partial[(long long)(p0 + j) * n + i] : 0.0f;
+  double s = 0.0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) s += v[j];
-    }
-    for (; p < n_parts; ++p) s += partial[(long long)p * n + i];
-    if (i < kTaps * kC * kC) gw[i] = (float)s;
-    else gb[i - kTaps * kC * kC] = (float)s;
-  }
+  for (int j = 0; j < kRedGroup; ++j) s += v[j];
+  stage[(long long)g * n + i] = s;
+}
+
+__global__ void wgrad_reduce2_kernel(const double* __restrict__ stage, int n_groups,
+                                     float* __restrict__ gw, float* __restrict__ gb) {
+  const int n = kTaps * kC * kC + kC;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int g = 0; g < n_groups; ++g) s += stage[(long long)g * n + i];
+  if (i < kTaps * kC * kC) gw[i] = (float)s;
+  else gb[i - kTaps * kC * kC] = (float)s;
 }
 
 // Forward and input-gradient BF16 weights from FP32 masters [27][o][i]:
@@ -313,7 +326,11 @@ cudaError_t launch_features(long long N, const float* vel, const float* ph, cons
 }
 
 int wgrad_blocks() { return 152 * 2; }
-size_t wgrad_partial_floats() { return (size_t)wgrad_blocks() * (kTaps * kC * kC + kC); }
+// per-CTA partials, then the FP64 group sums of the two-stage reduction
+size_t wgrad_partial_floats() {
+  const size_t n = kTaps * kC * kC + kC;
+  return (size_t)wgrad_blocks() * n + 2 * (size_t)((wgrad_blocks() + kRedGroup - 1) / kRedGroup) * n;
+}
 int mse_blocks() { return 152 * 4; }
 
 void conv_wgrad_halo_box(unsigned (&box)[4]) {
@@ -422,7 +439,12 @@ cudaError_t launch_wgrad(const WgradArgs& a, const CUtensorMap& xmap, const CUte
   conv_wgrad_kernel<<<grid, 256, 2 * kWStage + 256, s>>>(xmap, gmap, a, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  wgrad_reduce_kernel<<<(kTaps * kC * kC + kC + 63) / 64, 64, 0, s>>>(a.partial, grid, gw, gb);
+  const int n = kTaps * kC * kC + kC, groups = (grid + kRedGroup - 1) / kRedGroup;
+  double* stage = reinterpret_cast<double*>(a.partial + (size_t)wgrad_blocks() * n);
+  wgrad_reduce1_kernel<<<dim3((n + 127) / 128, groups), 128, 0, s>>>(a.partial, grid, stage);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  wgrad_reduce2_kernel<<<(n + 127) / 128, 128, 0, s>>>(stage, groups, gw, gb);
   return cudaGetLastError();
 }
 
