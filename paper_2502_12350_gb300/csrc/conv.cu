@@ -260,12 +260,15 @@ __global__ void mse_kernel(long long N, const float* __restrict__ out, const flo
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0] * inv_n;
 }
 
+// Fixed-order sum of n partials by one warp: lane l adds its contiguous
+// chunk in order, then the lanes combine in a fixed butterfly.
 __global__ void sum_kernel(const double* partial, int n, double* out) {
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += partial[i];
-    *out = s;
-  }
+  const int l = threadIdx.x, chunk = (n + 31) / 32;
+  double s = 0.0;
+  for (int i = l * chunk; i < min(n, (l + 1) * chunk); ++i) s += partial[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (l == 0) *out = s;
 }
 
 // Adam (Kingma and Ba 2015) with bias correction, FP32 master weights.
