@@ -16,7 +16,9 @@
 //  * Sec. 2.1 absorbing boundary by damping (Cerjan): sponge of `border` cells
 //    padded outside the model on all six faces; per-axis profile
 //    g(d) = exp(-(alpha d)^2), d = depth into the sponge (1..border); the 3-D
-//    factor is the product of the three axis profiles.  The update is
+//    factor is the product of the three axis profiles.  Parity unpinned: the
+//    value alpha = 0.015 (Cerjan's; the paper gives none) -- only alpha = 0
+//    (no damping, energy conserved) is pinned.  The update is
 //    u^{n+1} = g (B u^n - g u^{n-1} + A lap u^n) + source, A = c^2 dt^2,
 //    B = 2 - A m2.
 //  * The wavefield is zero outside the padded grid (Dirichlet).  c and rho are
