@@ -7,7 +7,7 @@
 // benchmark may load it; the product library never links, loads or calls it,
 // and it shares no source with the CUDA path.
 //
-// Conventions (each is a reading of the paper; the list is kept in the design doc):
+// Conventions (each is a reading of the paper where it is silent or ambiguous):
 //  * Eq. 1 (left): d2p/dt2 = c^2 lap p + S.  Eq. 1 (right): with density,
 //    q = p / sqrt(rho), d2q/dt2 = c^2 (lap q - m2 q) + S / sqrt(rho),
 //    m2 = lap(sqrt rho) / sqrt rho.
