@@ -9,8 +9,12 @@ fused time steps (stencil, sponge, source injection, receiver sampling) and
 the seismogram transpose.  Inputs are resident in HBM before the timed
 region and every array is larger than L2.
 
-Prints one JSON line.  --impl reference times the FP64 oracle on the host
-cores instead (a bounded sample of the same workload).
+Prints one JSON line.  It also carries a "gradient" object: FWI gradient
+shots/s of the 256^3 single-shot workload (2000 steps, automatic storage)
+through mamute_gradient, with its own CUDA-event time, bandwidth over the
+step loop and clocks (the headline value is the modelling number alone).
+--impl reference times the FP64 oracle on the host cores instead (a bounded
+sample of the same workload).
 """
 from __future__ import annotations
 
@@ -134,25 +138,52 @@ def workload(nt=None, kind="model"):
     return synth.forward_density() if nt is None else synth.forward_density(nt=nt)
 
 
-def cpu_oracle_rate(w, steps_lo=2, steps_hi=6):
-    """Oracle Gpt/s on the host cores: full grid, the difference of two runs
-    (steps_hi and steps_lo time steps) so that set-up cancels."""
+def cpu_model() -> str:
+    """Host CPU model name (lscpu, else /proc/cpuinfo), for the baseline line."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_oracle_rate(w, steps_lo=2, steps_hi=6, repeats=1):
+    """Oracle Gpt/s on the host cores: full grid, the difference of runs of
+    steps_hi and steps_lo time steps (so that set-up cancels), median over
+    `repeats` runs of steps_hi against one run of steps_lo."""
     from oracle import oracle
     og = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, steps_hi)
     wav = w.wavelet[:steps_hi].astype(np.float64)
-    t = []
-    for ns in (steps_lo, steps_hi):
+
+    def run(ns):
         og.nt = ns
         t0 = time.perf_counter()
         oracle.model(og, w.vel, w.src_xyz, wav[:ns], w.rec_offset, w.rec_xyz, rho=w.rho)
-        t.append(time.perf_counter() - t0)
-    dt = max(t[1] - t[0], 1e-9)
-    rate = w.n_padded * (steps_hi - steps_lo) / dt / 1e9
+        return time.perf_counter() - t0
+
+    t_lo = run(steps_lo)
+    rates, total = [], t_lo
+    for _ in range(repeats):
+        t_hi = run(steps_hi)
+        total += t_hi
+        rates.append(w.n_padded * (steps_hi - steps_lo) / max(t_hi - t_lo, 1e-9) / 1e9)
+    rate = statistics.median(rates)
     cores = os.cpu_count()
     sample = (f"{steps_hi - steps_lo} time steps of the full {w.padded[2]}x{w.padded[1]}x"
-              f"{w.padded[0]} padded grid (difference of a {steps_hi}-step and a {steps_lo}-step "
-              f"FP64 oracle run), OpenMP over z planes")
-    return rate, cores, sample, sum(t)
+              f"{w.padded[0]} padded grid (a {steps_hi}-step FP64 oracle run minus a "
+              f"{steps_lo}-step one, median of {repeats}), OpenMP over z planes on "
+              f"{cores} cores of {cpu_model()}")
+    return rate, cores, sample, total
 
 
 def run_reference(args):
@@ -184,9 +215,19 @@ def run_reference(args):
     return 0
 
 
-def run_gradient_bench(args):
-    """FWI gradient throughput (shots/s and Gpt-updates/s of forward + adjoint
-    work) through mamute_gradient, on one GPU."""
+GRAD_FWD_BYTES = (16, 4)  # per padded point (u^n, u^{n-1}, A, new level), per interior point (term store)
+GRAD_ADJ_BYTES = (24, 4)  # per padded point (psi levels, A, accumulator read + write), per interior point (term read)
+
+
+def gradient_metrics(workload, steps, warmup, autotune=False, snapshots=0, nt=None):
+    """FWI gradient throughput through mamute_gradient on one GPU: shots/s,
+    Gpt-updates/s of forward + adjoint work, CUDA-event time on the library's
+    stream, and the step loop's bandwidth against the algorithmic bytes of
+    the all-terms mode (each forward step reads u^n, u^{n-1}, A and writes
+    the new level, 16 B per padded point, and stores the imaging term, 4 B
+    per interior point; each adjoint step reads two psi levels and A, writes
+    the new level, reads and writes the accumulator, 24 B per padded point,
+    and reads the stored term, 4 B per interior point)."""
     import ctypes
 
     import torch
@@ -194,10 +235,10 @@ def run_gradient_bench(args):
     from paper_2502_12350_gb300 import build, mamute, synth
     build.build()
     dev = torch.device("cuda", 0)
-    if args.workload == "gradient_single":
-        w = synth.gradient_single() if args.nt is None else synth.gradient_single(nt=args.nt)
+    if workload == "gradient_single":
+        w = synth.gradient_single() if nt is None else synth.gradient_single(nt=nt)
     else:
-        w = synth.batched_shots() if args.nt is None else synth.batched_shots(nt=args.nt)
+        w = synth.batched_shots() if nt is None else synth.batched_shots(nt=nt)
     g = mamute.grid_of(w)
     stream = torch.cuda.current_stream(dev)
     ctx = mamute.Context(0, stream.cuda_stream)
@@ -216,51 +257,84 @@ def run_gradient_bench(args):
     grad = torch.empty_like(vinit)
 
     tiles = None
-    if args.autotune:  # measured adjoint decomposition (outside the timed region)
-        from paper_2502_12350_gb300 import autotune
+    if autotune:  # measured adjoint decomposition (outside the timed region)
+        from paper_2502_12350_gb300 import autotune as at
         # tune with the storage mode the full run takes: every term kept for
         # the single shot (134 GB fits), checkpointing for the 64-shot batch
-        ns = args.snapshots if args.snapshots != 0 else (
-            -1 if args.workload == "gradient_single" else 16)
-        tiles = autotune.tune_gradient(ctx, g, vinit, None, w.src_xyz, w.wavelet, w.rec_offset,
-                                       w.rec_xyz, dobs, aperture=w.aperture, n_snapshots=ns)
+        ns = snapshots if snapshots != 0 else (-1 if workload == "gradient_single" else 16)
+        tiles = at.tune_gradient(ctx, g, vinit, None, w.src_xyz, w.wavelet, w.rec_offset,
+                                 w.rec_xyz, dobs, aperture=w.aperture, n_snapshots=ns)
 
     def step():
         return ctx.gradient(g, vinit, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs,
-                            grad, aperture=w.aperture, n_snapshots=args.snapshots, tiles=tiles)
+                            grad, aperture=w.aperture, n_snapshots=snapshots, tiles=tiles)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches, steps_per_call = 0, 0
+    launches, steps_per_call, loop_ms = 0, 0, []
     with ClockSampler(0) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             J = step()
-            sl, tl = ctypes.c_longlong(), ctypes.c_longlong()
-            lib.mamute_ctx_last_timing(ctx._h, None, ctypes.byref(sl), ctypes.byref(tl))
+            lm, sl, tl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+            lib.mamute_ctx_last_timing(ctx._h, ctypes.byref(lm), ctypes.byref(sl), ctypes.byref(tl))
             launches += tl.value
             steps_per_call = sl.value
+            loop_ms.append(lm.value)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
     if w.aperture is not None:
         pts_shot = [int(a[1] - a[0] + 2 * w.border) * int(a[3] - a[2] + 2 * w.border) *
                     int(w.nz + 2 * w.border) for a in w.aperture]
+        int_shot = [int(a[1] - a[0]) * int(a[3] - a[2]) * int(w.nz) for a in w.aperture]
     else:
         pts_shot = [int(w.n_padded)] * w.n_src
-    line = {"metric": "FWI gradient shots/s", "value": w.n_src / (ms / 1e3), "unit": "shots/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": w.name, "shots": w.n_src, "nt": w.nt,
-                       "points_per_step": int(sum(pts_shot)), "snapshots": args.snapshots,
-                       "tiles": tiles if tiles is not None else "cost model",
-                       "step_launches_per_gradient": steps_per_call},
-            "gpt_updates_per_s": sum(pts_shot) * steps_per_call / (ms / 1e3) / 1e9,
-            "misfit": J, "gpu_launches": int(launches), "clocks": clk.summary()}
+        int_shot = [int(w.nx * w.ny * w.nz)] * w.n_src
+    all_terms = steps_per_call == 2 * w.nt  # one forward and one adjoint launch per step
+    out = {"value": w.n_src / (ms / 1e3), "unit": "shots/s", "ms_per_gradient": ms,
+           "workload": w.name, "shots": w.n_src, "nt": w.nt,
+           "points_per_step": int(sum(pts_shot)), "snapshots": snapshots,
+           "storage": "all imaging terms" if all_terms else "revolve checkpoints",
+           "tiles": tiles if tiles is not None else "cost model",
+           "step_launches_per_gradient": steps_per_call,
+           "gpt_updates_per_s": sum(pts_shot) * steps_per_call / (ms / 1e3) / 1e9,
+           "misfit": J, "gpu_launches": int(launches), "clocks": clk.summary()}
+    if all_terms:
+        peak, peak_kind = _peaks()
+        byts = w.nt * sum(GRAD_FWD_BYTES[0] * p + GRAD_FWD_BYTES[1] * q +
+                          GRAD_ADJ_BYTES[0] * p + GRAD_ADJ_BYTES[1] * q
+                          for p, q in zip(pts_shot, int_shot))
+        lms = statistics.median(loop_ms)
+        ach = byts / (lms / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                           "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
+                           "kernel": "step_kernel<forward+store> and step_kernel<adjoint, stored term>",
+                           "algorithmic_bytes_per_gradient": byts, "loop_ms": lms,
+                           "bytes_per_point": {"forward": list(GRAD_FWD_BYTES),
+                                               "adjoint": list(GRAD_ADJ_BYTES)}}
     ctx.close()
+    return out
+
+
+def run_gradient_bench(args):
+    """FWI gradient throughput (shots/s and Gpt-updates/s of forward + adjoint
+    work) through mamute_gradient, on one GPU."""
+    gm = gradient_metrics(args.workload, args.steps, args.warmup, args.autotune, args.snapshots,
+                          args.nt)
+    line = {"metric": "FWI gradient shots/s", "value": gm["value"], "unit": "shots/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": gm["ms_per_gradient"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {k: gm[k] for k in ("workload", "shots", "nt", "points_per_step",
+                                          "snapshots", "storage", "tiles",
+                                          "step_launches_per_gradient")},
+            "gpt_updates_per_s": gm["gpt_updates_per_s"], "misfit": gm["misfit"],
+            "gpu_launches": gm["gpu_launches"], "clocks": gm["clocks"]}
+    if "roofline" in gm:
+        line["roofline"] = gm["roofline"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -399,6 +473,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--nt", type=int, default=None, help="time steps (default: the workload's 4000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gradient", action="store_true",
+                    help="skip the 256^3 FWI gradient object of the headline line")
     ap.add_argument("--workload", default="model",
                     choices=["model", "model_small", "gradient_single", "gradient_batched", "cnn",
                              "gn_labels"],
@@ -531,11 +607,17 @@ def main():
                      "bytes_per_point": bpp, "kernel_ms": kernel_ms},
         "clocks": clocks,
     }
+    ctx.close()
+    del vel, rho, seis
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_gradient and args.nt is None and args.workload == "model":
+        # FWI gradient throughput of the 256^3 single-shot workload (2000 steps,
+        # automatic storage), timed on its own; the headline value is unchanged.
+        line["gradient"] = gradient_metrics("gradient_single", steps=3, warmup=2)
     if rank == 0 and not args.no_cpu_baseline:
-        r, cores, sample, _ = cpu_oracle_rate(w)
+        r, cores, sample, _ = cpu_oracle_rate(w, 2, 22, repeats=3)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample}
-    ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -78,7 +78,7 @@ typedef struct {
  *                   states may use when n_snapshots == 0 (default 0.8).
  *   n_snapshots     0: automatic: keep the imaging term of every step when
  *                   nt x (interior points) x 4 bytes fits in check_mem of
- *                   the free memory and phess is NULL, else as many revolve
+ *                   the free memory, else as many revolve
  *                   slots as check_mem allows; >0: exactly that many revolve
  *                   slots; -1: keep the imaging term of every step (no
  *                   recomputation).
@@ -285,11 +285,13 @@ int mamute_ctx_dft_timing(const mamute_ctx* ctx, double* dft_ms, long long* dft_
  * for callers that cannot allocate device memory, e.g. because a host
  * framework's caching allocator already holds the device's memory, or because
  * a latency-sensitive loop must not pay for cudaMalloc's implicit
- * synchronisation of the device.  The paper has no counterpart: this is the
- * reduction that mamute_gradient uses for its misfit, with its per-block
- * partial sums kept in a fixed file-scope device array (128 KiB on every
- * device that loads the library, held until the process exits) instead of
- * context scratch.  No context is needed and nothing is allocated or freed.
+ * synchronisation of the device.  The paper has no counterpart: it is the
+ * formula mamute_gradient uses for its misfit, summed in a different order
+ * (16384-sample blocks, then one warp in a fixed order), so the two agree to
+ * rounding, not bit for bit.  Its per-block partial sums are kept in a fixed
+ * file-scope device array (128 KiB on every device that loads the library,
+ * held until the process exits) instead of context scratch.  No context is
+ * needed and nothing is allocated or freed.
  *   d, d_obs   device [n] float32 (any layout, the same for both)
  *   n          number of samples, 0 <= n <= MAMUTE_MISFIT_NOALLOC_MAX_SAMPLES
  *   cuda_stream stream to run on (NULL = legacy default stream); the call

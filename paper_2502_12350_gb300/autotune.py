@@ -11,8 +11,11 @@ the `tiles` option (the numerical result does not depend on the choice).
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import json
 import os
+
+import numpy as np
 
 from . import mamute
 
@@ -43,8 +46,15 @@ def _store(c):
 
 
 def key(grid, n_src, dens, kind, aperture=None):
+    """Cache key of a problem.  Apertures enter through a SHA-1 digest of
+    their int32 bytes, which (unlike Python's per-process salted hash of
+    bytes) is the same in every process, so cached tiles are reused."""
     b = 2 * grid.border
-    ap = "full" if aperture is None else "ap%d" % (hash(bytes(memoryview(aperture))) & 0xffffffff)
+    if aperture is None:
+        ap = "full"
+    else:
+        raw = np.ascontiguousarray(aperture, dtype=np.int32).tobytes()
+        ap = "ap" + hashlib.sha1(raw).hexdigest()[:16]
     return f"{kind}:{grid.nx + b}x{grid.ny + b}x{grid.nz + b}:s{n_src}:d{int(dens)}:{ap}"
 
 

@@ -630,7 +630,9 @@ StepArgs fwd_args(mamute_ctx* ctx, const Plan& P, int n, const float* wavelet, f
   a.wn = wavelet[n];
   a.fout = (float*)ctx->pool[(n + 1) & 1].p;
   a.acc = (float*)ctx->acc.p;
-  a.tstore = (mode == MODE_FWD_STORE) ? (float*)ctx->tstore.p + (size_t)n * P.term_elems : nullptr;
+  a.tstore = (mode == MODE_FWD_STORE || mode == MODE_FWD_STORE_PH)
+                 ? (float*)ctx->tstore.p + (size_t)n * P.term_elems
+                 : nullptr;
   a.rec_ptr = (const int*)ctx->recptr.p;
   a.rec = (const RecEntry*)ctx->rec.p;
   a.dout = dout;
@@ -844,7 +846,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   const int nsnap = opts ? opts->n_snapshots : 0;
   const double frac = (opts && opts->check_mem > 0.f) ? opts->check_mem : 0.8;
   bool all_mode = nsnap < 0;
-  if (nsnap == 0 && !ph) {
+  if (nsnap == 0) {
     // Automatic: keep every step's imaging term (no recomputation) when the
     // store fits in check_mem of the free memory, else revolve.
     size_t fr = 0, tot = 0;
@@ -897,8 +899,8 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     cudaGetLastError();
     slots = slots * 3 / 4;
   }
-  const int fmode_first = all_mode ? MODE_FWD_STORE : (ph ? MODE_FWD_PH : MODE_FWD);
-  if (all_mode && ph) return fail(ctx, MAMUTE_EINVAL, "phess is not available with n_snapshots = -1");
+  const int fmode_first = all_mode ? (ph ? MODE_FWD_STORE_PH : MODE_FWD_STORE)
+                                    : (ph ? MODE_FWD_PH : MODE_FWD);
   // Buffers of the forward state: the two working pools (slot -1) or the two
   // halves of a checkpoint slot.  A restore only switches the state to the
   // slot's halves; the next step reads them through the slot's own maps and

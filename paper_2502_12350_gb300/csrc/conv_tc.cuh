@@ -264,12 +264,19 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
     for (int o = 0; o < kC; ++o) bias[o] = a.bias ? a.bias[o] : 0.f;
     uint32_t p = 0;
-    for (long long it = blockIdx.x; it < pl.items && !*ab; it += gridDim.x) {
+    // Lane 0 waits and reads the abort flag for the warp, so the break and
+    // the tcgen05.ld that follows (a .sync.aligned warp instruction) are
+    // taken by the whole warp together.
+    auto warp_stop = [&]() { return __shfl_sync(0xffffffffu, lane == 0 ? (int)(*ab != 0) : 0, 0) != 0; };
+    for (long long it = blockIdx.x; it < pl.items && !warp_stop(); it += gridDim.x) {
       int xs, y0, z0, nz;
       geom(it, xs, y0, z0, nz);
+      bool ok = true;
       for (int j = 0; j < nz; ++j, ++p) {
         const int buf = (int)(p & 1);
-        if (!tc_wait(&tfull[buf], (p >> 1) & 1, status, ab)) break;
+        int got = 0;
+        if (lane == 0) got = tc_wait(&tfull[buf], (p >> 1) & 1, status, ab) ? 1 : 0;
+        if (!(ok = __shfl_sync(0xffffffffu, got, 0) != 0)) break;
         tc_fence_after();
         const int z = z0 + j;
         for (int c0 = 0; c0 < pl.NCH; c0 += 4) {  // 4 chunks (64 columns) per TMEM load
@@ -320,6 +327,7 @@ __global__ void __launch_bounds__(192, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
       }
+      if (!ok) break;
     }
   }
   tc_fence_before();

@@ -49,12 +49,18 @@ __global__ void partial_kernel(const float* __restrict__ d, const float* __restr
   if (threadIdx.x == 0) scratch[blockIdx.x] = red[0];
 }
 
+// One warp: lane l adds the partials of its contiguous chunk in order, then
+// the lanes combine in a fixed butterfly, so the total does not depend on
+// timing and the partials are read in parallel.
 __global__ void total_kernel(int nb, double* __restrict__ scratch) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < nb; ++k) s += scratch[k];
-    scratch[kMaxPartials] = s;
-  }
+  if (blockIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
+  const int per = (nb + 31) / 32;
+  const int b = lane * per, e = b + per < nb ? b + per : nb;
+  double s = 0.0;
+  for (int k = b; k < e; ++k) s += scratch[k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) scratch[kMaxPartials] = s;
 }
 
 }  // namespace

@@ -14,7 +14,8 @@ bool tile_supported(int tx, int ty) {
 
 static cudaError_t dispatch(const StepArgs& a, int n_items, int max_planes, int tx, int ty,
                             bool dens, int mode, cudaStream_t s, int* occ) {
-  if (mode == MODE_FWD || mode == MODE_FWD_PH || mode == MODE_FWD_STORE)
+  if (mode == MODE_FWD || mode == MODE_FWD_PH || mode == MODE_FWD_STORE ||
+      mode == MODE_FWD_STORE_PH)
     return dispatch_forward(a, n_items, max_planes, tx, ty, dens, mode, s, occ);
   return dispatch_adjoint(a, n_items, max_planes, tx, ty, dens, mode, s, occ);
 }

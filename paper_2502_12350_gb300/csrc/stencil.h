@@ -14,6 +14,7 @@ enum StepMode {
   MODE_ADJ = 3,
   MODE_ADJ_STORED = 4,
   MODE_ADJ_TERM = 5,
+  MODE_FWD_STORE_PH = 6,
 };
 
 struct StepArgs {

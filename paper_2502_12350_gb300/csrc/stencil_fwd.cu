@@ -1,4 +1,5 @@
-// Instantiations of the forward time-step kernel (modes FWD, FWD_PH, FWD_STORE).
+// Instantiations of the forward time-step kernel (modes FWD, FWD_PH, FWD_STORE,
+// FWD_STORE_PH).
 #include "stencil_impl.cuh"
 
 namespace mamute {
@@ -21,6 +22,12 @@ cudaError_t dispatch_forward(const StepArgs& a, int n_items, int max_planes, int
     case MODE_FWD_STORE:
 #define MAMUTE_T(TX, TY) \
   if (tx == TX && ty == TY) return launch_mode<TX, TY, MODE_FWD_STORE>(a, n_items, max_planes, dens, s, occ);
+      MAMUTE_TILES(MAMUTE_T)
+#undef MAMUTE_T
+      return cudaErrorInvalidValue;
+    case MODE_FWD_STORE_PH:
+#define MAMUTE_T(TX, TY) \
+  if (tx == TX && ty == TY) return launch_mode<TX, TY, MODE_FWD_STORE_PH>(a, n_items, max_planes, dens, s, occ);
       MAMUTE_TILES(MAMUTE_T)
 #undef MAMUTE_T
       return cudaErrorInvalidValue;

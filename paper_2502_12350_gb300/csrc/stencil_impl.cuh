@@ -133,6 +133,7 @@ struct PlaneInfo {
 //   MODE_FWD        forward step
 //   MODE_FWD_PH     forward step + pseudo-Hessian accumulation (acc += (g t)^2)
 //   MODE_FWD_STORE  forward step + store of the imaging term t on the interior
+//   MODE_FWD_STORE_PH  both of the above (all-terms gradient with pseudo-Hessian)
 //   MODE_ADJ        adjoint step + imaging against a recomputed forward field
 //   MODE_ADJ_STORED adjoint step + imaging against the stored imaging term
 // Resident CTAs per SM the register budget is sized for: the adjoint with a
@@ -148,7 +149,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
     step_kernel(const StepArgs a) {
   constexpr bool ADJ = (MODE == MODE_ADJ || MODE == MODE_ADJ_STORED || MODE == MODE_ADJ_TERM);
   constexpr bool RECOMP = (MODE == MODE_ADJ);
-  constexpr bool ACC = (MODE == MODE_FWD_PH || MODE == MODE_ADJ || MODE == MODE_ADJ_STORED);
+  constexpr bool ACC = (MODE == MODE_FWD_PH || MODE == MODE_FWD_STORE_PH || MODE == MODE_ADJ ||
+                       MODE == MODE_ADJ_STORED);
   constexpr bool TERM = (MODE == MODE_ADJ_STORED);  // stored imaging term as a centre array
   using LY = Layout<TX, TY, ADJ, RECOMP>;
   constexpr int NCT = LY::NCT, HS = LY::HS, CS = LY::CS, NSU = LY::NSU, NSC = LY::NSC;
@@ -219,18 +221,36 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
       if (TERM) tmap_acquire(mapT);
       const int nu = npl + 2 * kHalo;
       const int cx = V.cx0 + x0, cy = V.cy0 + y0;
+      int nF = 0, nC = 0;  // loads issued into the halo and centre rings
+      // After a wait runs out: let every load already issued land before the
+      // CTA exits (bulk copies must not target the shared memory of a CTA
+      // that has finished).  Stage s of a ring holds loads s, s + depth, ...;
+      // the last one issued into it completes phase (count - 1).
+      auto drain = [&]() {
+        for (int s = 0; s < NSU && s < nF; ++s)
+          mbar_wait(&fullF[s], (uint32_t)(((nF - 1 - s) / NSU) & 1), a.status);
+        for (int c = 0; c < NSC && c < nC; ++c)
+          mbar_wait(&fullC[c], (uint32_t)(((nC - 1 - c) / NSC) & 1), a.status);
+      };
       for (int i = 0; i < nu; ++i) {
         const int s = i % NSU, r = i / NSU;
-        if (r > 0 && !mbar_wait(&emptyF[s], (r & 1) ^ 1, a.status)) return;
+        if (r > 0 && !mbar_wait(&emptyF[s], (r & 1) ^ 1, a.status)) {
+          drain();
+          return;
+        }
         const int p = zb - kHalo + i;
         mbar_arrive_expect_tx(&fullF[s], NHALO * HS * 4);
         float* dst = ring + s * NHALO * HS;
         tma_load_3d(dst, mapF, x0 - kHalo, y0 - kHalo, p, &fullF[s]);
         if (RECOMP) tma_load_3d(dst + HS, mapU, x0 - kHalo, y0 - kHalo, p, &fullF[s]);
+        ++nF;
         if (i >= 2 * kHalo) {
           const int j = i - 2 * kHalo, q = zb + j;
           const int c = j % NSC, rc = j / NSC;
-          if (rc > 0 && !mbar_wait(&emptyC[c], (rc & 1) ^ 1, a.status)) return;
+          if (rc > 0 && !mbar_wait(&emptyC[c], (rc & 1) ^ 1, a.status)) {
+            drain();
+            return;
+          }
           mbar_arrive_expect_tx(&fullC[c], NC * CS * 4);
           float* cd = cring + c * NC * CS;
           tma_load_3d(cd + CI_PREV * CS, mapP, x0, y0, q, &fullC[c]);
@@ -240,6 +260,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
           if (TERM)
             tma_load_4d(cd + CI_T * CS, mapT, x0 - V.txoff, y0 - V.border, q - V.border, a.tstep,
                         &fullC[c]);
+          ++nC;
         }
       }
     }
@@ -360,8 +381,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
       }
     }
     // Imaging / accumulation.
-    if (MODE == MODE_FWD_PH || MODE == MODE_FWD_STORE || MODE == MODE_ADJ ||
-        MODE == MODE_ADJ_STORED) {
+    if (MODE == MODE_FWD_PH || MODE == MODE_FWD_STORE || MODE == MODE_FWD_STORE_PH ||
+        MODE == MODE_ADJ || MODE == MODE_ADJ_STORED) {
       F4 t;
       if (MODE == MODE_ADJ) {
         float lu[4];
@@ -374,7 +395,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
 #pragma unroll
         for (int e = 0; e < 4; ++e) t.v[e] = img_term(q[4].v[e], Av.v[e], Mv.v[e], lap[e], DENS);
       }
-      if (MODE == MODE_FWD_STORE) {
+      if (MODE == MODE_FWD_STORE || MODE == MODE_FWD_STORE_PH) {
         const int b = V.border, zi = z - b, yi = gyl - b;
         if (row_ok && col_ok && yi >= 0 && yi < V.nyi && zi >= 0 && zi < V.nzi) {
 #pragma unroll
@@ -385,7 +406,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
                   t.v[e];
           }
         }
-      } else {
+      }
+      if (ACC) {
         const F4 acc = ld4s(cs + CI_ACC * CS);
         F4 nacc;
 #pragma unroll
@@ -433,7 +455,8 @@ template <int TX, int TY, bool DENS, int MODE>
 static size_t smem_bytes_base() {
   constexpr bool ADJ = (MODE == MODE_ADJ || MODE == MODE_ADJ_STORED || MODE == MODE_ADJ_TERM);
   constexpr bool RECOMP = (MODE == MODE_ADJ);
-  constexpr bool ACC = (MODE == MODE_FWD_PH || MODE == MODE_ADJ || MODE == MODE_ADJ_STORED);
+  constexpr bool ACC = (MODE == MODE_FWD_PH || MODE == MODE_FWD_STORE_PH || MODE == MODE_ADJ ||
+                       MODE == MODE_ADJ_STORED);
   using LY = Layout<TX, TY, ADJ, RECOMP>;
   constexpr int NC = 2 + (DENS ? 1 : 0) + (ACC ? 1 : 0) + (MODE == MODE_ADJ_STORED ? 1 : 0);
   return sizeof(float) * (size_t)(LY::NSU * LY::NHALO * LY::HS + LY::NSC * NC * LY::CS + LY::CS) +

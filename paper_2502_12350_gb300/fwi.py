@@ -162,20 +162,29 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
         accepted = None
         for kind in kinds:
             dg = diag_for(kind, x, ph)
-            d = two_loop(g, pairs, dg)
+            # Each kind restarts its own view of the memory when its direction
+            # is not a descent direction, so a rejected learned attempt does
+            # not change the fallback step; the shared memory is cleared only
+            # if the accepted kind restarted it.
+            mem = pairs
+            d = two_loop(g, mem, dg)
             if np.dot(d, g) >= 0:  # not a descent direction: restart the memory
-                pairs = []
-                d = two_loop(g, pairs, dg)
-            alpha = first_step / max(np.abs(d).max(), 1e-30) if not pairs else 1.0
+                mem = []
+                d = two_loop(g, mem, dg)
+            alpha = first_step / max(np.abs(d).max(), 1e-30) if not mem else 1.0
             nb = learned_backtracks if (kind == "learned") else max_backtracks
-            xn, Jn = line_search(d, J, g, x, nb, alpha, expand=not pairs)
+            xn, Jn = line_search(d, J, g, x, nb, alpha, expand=not mem)
             if xn is not None:
                 accepted = (kind, xn, Jn)
+                pairs = mem
                 break
         if accepted is None:
             hist.append((time.perf_counter() - t0, J, "stalled"))
             break
         kind, xn, _ = accepted
+        # The misfit of the accepted point is taken again from the gradient
+        # call: the line search's values come from the allocation-free misfit
+        # reduction, which sums the same residuals in another order.
         Jn, gn, ph = prob.gradient(xn.reshape(shape))
         s, y = xn - x, gn - g
         sy = np.dot(s, y)

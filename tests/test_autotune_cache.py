@@ -2,6 +2,9 @@
 shot counts, density, kernel kinds and apertures, and the JSON cache
 round-trips atomically (no GPU needed)."""
 import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 
@@ -30,3 +33,22 @@ def test_cache_round_trip(tmp_path, monkeypatch):
     assert autotune._load()["fwd:1"]["ms_per_step"] == 0.3
     path.write_text("{not json")
     assert autotune._load() == {}  # a damaged cache is ignored, not fatal
+
+
+def test_aperture_key_stable_across_processes():
+    """The key of an aperture workload is the same in processes with
+    different hash salts (PYTHONHASHSEED), so the cache is reused."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import numpy as np; from paper_2502_12350_gb300 import autotune, mamute; "
+            "g = mamute.make_grid(64, 48, 32, 8, 10.0, 1e-3, 100); "
+            "print(autotune.key(g, 2, False, 'adj-1', np.array([[0, 32, 0, 16], [4, 36, 8, 40]], np.int32)))")
+    keys = set()
+    for seed in ("1", "2", "12345"):
+        env = dict(os.environ, PYTHONHASHSEED=seed, PYTHONPATH=root)
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             check=True, cwd=root).stdout.strip()
+        keys.add(out)
+    assert len(keys) == 1, keys
+    g = mamute.make_grid(64, 48, 32, 8, 10.0, 1e-3, 100)
+    here = autotune.key(g, 2, False, "adj-1", np.array([[0, 32, 0, 16], [4, 36, 8, 40]], np.int32))
+    assert keys == {here}

@@ -171,6 +171,27 @@ def test_gradient_bitwise_identical_across_snapshot_modes(ctx):
         np.testing.assert_array_equal(g, g0)
 
 
+def test_pseudo_hessian_with_all_terms_storage(ctx, oracle):
+    """The pseudo-Hessian is accumulated in the all-terms forward sweep too:
+    with every imaging term kept, the gradient is bitwise the one without
+    the pseudo-Hessian, and P matches the revolve-mode P bitwise and the
+    oracle to 1e-4."""
+    w = _grad_case(True, seed=14, nt=31)
+    dobs = np.zeros((int(w.rec_offset[-1]), w.nt), np.float32)
+    J0, g0 = gpu_gradient(ctx, w, dobs, n_snapshots=-1)
+    ph_all = torch.zeros(w.vel.shape, device="cuda:0")
+    J1, g1 = gpu_gradient(ctx, w, dobs, n_snapshots=-1, phess=ph_all)
+    ph_rev = torch.zeros(w.vel.shape, device="cuda:0")
+    J2, g2 = gpu_gradient(ctx, w, dobs, n_snapshots=3, phess=ph_rev)
+    assert J1 == J0 and J2 == J0
+    np.testing.assert_array_equal(g1, g0)
+    np.testing.assert_array_equal(g2, g0)
+    np.testing.assert_array_equal(ph_all.cpu().numpy(), ph_rev.cpu().numpy())
+    _, ref = oracle.model(ogrid(oracle, w), w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                          rho=w.rho, phess=True)
+    assert rel(ph_all.cpu().numpy(), ref) <= 1e-4
+
+
 def test_automatic_storage_keeps_every_term_when_it_fits(ctx):
     """n_snapshots = 0 on a small grid keeps every imaging term: one forward
     and one adjoint launch per step, and the all-states result."""

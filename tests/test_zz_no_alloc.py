@@ -3,9 +3,9 @@ device memory (a framework allocator already holding the device's memory, or
 a loop that must not pay for cudaMalloc's device-wide synchronisation).
 
 It is called through the C ABI and compared with the misfit that
-mamute_gradient returns for the same modelled and observed data, on two
-calls in a row (the second call reuses the fixed scratch the first one left
-behind).  This file is collected last on purpose."""
+mamute_gradient returns for the same modelled and observed data and with an
+FP64 host sum of the same arrays, on two calls in a row (the second call
+reuses the fixed scratch the first one left behind).  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -58,7 +58,13 @@ def test_noalloc_misfit_matches_gradient_misfit(lib):
                                           d.numel(), ctypes.c_void_p(stream), ctypes.byref(J))
             assert rc == mamute.OK
             assert J.value > 0
+            # the same formula summed in another order: agreement to rounding
             assert abs(J.value - J_ref) <= 1e-9 * J_ref, (trial, J.value, J_ref)
+            # and the definition itself, summed on the host in FP64 from the
+            # FP32 residuals of the same two arrays
+            r32 = d.cpu().numpy() - dobs  # FP32 residual, as on the device
+            J_host = 0.5 * float(np.sum(r32.astype(np.float64) ** 2))
+            assert abs(J.value - J_host) <= 1e-12 * J_host, (trial, J.value, J_host)
     finally:
         ctx.close()
 
