@@ -286,9 +286,10 @@ int mamute_ctx_dft_timing(const mamute_ctx* ctx, double* dft_ms, long long* dft_
  * framework's caching allocator already holds the device's memory, or because
  * a latency-sensitive loop must not pay for cudaMalloc's implicit
  * synchronisation of the device.  The paper has no counterpart: it is the
- * formula mamute_gradient uses for its misfit, summed in a different order
- * (16384-sample blocks, then one warp in a fixed order), so the two agree to
- * rounding, not bit for bit.  Its per-block partial sums are kept in a fixed
+ * formula mamute_gradient uses for its misfit, summed in the same order
+ * (16384-sample blocks over the [n_rec][nt] layout, then one warp in a fixed
+ * order), so for the same arrays the two agree bit for bit.  Its per-block
+ * partial sums are kept in a fixed
  * file-scope device array (128 KiB on every device that loads the library,
  * held until the process exits) instead of context scratch.  No context is
  * needed and nothing is allocated or freed.

@@ -835,7 +835,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   const size_t ncol = std::max(P.ncol, 1);
   CK(ensure(ctx->dint, (size_t)P.nt * ncol * 4));
   CK(ensure(ctx->rint, (size_t)P.nt * ncol * 4));
-  CK(ensure(ctx->partial, (size_t)std::max(data_in_blocks(P.nt, P.ncol), 1) * 8));
+  CK(ensure(ctx->partial, (size_t)std::max(misfit_blocks((long long)P.nt * P.ncol), 1) * 8));
   for (int i = 0; i < 2; ++i) {
     CK(cudaMemsetAsync(ctx->pool[i].p, 0, pool, ctx->stream));
     CK(cudaMemsetAsync(ctx->psi[i].p, 0, pool, ctx->stream));
@@ -975,8 +975,12 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
       CK(aux_count(ctx, launch_data_in((const float*)ctx->dtmp.p, (const int*)ctx->acolmap.p, P.nt, P.ncol,
                         nullptr, -1.0f, (float*)ctx->dint.p, nullptr, nullptr, ctx->stream)));
       CK(aux_count(ctx, launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, (const float*)ctx->dint.p,
-                        1.0f, (float*)ctx->rint.p, (double*)ctx->partial.p, (double*)ctx->misfit.p,
-                        ctx->stream)));
+                        1.0f, (float*)ctx->rint.p, nullptr, nullptr, ctx->stream)));
+      // The misfit is summed over the user's [n_rec][nt] layout, so it does
+      // not depend on the tile shapes of either propagation.
+      ctx->launches += 2;
+      CK(launch_misfit((const float*)ctx->dtmp.p, d_in, (long long)P.nt * P.ncol,
+                       (double*)ctx->partial.p, (double*)ctx->misfit.p, ctx->stream));
     } else {
       CK(aux_count(ctx, launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, nullptr, -1.0f,
                         (float*)ctx->rint.p, nullptr, nullptr, ctx->stream)));

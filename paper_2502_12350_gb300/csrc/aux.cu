@@ -138,6 +138,41 @@ __global__ void data_in_kernel(const float* __restrict__ src, const int* __restr
   }
 }
 
+// Misfit over two arrays in the same layout (the user's [n_rec][nt]): block b
+// reduces samples [b * kMisfitChunk, (b + 1) * kMisfitChunk) into partial[b];
+// the total is then formed by one warp in a fixed order.  Neither depends on
+// the work decomposition of the time-step kernels.
+constexpr long long kMisfitChunk = 16384;
+
+__global__ void misfit_partial_kernel(const float* __restrict__ d, const float* __restrict__ dobs,
+                                      long long n, double* __restrict__ partial) {
+  __shared__ double red[256];
+  const long long b = (long long)blockIdx.x * kMisfitChunk;
+  const long long e = b + kMisfitChunk < n ? b + kMisfitChunk : n;
+  double acc = 0.0;
+  for (long long i = b + threadIdx.x; i < e; i += 256) {
+    const float r = d[i] - dobs[i];
+    acc += 0.5 * (double)r * (double)r;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void warp_total_kernel(const double* __restrict__ partial, int n, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int per = (n + 31) / 32;
+  const int b = lane * per, e = b + per < n ? b + per : n;
+  double s = 0.0;
+  for (int k = b; k < e; ++k) s += partial[k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) *out = s;
+}
+
 __global__ void sum_partials_kernel(const double* partial, int n, double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double s = 0.0;
@@ -235,6 +270,18 @@ cudaError_t launch_data_in(const float* src, const int* colmap, int nt, int ncol
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !total) return e;
   sum_partials_kernel<<<1, 32, 0, s>>>(partial, g.x * g.y, total);
+  return cudaGetLastError();
+}
+
+int misfit_blocks(long long n) { return (int)((n + kMisfitChunk - 1) / kMisfitChunk); }
+
+cudaError_t launch_misfit(const float* d, const float* dobs, long long n, double* partial,
+                         double* total, cudaStream_t s) {
+  if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(double), s);
+  misfit_partial_kernel<<<misfit_blocks(n), 256, 0, s>>>(d, dobs, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  warp_total_kernel<<<1, 32, 0, s>>>(partial, misfit_blocks(n), total);
   return cudaGetLastError();
 }
 

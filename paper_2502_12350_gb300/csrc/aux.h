@@ -54,6 +54,11 @@ int data_in_blocks(int nt, int ncol);
 cudaError_t launch_data_in(const float* src, const int* colmap, int nt, int ncol,
                            const float* d_int, float sign, float* r_int, double* partial,
                            double* total, cudaStream_t s);
+// J = 1/2 sum (d - dobs)^2 over n samples of two arrays in the same layout,
+// FP64 partial sums in fixed blocks and a fixed-order total.
+int misfit_blocks(long long n);
+cudaError_t launch_misfit(const float* d, const float* dobs, long long n, double* partial,
+                         double* total, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 
 }  // namespace mamute

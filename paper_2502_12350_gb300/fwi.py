@@ -112,17 +112,57 @@ def _diag(h, water=0.05):
     return 1.0 / (h + water * h.max())
 
 
+def _save_state(ckpt, it, x, J, g, ph, pairs, hist):
+    arrays = {"x": x, "g": g, "ph": ph.detach().cpu().numpy()}
+    for k, (s, y, _) in enumerate(pairs):
+        arrays[f"s{k}"], arrays[f"y{k}"] = s, y
+    ckpt.save(arrays, {"iteration": it, "J": J, "n_pairs": len(pairs),
+                       "rho": [r for _, _, r in pairs], "history": hist})
+
+
+def _load_state(ckpt, dev):
+    got = ckpt.load()
+    if got is None:
+        return None
+    a, m = got
+    pairs = [(a[f"s{k}"], a[f"y{k}"], m["rho"][k]) for k in range(m["n_pairs"])]
+    ph = torch.from_numpy(a["ph"]).to(dev)
+    hist = [tuple(h) for h in m["history"]]
+    return m["iteration"], a["x"], m["J"], a["g"], ph, pairs, hist
+
+
 def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net=None,
         memory: int = 5, first_step: float = 40.0, learned_backtracks: int = 4,
-        max_backtracks: int = 8, c1: float = 1e-4, water: float = 0.05) -> Result:
+        max_backtracks: int = 8, c1: float = 1e-4, water: float = 0.05,
+        checkpoint: str | None = None, on_iteration=None) -> Result:
     """Projected L-BFGS on the misfit.  first_step (m/s) scales the first
-    direction; later iterations try the unit L-BFGS step first."""
+    direction; later iterations try the unit L-BFGS step first.
+
+    checkpoint: path of an optimizer-state file (resilience.Checkpoint).  The
+    state (model, misfit, gradient, pseudo-Hessian, L-BFGS pairs, iteration,
+    history) is written after every iteration; if the file exists when the
+    run starts, the run resumes from it instead of starting from v0, and a
+    resumed run ends with the same model as an uninterrupted one.
+    on_iteration(it, x, J): called after iteration `it` has been saved."""
     shape = v0.shape
-    x = prob.project(np.asarray(v0, np.float64).ravel())
+    ckpt = None
+    state = None
+    if checkpoint is not None:
+        from .resilience import Checkpoint
+        ckpt = Checkpoint(checkpoint)
+        state = _load_state(ckpt, prob.dev)
     t0 = time.perf_counter()
-    J, g, ph = prob.gradient(x.reshape(shape))
-    hist = [(time.perf_counter() - t0, J, "start")]
-    pairs = []
+    if state is not None:
+        it0, x, J, g, ph, pairs, hist = state
+        x = np.asarray(x, np.float64)
+    else:
+        it0 = 0
+        x = prob.project(np.asarray(v0, np.float64).ravel())
+        J, g, ph = prob.gradient(x.reshape(shape))
+        hist = [(time.perf_counter() - t0, J, "start")]
+        pairs = []
+        if ckpt is not None:
+            _save_state(ckpt, 0, x, J, g, ph, pairs, hist)
 
     def diag_for(kind, x, ph):
         if kind == "none":
@@ -157,7 +197,7 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
             alpha *= 0.5
         return None, None
 
-    for it in range(n_iter):
+    for it in range(it0, n_iter):
         kinds = ["learned", "pseudo"] if precond == "learned" else [precond]
         accepted = None
         for kind in kinds:
@@ -182,9 +222,8 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
             hist.append((time.perf_counter() - t0, J, "stalled"))
             break
         kind, xn, _ = accepted
-        # The misfit of the accepted point is taken again from the gradient
-        # call: the line search's values come from the allocation-free misfit
-        # reduction, which sums the same residuals in another order.
+        # The line search's misfits come from the allocation-free reduction,
+        # which sums the residuals in the same order as the gradient call.
         Jn, gn, ph = prob.gradient(xn.reshape(shape))
         s, y = xn - x, gn - g
         sy = np.dot(s, y)
@@ -193,4 +232,8 @@ def run(prob: Problem, v0: np.ndarray, n_iter: int, precond: str = "pseudo", net
             pairs = pairs[-memory:]
         x, J, g = xn, Jn, gn
         hist.append((time.perf_counter() - t0, J, kind))
+        if ckpt is not None:
+            _save_state(ckpt, it + 1, x, J, g, ph, pairs, hist)
+        if on_iteration is not None:
+            on_iteration(it + 1, x, J)
     return Result(x.reshape(shape), hist, prob.n_grad, prob.n_fwd)

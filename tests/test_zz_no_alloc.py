@@ -58,8 +58,9 @@ def test_noalloc_misfit_matches_gradient_misfit(lib):
                                           d.numel(), ctypes.c_void_p(stream), ctypes.byref(J))
             assert rc == mamute.OK
             assert J.value > 0
-            # the same formula summed in another order: agreement to rounding
+            # the same formula in the same summation order as the gradient's
             assert abs(J.value - J_ref) <= 1e-9 * J_ref, (trial, J.value, J_ref)
+            assert J.value == J_ref, (trial, J.value, J_ref)
             # and the definition itself, summed on the host in FP64 from the
             # FP32 residuals of the same two arrays
             r32 = d.cpu().numpy() - dobs  # FP32 residual, as on the device
