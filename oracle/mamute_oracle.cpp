@@ -46,6 +46,19 @@
 //    function on the same data, so every mode gives bitwise the same result.
 //  * Pseudo-Hessian (optional output): P(x) = sum_shots sum_n
 //    (g (lap - m2) u^n)(x)^2, the squared source-side factor of the Jacobian.
+//  * Free surface (Sec. 2, modelling options; free_surface = 1): the top
+//    model plane (padded plane z_s = border) is a pressure-release surface,
+//    imposed by the image method: the field is odd about z_s, so values at
+//    planes z_s - m are read as -u(z_s + m) and u(z_s) = 0 (g = 0 on z <= z_s,
+//    which also keeps the planes above the surface at zero); the top face
+//    has no sponge.  Sources and receivers on the surface plane are rejected.
+//    The mirrored Laplacian is symmetric on the cells below the surface, so
+//    the adjoint keeps the same form.
+//  * Off-grid points (xyz_interp = 1): trilinear weights over the (up to)
+//    8 nodes around a source or receiver; the source is spread with weights
+//    w_e dt^2 / (dx dy dz sqrt(rho_e)) and a receiver samples
+//    sum_e w_e sqrt(rho_e) u_e (nodes with zero weight, and nodes on a free
+//    surface, are dropped).  xyz_interp = 0 is the nearest node.
 
 #include <cmath>
 #include <cstdint>
@@ -64,10 +77,13 @@ struct Grid {
   int nt;
   double ox, oy, oz;
   double cerjan;  // sponge constant alpha; 0 disables damping (g == 1)
+  int free_surface;  // 1: pressure-release surface at the top model plane
+  int xyz_interp;    // 0: nearest node, 1: trilinear weights
 };
 
 struct Dims {
   long Nx, Ny, Nz;
+  long zs = -1;  // padded plane of the free surface, -1 without one
   long n() const { return Nx * Ny * Nz; }
   long at(long i, long j, long k) const { return (k * Ny + j) * Nx + i; }
 };
@@ -77,20 +93,23 @@ Dims padded(const Grid& g) {
   d.Nx = g.nx + 2L * g.border;
   d.Ny = g.ny + 2L * g.border;
   d.Nz = g.nz + 2L * g.border;
+  d.zs = g.free_surface ? g.border : -1;
   return d;
 }
 
 long clampl(long v, long lo, long hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Per-axis Cerjan profile on the padded axis of length N.
-std::vector<double> sponge_profile(long N, int border, double alpha) {
+// Per-axis Cerjan profile on the padded axis of length N.  With a free
+// surface at plane zs (z axis only) the low face has no sponge and the
+// factor is 0 on and above the surface.
+std::vector<double> sponge_profile(long N, int border, double alpha, long zs = -1) {
   std::vector<double> p(N, 1.0);
   for (long i = 0; i < N; ++i) {
     long d = 0;
-    if (i < border) d = border - i;
+    if (i < border && zs < 0) d = border - i;
     else if (i > N - 1 - border) d = i - (N - 1 - border);
     double a = alpha * (double)d;
-    p[i] = std::exp(-a * a);
+    p[i] = (zs >= 0 && i <= zs) ? 0.0 : std::exp(-a * a);
   }
   return p;
 }
@@ -156,7 +175,7 @@ Medium build_medium(const Grid& gr, const double* vel, const double* rho) {
   }
   std::vector<double> gx = sponge_profile(d.Nx, b, gr.cerjan);
   std::vector<double> gy = sponge_profile(d.Ny, b, gr.cerjan);
-  std::vector<double> gz = sponge_profile(d.Nz, b, gr.cerjan);
+  std::vector<double> gz = sponge_profile(d.Nz, b, gr.cerjan, d.zs);
 #pragma omp parallel for schedule(static)
   for (long k = 0; k < d.Nz; ++k)
     for (long j = 0; j < d.Ny; ++j)
@@ -174,11 +193,17 @@ long node_of(const Grid& gr, const Dims& d, const double* xyz) {
 }
 
 // lap of a wavefield (zero outside the padded grid) at one node, in type T.
+// With a free surface, planes at or above it are read through the odd image.
 template <typename T>
 T lap_field(const Dims& d, const T* u, long i, long j, long k, T ix2, T iy2, T iz2) {
   auto v = [&](long a, long b, long c) -> T {
+    T sign = T(1);
+    if (d.zs >= 0 && c <= d.zs) {
+      c = 2 * d.zs - c;
+      sign = T(-1);
+    }
     if (a < 0 || a >= d.Nx || b < 0 || b >= d.Ny || c < 0 || c >= d.Nz) return T(0);
-    return u[d.at(a, b, c)];
+    return sign * u[d.at(a, b, c)];
   };
   T c0 = (T)kC[0];
   T sx = c0 * v(i, j, k), sy = c0 * v(i, j, k), sz = c0 * v(i, j, k);
@@ -262,11 +287,12 @@ Medium window(const Medium& G, const Grid& gr, int a0, int a1, int a2, int a3) {
   W.d.Nx = (a1 - a0) + 2L * b;
   W.d.Ny = (a3 - a2) + 2L * b;
   W.d.Nz = G.d.Nz;
+  W.d.zs = G.d.zs;
   const long n = W.d.n();
   W.c.resize(n); W.A.resize(n); W.m2.resize(n); W.g.resize(n); W.srho.resize(n);
   std::vector<double> gx = sponge_profile(W.d.Nx, b, gr.cerjan);
   std::vector<double> gy = sponge_profile(W.d.Ny, b, gr.cerjan);
-  std::vector<double> gz = sponge_profile(W.d.Nz, b, gr.cerjan);
+  std::vector<double> gz = sponge_profile(W.d.Nz, b, gr.cerjan, W.d.zs);
   for (long k = 0; k < W.d.Nz; ++k)
     for (long j = 0; j < W.d.Ny; ++j)
       for (long i = 0; i < W.d.Nx; ++i) {
@@ -280,14 +306,20 @@ Medium window(const Medium& G, const Grid& gr, int a0, int a1, int a2, int a3) {
   return W;
 }
 
-struct Shot {
-  long src;                 // padded node of the source
-  double src_scale;         // dt^2 / (dx dy dz sqrt(rho))
-  std::vector<long> rec;    // padded nodes of the receivers
-  std::vector<double> rsc;  // sqrt(rho) at the receivers
+// A source or receiver: padded nodes and their weights (the source weights
+// include dt^2 / (dx dy dz sqrt(rho)), the receiver weights sqrt(rho)).
+struct Point {
+  std::vector<long> node;
+  std::vector<double> w;
 };
 
-// Node of a coordinate in a shot window; -1 outside the model or aperture.
+struct Shot {
+  Point src;
+  std::vector<Point> rec;
+};
+
+// Node of a coordinate in a shot window (nearest node); -1 outside the model
+// or aperture.
 long node_in(const Grid& gr, const Dims& d, const double* xyz, const int* ap) {
   long i = (long)std::floor((xyz[0] - gr.ox) / gr.dx + 0.5);
   long j = (long)std::floor((xyz[1] - gr.oy) / gr.dy + 0.5);
@@ -300,6 +332,52 @@ long node_in(const Grid& gr, const Dims& d, const double* xyz, const int* ap) {
     a2 = ap[2];
   }
   return d.at(i + gr.border - a0, j + gr.border - a2, k + gr.border);
+}
+
+// Nodes and interpolation weights of a coordinate (before the density and
+// source scales): the nearest node with weight 1, or the trilinear weights
+// of the cell that holds the point.  Returns -1 if the point (or one of its
+// nodes with non-zero weight) lies outside the model or aperture, or if all
+// of its weight falls on a free surface.
+int locate(const Grid& gr, const Dims& d, const double* xyz, const int* ap, Point& P) {
+  P.node.clear();
+  P.w.clear();
+  const long a0 = ap ? ap[0] : 0, a2 = ap ? ap[2] : 0;
+  const long lo[3] = {a0, a2, 0};
+  const long hi[3] = {ap ? ap[1] : gr.nx, ap ? ap[3] : gr.ny, gr.nz};
+  if (!gr.xyz_interp) {
+    long p = node_in(gr, d, xyz, ap);
+    if (p < 0) return -1;
+    if (d.zs >= 0 && p / (d.Nx * d.Ny) <= d.zs) return -1;
+    P.node.push_back(p);
+    P.w.push_back(1.0);
+    return 0;
+  }
+  const double o[3] = {gr.ox, gr.oy, gr.oz}, h[3] = {gr.dx, gr.dy, gr.dz};
+  long base[3];
+  double t[3];
+  for (int a = 0; a < 3; ++a) {
+    const double f = (xyz[a] - o[a]) / h[a];
+    base[a] = (long)std::floor(f);
+    t[a] = f - (double)base[a];
+  }
+  for (int c = 0; c < 8; ++c) {
+    long idx[3];
+    double w = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      const int up = (c >> a) & 1;
+      idx[a] = base[a] + up;
+      w *= up ? t[a] : 1.0 - t[a];
+    }
+    if (w == 0.0) continue;
+    for (int a = 0; a < 3; ++a)
+      if (idx[a] < lo[a] || idx[a] >= hi[a]) return -1;
+    const long k = idx[2] + gr.border;
+    if (d.zs >= 0 && k <= d.zs) continue;  // the field is zero on the surface
+    P.node.push_back(d.at(idx[0] + gr.border - a0, idx[1] + gr.border - a2, k));
+    P.w.push_back(w);
+  }
+  return P.node.empty() ? -1 : 0;
 }
 
 // Shot s with its medium (the global one, or its aperture window).
@@ -327,17 +405,29 @@ int make_shot(const Grid& gr, const Medium& G, int s, const double* src_xyz, con
   const Medium& M = *S.M;
   Shot& sh = S.sh;
   sh.rec.clear();
-  sh.rsc.clear();
-  sh.src = node_in(gr, M.d, src_xyz + 3 * s, ap);
-  if (sh.src < 0) return -1;
-  sh.src_scale = gr.dt * gr.dt / (gr.dx * gr.dy * gr.dz * M.srho[sh.src]);
+  if (locate(gr, M.d, src_xyz + 3 * s, ap, sh.src)) return -1;
+  for (size_t e = 0; e < sh.src.node.size(); ++e)
+    sh.src.w[e] *= gr.dt * gr.dt / (gr.dx * gr.dy * gr.dz * M.srho[sh.src.node[e]]);
   for (int r = rec_offset[s]; r < rec_offset[s + 1]; ++r) {
-    long p = node_in(gr, M.d, rec_xyz + 3 * (long)r, ap);
-    if (p < 0) return -1;
-    sh.rec.push_back(p);
-    sh.rsc.push_back(M.srho[p]);
+    Point P;
+    if (locate(gr, M.d, rec_xyz + 3 * (long)r, ap, P)) return -1;
+    for (size_t e = 0; e < P.node.size(); ++e) P.w[e] *= M.srho[P.node[e]];
+    sh.rec.push_back(P);
   }
   return 0;
+}
+
+// Source injection and receiver sampling of one shot.
+template <typename T>
+void inject(std::vector<T>& u, const Point& P, double amount) {
+  for (size_t e = 0; e < P.node.size(); ++e) u[P.node[e]] += (T)(P.w[e] * amount);
+}
+
+template <typename T>
+double sample(const std::vector<T>& u, const Point& P) {
+  double v = 0.0;
+  for (size_t e = 0; e < P.node.size(); ++e) v += P.w[e] * (double)u[P.node[e]];
+  return v;
 }
 
 // Forward modelling of one shot in type T (Algorithm 1, "Forward
@@ -363,8 +453,8 @@ void forward_shot(const Grid& gr, const Dims& d, const Coef<T>& c, const Shot& s
           }
     }
     step<T>(d, c, u0.data(), u1.data());  // u0 <- u^{n+1}
-    u0[sh.src] += (T)(sh.src_scale * wavelet[it]);
-    for (long r = 0; r < nr; ++r) trace[r * gr.nt + it] = sh.rsc[r] * (double)u0[sh.rec[r]];
+    inject(u0, sh.src, wavelet[it]);
+    for (long r = 0; r < nr; ++r) trace[r * gr.nt + it] = sample(u0, sh.rec[r]);
     std::swap(u0, u1);
   }
 }
@@ -499,8 +589,8 @@ int oracle_gradient(const oracle_grid* gr, const double* vel, const double* rho,
       for (int it = 0; it < nt; ++it) {
         if (it % seg == 0) { ck_prev.push_back(u0); ck_cur.push_back(u1); }
         step<double>(d, c, u0.data(), u1.data());
-        u0[sh.src] += sh.src_scale * wavelet[it];
-        for (long r = 0; r < nr; ++r) d_mod[r * nt + it] = sh.rsc[r] * u0[sh.rec[r]];
+        inject(u0, sh.src, wavelet[it]);
+        for (long r = 0; r < nr; ++r) d_mod[r * nt + it] = sample(u0, sh.rec[r]);
         std::swap(u0, u1);
       }
     }
@@ -527,16 +617,16 @@ int oracle_gradient(const oracle_grid* gr, const double* vel, const double* rho,
           states.push_back(u1);  // u^{it}
           if (it + 1 < m1) {
             step<double>(d, c, u0.data(), u1.data());
-            u0[sh.src] += sh.src_scale * wavelet[it];
+            inject(u0, sh.src, wavelet[it]);
             std::swap(u0, u1);
           }
         }
       }
       for (int k = m1; k > m0; --k) {  // lambda^k pairs with u^{k-1}
         adjoint_step(d, c, lam2.data(), lam1.data());  // lam2 <- (B+lap A) g lam1 - g^2 lam2
-        for (long r = 0; r < nr; ++r) lam2[sh.rec[r]] += sh.rsc[r] * res[r * nt + (k - 1)];
+        for (long r = 0; r < nr; ++r) inject(lam2, sh.rec[r], res[r * nt + (k - 1)]);
         std::swap(lam1, lam2);  // lam1 = lambda^k, lam2 = lambda^{k+1}
-        if (dwav) dwav[k - 1] += sh.src_scale * lam1[sh.src];
+        if (dwav) dwav[k - 1] += sample(lam1, sh.src);
         const std::vector<double>& u = states[k - 1 - m0];
 #pragma omp parallel for schedule(static)
         for (long kk = 0; kk < d.Nz; ++kk)
@@ -577,9 +667,10 @@ int oracle_forward_terms(const oracle_grid* gr, const double* vel, const double*
   const Dims& d = M.d;
   const long n = d.n();
   Coef<double> c = coef_of<double>(M, *gr);
-  long src = node_in(*gr, d, src_xyz + 3 * shot, nullptr);
-  if (src < 0) return -1;
-  const double sc = gr->dt * gr->dt / (gr->dx * gr->dy * gr->dz * M.srho[src]);
+  Point src;
+  if (locate(*gr, d, src_xyz + 3 * shot, nullptr, src)) return -1;
+  for (size_t e = 0; e < src.node.size(); ++e)
+    src.w[e] *= gr->dt * gr->dt / (gr->dx * gr->dy * gr->dz * M.srho[src.node[e]]);
   const int b = gr->border;
   const long ni = (long)gr->nx * gr->ny * gr->nz;
   std::vector<double> u0(n, 0.0), u1(n, 0.0);
@@ -592,7 +683,7 @@ int oracle_forward_terms(const oracle_grid* gr, const double* vel, const double*
           a[it * ni + (k * gr->ny + j) * gr->nx + i] = c.g[p] * (l - c.m2[p] * u1[p]);
         }
     step<double>(d, c, u0.data(), u1.data());
-    u0[src] += sc * wavelet[it];
+    inject(u0, src, wavelet[it]);
     std::swap(u0, u1);
   }
   return 0;
@@ -605,13 +696,13 @@ int oracle_cell_response(const oracle_grid* gr, const double* vel, const double*
   Medium M = build_medium(*gr, vel, rho);
   Coef<double> c = coef_of<double>(M, *gr);
   Shot sh;
-  sh.src = M.d.at(ci + gr->border, cj + gr->border, ck + gr->border);
-  sh.src_scale = 1.0;
+  sh.src.node.push_back(M.d.at(ci + gr->border, cj + gr->border, ck + gr->border));
+  sh.src.w.push_back(1.0);
   for (int r = 0; r < n_rec; ++r) {
-    long p = node_in(*gr, M.d, rec_xyz + 3 * r, nullptr);
-    if (p < 0) return -1;
-    sh.rec.push_back(p);
-    sh.rsc.push_back(M.srho[p]);
+    Point P;
+    if (locate(*gr, M.d, rec_xyz + 3 * r, nullptr, P)) return -1;
+    for (size_t e = 0; e < P.node.size(); ++e) P.w[e] *= M.srho[P.node[e]];
+    sh.rec.push_back(P);
   }
   std::vector<double> imp(gr->nt, 0.0);
   imp[0] = 1.0;
@@ -628,14 +719,15 @@ int oracle_receiver_response(const oracle_grid* gr, const double* vel, const dou
   const Dims& d = M.d;
   const long n = d.n();
   Coef<double> c = coef_of<double>(M, *gr);
-  long rp = node_in(*gr, d, rec_xyz1, nullptr);
-  if (rp < 0) return -1;
+  Point rp;
+  if (locate(*gr, d, rec_xyz1, nullptr, rp)) return -1;
+  for (size_t e = 0; e < rp.node.size(); ++e) rp.w[e] *= M.srho[rp.node[e]];
   const int nt = gr->nt, b = gr->border;
   const long ni = (long)gr->nx * gr->ny * gr->nz;
   std::vector<double> lam1(n, 0.0), lam2(n, 0.0);
   for (int k = nt; k >= 1; --k) {
     adjoint_step(d, c, lam2.data(), lam1.data());
-    if (k == nt) lam2[rp] += M.srho[rp];
+    if (k == nt) inject(lam2, rp, 1.0);
     std::swap(lam1, lam2);  // lam1 = lambda^k
     const int j = nt - k;
     for (long kk = 0; kk < gr->nz; ++kk)

@@ -37,7 +37,8 @@ class OGrid(ctypes.Structure):
                 ("border", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("dz", ctypes.c_double), ("dt", ctypes.c_double), ("nt", ctypes.c_int),
                 ("ox", ctypes.c_double), ("oy", ctypes.c_double), ("oz", ctypes.c_double),
-                ("cerjan", ctypes.c_double)]
+                ("cerjan", ctypes.c_double), ("free_surface", ctypes.c_int),
+                ("xyz_interp", ctypes.c_int)]
 
 
 def _load():
@@ -60,9 +61,12 @@ def _f64(a):
 
 
 def make_grid(nx, ny, nz, border, h, dt, nt, origin=(0.0, 0.0, 0.0), cerjan=0.015,
-              spacing=None) -> OGrid:
+              spacing=None, free_surface=0, xyz_interp=0) -> OGrid:
+    """free_surface = 1: pressure-release top model plane (image method);
+    xyz_interp = 1: trilinear sources and receivers (0: nearest node)."""
     dx, dy, dz = spacing if spacing is not None else (h, h, h)
-    return OGrid(nx, ny, nz, border, dx, dy, dz, dt, nt, origin[0], origin[1], origin[2], cerjan)
+    return OGrid(nx, ny, nz, border, dx, dy, dz, dt, nt, origin[0], origin[1], origin[2], cerjan,
+                 int(free_surface), int(xyz_interp))
 
 
 def padded_shape(g: OGrid):
