@@ -58,10 +58,17 @@ struct Plan {
   std::vector<long long> rec_cell, arec_cell;
   std::vector<float> rec_g, arec_g;
   std::vector<int> colmap, acolmap;
-  std::vector<long long> src_cell;
+  // receiver -> its internal columns (forward tiling), ascending; identity
+  // when every receiver is one node
+  std::vector<int> rcol_ptr, rcols;
+  bool one_node = true;
+  std::vector<long long> src_cell;  // 8 per shot (-1: corner not used)
+  std::vector<float> src_w;         // 8 per shot
+  int zs = -1;                      // padded plane of the free surface
   std::vector<float> gx, gy, gz;
   long long pool_elems = 0, term_elems = 0;
-  int ncol = 0;
+  int ncol = 0;   // internal data columns (receiver nodes)
+  int nrec = 0;   // receivers
 };
 
 }  // namespace
@@ -73,6 +80,7 @@ struct mamute_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   // scratch (grow-only)
   DevBuf coefA, coefM, srho, pool[2], psi[2], acc, slots, tstore, dint, rint, dtmp, partial, misfit;
+  DevBuf ident, rcolptr, rcols, ecol, srcw;  // receiver-node combination (trilinear)
   DevBuf items, vols, maps, cmaps, recptr, rec, colmap, gx, gy, gz, cells, gvals, srccell,
       aitems, arecptr, arec, acolmap, acells, agvals;
   DevBuf hvel, hrho, hseis, hobs, hgrad, hphess;  // staging for the *_host calls
@@ -147,14 +155,16 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t s) {
   return cudaStreamSynchronize(s);  // host vectors are released after the call
 }
 
-std::vector<float> sponge(int N, int b, double alpha) {
+// Cerjan profile of one padded axis; with a free surface at plane zs (z axis
+// only) the low face is not damped and the factor is 0 on and above it.
+std::vector<float> sponge(int N, int b, double alpha, int zs = -1) {
   std::vector<float> p(N);
   for (int i = 0; i < N; ++i) {
     int d = 0;
-    if (i < b) d = b - i;
+    if (i < b && zs < 0) d = b - i;
     else if (i > N - 1 - b) d = i - (N - 1 - b);
     const double a = alpha * d;
-    p[i] = (float)std::exp(-a * a);
+    p[i] = (zs >= 0 && i <= zs) ? 0.0f : (float)std::exp(-a * a);
   }
   return p;
 }
@@ -190,21 +200,30 @@ int max_piece(const std::vector<int>& b) {
   return m;
 }
 
+// A receiver's node with non-zero weight (nearest node: one per receiver;
+// trilinear: up to 8), in the shot window's local padded coordinates.
+struct NodeEntry {
+  int lx, ly, lz;
+  long long cell;  // model cell of the node
+  int r;           // receiver
+  int shot;
+  float w;         // interpolation weight
+};
+
 // Receiver tables for one tiling (items ordered z block, row, column).
-void build_receivers(Plan& P, int TX, int zsplit, const std::vector<std::vector<int>>& recnode,
+void build_receivers(Plan& P, int TX, int zsplit, const std::vector<NodeEntry>& ent,
                      const std::vector<int>& item_base, const std::vector<Tiling>& tilings,
                      std::vector<WorkItem>& items, std::vector<int>& rec_ptr,
                      std::vector<RecEntry>& rec, std::vector<long long>& cells,
-                     std::vector<float>& gvals, std::vector<int>& colmap, int n_rec_total,
-                     const std::vector<long long>& rcell_all, const std::vector<int>& rshot) {
+                     std::vector<float>& gvals, std::vector<int>& colmap) {
   struct Tmp {
     int item, z, lxy, r;
   };
   std::vector<Tmp> t;
-  t.reserve(n_rec_total);
-  for (int r = 0; r < n_rec_total; ++r) {
-    const int s = rshot[r];
-    const int lx = recnode[r][0], ly = recnode[r][1], lz = recnode[r][2];
+  t.reserve(ent.size());
+  for (int r = 0; r < (int)ent.size(); ++r) {
+    const int s = ent[r].shot;
+    const int lx = ent[r].lx, ly = ent[r].ly, lz = ent[r].lz;
     const Tiling& T = tilings[s];
     const int ti = (int)(std::upper_bound(T.xs.begin(), T.xs.end(), lx) - T.xs.begin()) - 1;
     const int tj = (int)(std::upper_bound(T.ys.begin(), T.ys.end(), ly) - T.ys.begin()) - 1;
@@ -243,16 +262,16 @@ void build_receivers(Plan& P, int TX, int zsplit, const std::vector<std::vector<
     e = f;
   }
   for (size_t i = 0; i < t.size(); ++i) {
+    const NodeEntry& E = ent[t[i].r];
     RecEntry& R = rec[i];
     R.lxy = t[i].lxy;
     R.col = (int)i;
     R.group = 0;
-    colmap[i] = t[i].r;
-    cells[i] = rcell_all[t[i].r];
-    const int s = rshot[t[i].r];
-    const VolDesc& V = P.vols[s];
-    const int lx = recnode[t[i].r][0], ly = recnode[t[i].r][1], lz = recnode[t[i].r][2];
-    gvals[i] = P.gx[V.gx_off + lx] * P.gy[V.gy_off + ly] * P.gz[lz];
+    R.wgt = E.w;
+    colmap[i] = E.r;
+    cells[i] = E.cell;
+    const VolDesc& V = P.vols[E.shot];
+    gvals[i] = P.gx[V.gx_off + E.lx] * P.gy[V.gy_off + E.ly] * P.gz[E.lz];
   }
   for (size_t i = 0; i < t.size();) {
     size_t j = i;
@@ -339,7 +358,12 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->border < 0 || g->nt < 1)
     return fail(ctx, MAMUTE_EINVAL, "bad grid dimensions");
   if (!(g->h > 0.f) || !(g->dt > 0.f)) return fail(ctx, MAMUTE_EINVAL, "h and dt must be > 0");
-  if (g->free_surface != 0) return fail(ctx, MAMUTE_EINVAL, "free_surface is not supported");
+  if (g->free_surface != 0 && g->free_surface != 1)
+    return fail(ctx, MAMUTE_EINVAL, "free_surface must be 0 or 1");
+  if (g->free_surface && g->nz < 5)
+    return fail(ctx, MAMUTE_EINVAL, "a free surface needs nz >= 5 (the image of the stencil)");
+  if (g->xyz_interp != 0 && g->xyz_interp != 1)
+    return fail(ctx, MAMUTE_EINVAL, "xyz_interp must be 0 or 1");
   if (!(g->cerjan >= 0.f)) return fail(ctx, MAMUTE_EINVAL, "cerjan must be >= 0");
   if (n_src < 1 || !src_xyz || !rec_offset) return fail(ctx, MAMUTE_EINVAL, "no shots");
   if (rec_offset[0] != 0) return fail(ctx, MAMUTE_EINVAL, "rec_offset[0] must be 0");
@@ -354,16 +378,56 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   const long long nmax = 1LL << 31;
   if ((long long)P.Nz * P.Ny * P.pitchG >= nmax * 4)
     return fail(ctx, MAMUTE_EINVAL, "grid too large");
-  P.gz = sponge(P.Nz, P.b, g->cerjan);
-  auto node = [&](const float* xyz, int& i, int& j, int& k) {
-    i = (int)std::floor(((double)xyz[0] - g->ox) / g->h + 0.5);
-    j = (int)std::floor(((double)xyz[1] - g->oy) / g->h + 0.5);
-    k = (int)std::floor(((double)xyz[2] - g->oz) / g->h + 0.5);
-    return i >= 0 && i < P.nx && j >= 0 && j < P.ny && k >= 0 && k < P.nz;
+  P.zs = g->free_surface ? P.b : -1;
+  P.gz = sponge(P.Nz, P.b, g->cerjan, P.zs);
+  // Model cells and weights of a point: its nearest node, or the trilinear
+  // weights of the cell that holds it (zero weights dropped).  Nodes on a
+  // free surface are dropped too (the field is zero there); false if the
+  // point or a node it needs lies outside [lo, hi) or no node is left.
+  struct Corner {
+    int i, j, k;
+    double w;
   };
-  std::vector<std::vector<int>> recnode(n_rec, std::vector<int>(3));
-  std::vector<long long> rcell(n_rec);
-  std::vector<int> rshot(n_rec);
+  auto locate = [&](const float* xyz, const int lo[2], const int hi[2], std::vector<Corner>& out) {
+    out.clear();
+    const double f[3] = {((double)xyz[0] - g->ox) / g->h, ((double)xyz[1] - g->oy) / g->h,
+                         ((double)xyz[2] - g->oz) / g->h};
+    const int lim_lo[3] = {lo[0], lo[1], 0}, lim_hi[3] = {hi[0], hi[1], P.nz};
+    if (!g->xyz_interp) {
+      int id[3];
+      for (int a = 0; a < 3; ++a) {
+        id[a] = (int)std::floor(f[a] + 0.5);
+        if (id[a] < lim_lo[a] || id[a] >= lim_hi[a]) return false;
+      }
+      if (P.zs >= 0 && id[2] == 0) return false;
+      out.push_back(Corner{id[0], id[1], id[2], 1.0});
+      return true;
+    }
+    int base[3];
+    double t[3];
+    for (int a = 0; a < 3; ++a) {
+      base[a] = (int)std::floor(f[a]);
+      t[a] = f[a] - (double)base[a];
+    }
+    for (int c = 0; c < 8; ++c) {
+      int id[3];
+      double w = 1.0;
+      for (int a = 0; a < 3; ++a) {
+        const int up = (c >> a) & 1;
+        id[a] = base[a] + up;
+        w *= up ? t[a] : 1.0 - t[a];
+      }
+      if (w == 0.0) continue;
+      for (int a = 0; a < 3; ++a)
+        if (id[a] < lim_lo[a] || id[a] >= lim_hi[a]) return false;
+      if (P.zs >= 0 && id[2] == 0) continue;
+      out.push_back(Corner{id[0], id[1], id[2], w});
+    }
+    return !out.empty();
+  };
+  std::vector<NodeEntry> ent;
+  std::vector<int> rcount(n_rec, 0);
+  std::vector<Corner> cs;
   long long off = 0, toff = 0;
   for (int s = 0; s < n_src; ++s) {
     int a0 = 0, a1 = P.nx, a2 = 0, a3 = P.ny;
@@ -388,26 +452,41 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
     std::vector<float> px = sponge(V.Nx, P.b, g->cerjan), py = sponge(V.Ny, P.b, g->cerjan);
     P.gx.insert(P.gx.end(), px.begin(), px.end());
     P.gy.insert(P.gy.end(), py.begin(), py.end());
-    int i, j, k;
-    if (!node(src_xyz + 3 * s, i, j, k)) return fail(ctx, MAMUTE_EINVAL, "source %d outside the model", s);
-    if (i < a0 || i >= a1 || j < a2 || j >= a3)
-      return fail(ctx, MAMUTE_EINVAL, "source %d outside its aperture", s);
-    V.src_x = i + P.b - a0; V.src_y = j + P.b - a2; V.src_z = k + P.b;
-    P.src_cell.push_back(((long long)k * P.ny + j) * P.nx + i);
+    const int lo[2] = {a0, a2}, hi[2] = {a1, a3};
+    if (!locate(src_xyz + 3 * s, lo, hi, cs))
+      return fail(ctx, MAMUTE_EINVAL, "source %d outside the model, its aperture or on the free surface", s);
+    // corner (0,0,0) of the source's cell; the 8 scales are set on the device
+    int bi = cs[0].i, bj = cs[0].j, bk = cs[0].k;
+    for (const Corner& c : cs) {
+      bi = std::min(bi, c.i); bj = std::min(bj, c.j); bk = std::min(bk, c.k);
+    }
+    V.src_x = bi + P.b - a0; V.src_y = bj + P.b - a2; V.src_z = bk + P.b;
+    for (int e = 0; e < 8; ++e) {
+      P.src_cell.push_back(-1);
+      P.src_w.push_back(0.f);
+    }
+    for (const Corner& c : cs) {
+      const int e = (c.i - bi) + 2 * (c.j - bj) + 4 * (c.k - bk);
+      P.src_cell[8 * s + e] = ((long long)c.k * P.ny + c.j) * P.nx + c.i;
+      P.src_w[8 * s + e] = (float)c.w;
+    }
     for (int r = rec_offset[s]; r < rec_offset[s + 1]; ++r) {
-      if (!node(rec_xyz + 3 * (long long)r, i, j, k))
-        return fail(ctx, MAMUTE_EINVAL, "receiver %d outside the model", r);
-      if (i < a0 || i >= a1 || j < a2 || j >= a3)
-        return fail(ctx, MAMUTE_EINVAL, "receiver %d outside the aperture of its shot", r);
-      recnode[r] = {i + P.b - a0, j + P.b - a2, k + P.b};
-      rcell[r] = ((long long)k * P.ny + j) * P.nx + i;
-      rshot[r] = s;
+      if (!locate(rec_xyz + 3 * (long long)r, lo, hi, cs))
+        return fail(ctx, MAMUTE_EINVAL,
+                    "receiver %d outside the model, the aperture of its shot or on the free surface", r);
+      for (const Corner& c : cs)
+        ent.push_back(NodeEntry{c.i + P.b - a0, c.j + P.b - a2, c.k + P.b,
+                                ((long long)c.k * P.ny + c.j) * P.nx + c.i, r, s, (float)c.w});
+      rcount[r] = (int)cs.size();
     }
     P.vols.push_back(V);
   }
   P.pool_elems = off;
   P.term_elems = toff;
-  P.ncol = n_rec;
+  P.ncol = (int)ent.size();
+  P.nrec = n_rec;
+  P.one_node = true;
+  for (int r = 0; r < n_rec; ++r) P.one_node = P.one_node && rcount[r] == 1;
   // Work items: one per tile, all planes, for the forward and adjoint kernels.
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -438,11 +517,20 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   };
   std::vector<int> base;
   make_items(fc, P.items, base);
-  build_receivers(P, P.tx, fc.zsplit, recnode, base, fc.tilings, P.items, P.rec_ptr, P.rec,
-                  P.rec_cell, P.rec_g, P.colmap, n_rec, rcell, rshot);
+  build_receivers(P, P.tx, fc.zsplit, ent, base, fc.tilings, P.items, P.rec_ptr, P.rec,
+                  P.rec_cell, P.rec_g, P.colmap);
+  // receiver -> internal columns of the forward tables, ascending
+  P.rcol_ptr.assign(n_rec + 1, 0);
+  for (int c = 0; c < P.ncol; ++c) ++P.rcol_ptr[P.colmap[c] + 1];
+  for (int r = 0; r < n_rec; ++r) P.rcol_ptr[r + 1] += P.rcol_ptr[r];
+  P.rcols.assign(P.ncol, 0);
+  {
+    std::vector<int> fill(P.rcol_ptr.begin(), P.rcol_ptr.end() - 1);
+    for (int c = 0; c < P.ncol; ++c) P.rcols[fill[P.colmap[c]]++] = c;
+  }
   make_items(ac, P.aitems, base);
-  build_receivers(P, P.atx, ac.zsplit, recnode, base, ac.tilings, P.aitems, P.arec_ptr, P.arec,
-                  P.arec_cell, P.arec_g, P.acolmap, n_rec, rcell, rshot);
+  build_receivers(P, P.atx, ac.zsplit, ent, base, ac.tilings, P.aitems, P.arec_ptr, P.arec,
+                  P.arec_cell, P.arec_g, P.acolmap);
   if (env_int("MAMUTE_VERBOSE", 0))
     fprintf(stderr, "mamute plan: %d shots, forward tile %dx%d/%dz (%zu CTAs), adjoint tile %dx%d/%dz (%zu CTAs)\n",
             n_src, P.tx, P.ty, fc.zsplit, P.items.size(), P.atx, P.aty, ac.zsplit, P.aitems.size());
@@ -516,16 +604,26 @@ int setup(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho, bool nee
   CK(upload(ctx->acells, P.arec_cell, ctx->stream));
   CK(upload(ctx->agvals, P.arec_g, ctx->stream));
   CK(upload(ctx->srccell, P.src_cell, ctx->stream));
+  CK(upload(ctx->srcw, P.src_w, ctx->stream));
+  if (!P.one_node) {
+    std::vector<int> iota(P.ncol);
+    for (int c = 0; c < P.ncol; ++c) iota[c] = c;
+    CK(upload(ctx->ident, iota, ctx->stream));
+    CK(upload(ctx->rcolptr, P.rcol_ptr, ctx->stream));
+    CK(upload(ctx->rcols, P.rcols, ctx->stream));
+    CK(ensure(ctx->ecol, (size_t)P.ncol * P.nt * 4));
+  }
   CK(upload(ctx->gx, P.gx, ctx->stream));
   CK(upload(ctx->gy, P.gy, ctx->stream));
   CK(upload(ctx->gz, P.gz, ctx->stream));
   // Scales at receivers (both tables) and sources.
   GeomArgs ga{vel, rho, (int)P.rec.size(), (int)P.vols.size(), (const long long*)ctx->cells.p,
               (const float*)ctx->gvals.p, (RecEntry*)ctx->rec.p, (const long long*)ctx->srccell.p,
-              (VolDesc*)ctx->vols.p, P.h, P.dt};
+              (const float*)ctx->srcw.p, (VolDesc*)ctx->vols.p, P.h, P.dt};
   CK(aux_count(ctx, launch_geometry(ga, ctx->stream)));
   GeomArgs gb{vel, rho, (int)P.arec.size(), 0, (const long long*)ctx->acells.p,
-              (const float*)ctx->agvals.p, (RecEntry*)ctx->arec.p, nullptr, nullptr, P.h, P.dt};
+              (const float*)ctx->agvals.p, (RecEntry*)ctx->arec.p, nullptr, nullptr, nullptr,
+              P.h, P.dt};
   CK(aux_count(ctx, launch_geometry(gb, ctx->stream)));
   // Tensor maps (layout in ShotMaps).
   std::vector<ShotMaps> maps(P.vols.size());
@@ -673,6 +771,23 @@ int check_common(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     if (rc_ != MAMUTE_OK) return rc_; \
   } while (0)
 
+// Samples [n0, n1) of the recorded data (internal [nt][ncol] layout) into
+// the user's seis[n_rec][nt]: a transpose when every receiver is one node,
+// else a transpose to per-node rows followed by the fixed-order sum of each
+// receiver's nodes.
+int data_to_user(mamute_ctx* ctx, const Plan& P, int n0, int n1, float* seis, cudaStream_t s) {
+  if (P.one_node) {
+    CK(aux_count(ctx, launch_data_out_range((const float*)ctx->dint.p, (const int*)ctx->colmap.p,
+                                            n0, n1, P.nt, P.ncol, seis, s)));
+    return MAMUTE_OK;
+  }
+  CK(aux_count(ctx, launch_data_out_range((const float*)ctx->dint.p, (const int*)ctx->ident.p, n0,
+                                          n1, P.nt, P.ncol, (float*)ctx->ecol.p, s)));
+  CK(aux_count(ctx, launch_combine((const float*)ctx->ecol.p, (const int*)ctx->rcolptr.p,
+                                   (const int*)ctx->rcols.p, P.nrec, n0, n1, P.nt, seis, s)));
+  return MAMUTE_OK;
+}
+
 // host_seis (host, may be NULL): the seismograms also go to this host array,
 // segment by segment while later segments of the time loop run.
 int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* rho,
@@ -742,10 +857,9 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
       }
       CK(cudaEventRecord(ctx->seg_ev[k], ctx->stream));
       CK(cudaStreamWaitEvent(ctx->copy, ctx->seg_ev[k], 0));
-      CK(aux_count(ctx, launch_data_out_range((const float*)ctx->dint.p, (const int*)ctx->colmap.p,
-                                              t0, t1, P.nt, P.ncol, seis, ctx->copy)));
+      TRY(data_to_user(ctx, P, t0, t1, seis, ctx->copy));
       CK(cudaMemcpy2DAsync(host_seis + t0, (size_t)P.nt * 4, seis + t0, (size_t)P.nt * 4,
-                           (size_t)(t1 - t0) * 4, (size_t)P.ncol, cudaMemcpyDeviceToHost,
+                           (size_t)(t1 - t0) * 4, (size_t)P.nrec, cudaMemcpyDeviceToHost,
                            ctx->copy));
       t0 = t1;
     }
@@ -803,11 +917,10 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
       ctx->ev0_set = true;
     }
     ctx->step_launches = P.nt;
-    ctx->launches += P.nt + (stream_out ? std::min(P.nt, 8) : 0);
+    ctx->launches += P.nt + (stream_out ? std::min(P.nt, 8) * (P.one_node ? 1 : 2) : 0);
   }
   if (!stream_out)
-    CK(aux_count(ctx, launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt,
-                                      P.ncol, seis, ctx->stream)));
+    TRY(data_to_user(ctx, P, 0, P.nt, seis, ctx->stream));
   if (ph) {
     FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
                     P.nx, P.ny, P.nz, P.b, P.dt, 1, 0, opts->phess};
@@ -835,7 +948,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   const size_t ncol = std::max(P.ncol, 1);
   CK(ensure(ctx->dint, (size_t)P.nt * ncol * 4));
   CK(ensure(ctx->rint, (size_t)P.nt * ncol * 4));
-  CK(ensure(ctx->partial, (size_t)std::max(misfit_blocks((long long)P.nt * P.ncol), 1) * 8));
+  CK(ensure(ctx->partial, (size_t)std::max(misfit_blocks((long long)P.nt * P.nrec), 1) * 8));
   for (int i = 0; i < 2; ++i) {
     CK(cudaMemsetAsync(ctx->pool[i].p, 0, pool, ctx->stream));
     CK(cudaMemsetAsync(ctx->psi[i].p, 0, pool, ctx->stream));
@@ -969,8 +1082,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   auto make_residual = [&]() -> int {
     if (residual_mode) {
       CK(ensure(ctx->dtmp, (size_t)P.nt * ncol * 4));
-      CK(aux_count(ctx, launch_data_out((const float*)ctx->dint.p, (const int*)ctx->colmap.p, P.nt, P.ncol,
-                         (float*)ctx->dtmp.p, ctx->stream)));
+      TRY(data_to_user(ctx, P, 0, P.nt, (float*)ctx->dtmp.p, ctx->stream));
       // r = seis - d_obs: first r_int = -(-seis) then subtract d_obs.
       CK(aux_count(ctx, launch_data_in((const float*)ctx->dtmp.p, (const int*)ctx->acolmap.p, P.nt, P.ncol,
                         nullptr, -1.0f, (float*)ctx->dint.p, nullptr, nullptr, ctx->stream)));
@@ -979,7 +1091,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
       // The misfit is summed over the user's [n_rec][nt] layout, so it does
       // not depend on the tile shapes of either propagation.
       ctx->launches += 2;
-      CK(launch_misfit((const float*)ctx->dtmp.p, d_in, (long long)P.nt * P.ncol,
+      CK(launch_misfit((const float*)ctx->dtmp.p, d_in, (long long)P.nt * P.nrec,
                        (double*)ctx->partial.p, (double*)ctx->misfit.p, ctx->stream));
     } else {
       CK(aux_count(ctx, launch_data_in(d_in, (const int*)ctx->acolmap.p, P.nt, P.ncol, nullptr, -1.0f,
@@ -1109,6 +1221,8 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   }
   Plan P;
   TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz, nullptr, P));
+  if (!P.one_node)
+    return fail(ctx, MAMUTE_EINVAL, "the Gauss-Newton diagonal needs receivers on grid nodes");
   ctx->max_planes = P.Nz;
   TRY(check_cfl(ctx, P, vel));
   // Compact interior term layout: slot k of the ring is [nz][ny][nx].
@@ -1376,7 +1490,8 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
                    &ctx->hrho, &ctx->hseis, &ctx->hobs, &ctx->hgrad, &ctx->hphess,
                    &ctx->gnV, &ctx->gnRe, &ctx->gnIm, &ctx->gnS, &ctx->gnR, &ctx->gnW,
                    &ctx->gnBins, &ctx->gnWts, &ctx->gnRow, &ctx->nnPartial, &ctx->nnLoss,
-                   &ctx->slotmaps};
+                   &ctx->slotmaps, &ctx->ident, &ctx->rcolptr, &ctx->rcols, &ctx->ecol,
+                   &ctx->srcw};
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);

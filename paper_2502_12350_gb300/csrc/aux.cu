@@ -71,7 +71,8 @@ __global__ void max_kernel(const float* v, long long n, unsigned int* out) {
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// Receiver and source scales from the model at their nodes.
+// Receiver-node and source-corner scales from the model at their nodes,
+// times the interpolation weights.
 __global__ void geometry_kernel(GeomArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < a.n_rec) {
@@ -79,13 +80,33 @@ __global__ void geometry_kernel(GeomArgs a) {
     const double sr = a.rho ? sqrt((double)a.rho[cell]) : 1.0;
     const double cv = a.vel[cell];
     RecEntry& e = a.rec[t];
-    e.fscale = (float)sr;
-    e.ascale = (float)(cv * cv * a.dt * a.dt * (double)a.rec_g[t] * sr);
+    const double w = e.wgt;
+    e.fscale = (float)(w * sr);
+    e.ascale = (float)(w * cv * cv * a.dt * a.dt * (double)a.rec_g[t] * sr);
   }
   if (t < a.n_src) {
-    const long long cell = a.src_cell[t];
-    const double sr = a.rho ? sqrt((double)a.rho[cell]) : 1.0;
-    a.vols[t].src_scale = (float)(a.dt * a.dt / (a.h * a.h * a.h * sr));
+    for (int c = 0; c < 8; ++c) {
+      const long long cell = a.src_cell[8 * t + c];
+      float sc = 0.0f;
+      if (cell >= 0) {
+        const double sr = a.rho ? sqrt((double)a.rho[cell]) : 1.0;
+        sc = (float)((double)a.src_w[8 * t + c] * a.dt * a.dt / (a.h * a.h * a.h * sr));
+      }
+      a.vols[t].src_sc[c] = sc;
+    }
+  }
+}
+
+__global__ void combine_kernel(const float* __restrict__ ecol, const int* __restrict__ ptr,
+                               const int* __restrict__ cols, int n_rec, int n0, int n1, int nt,
+                               float* __restrict__ seis) {
+  const int r = blockIdx.y;
+  if (r >= n_rec) return;
+  const int b = ptr[r], e = ptr[r + 1];
+  for (int n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    for (int k = b; k < e; ++k) v += ecol[(long long)cols[k] * nt + n];
+    seis[(long long)r * nt + n] = v;
   }
 }
 
@@ -256,6 +277,15 @@ cudaError_t launch_data_out_range(const float* d_int, const int* colmap, int n0,
   dim3 g((ncol + 31) / 32, (n1 - n0 + 31) / 32), b(32, 8);
   data_out_kernel<<<g, b, 0, s>>>(d_int + (long long)n0 * ncol, colmap, n1 - n0, ncol, nt,
                                   seis + n0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const float* ecol, const int* ptr, const int* cols, int n_rec, int n0,
+                           int n1, int nt, float* seis, cudaStream_t s) {
+  if (n_rec == 0 || n1 <= n0) return cudaSuccess;
+  const int bx = (n1 - n0 + 127) / 128;
+  dim3 g(bx < 8 ? bx : 8, n_rec);
+  combine_kernel<<<g, 128, 0, s>>>(ecol, ptr, cols, n_rec, n0, n1, nt, seis);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ struct GeomArgs {
   const long long* rec_cell;  // model cell index per receiver entry
   const float* rec_g;         // sponge factor at the entry's node
   RecEntry* rec;
-  const long long* src_cell;  // model cell per shot
+  const long long* src_cell;  // model cell of each of the 8 source-cell corners per shot (-1: unused)
+  const float* src_w;         // interpolation weight of each corner
   VolDesc* vols;
   double h, dt;
 };
@@ -50,6 +51,10 @@ cudaError_t launch_data_out(const float* d_int, const int* colmap, int nt, int n
 // Samples [n0, n1) of the same transpose into seis rows of length nt.
 cudaError_t launch_data_out_range(const float* d_int, const int* colmap, int n0, int n1, int nt,
                                   int ncol, float* seis, cudaStream_t s);
+// seis[r][n] = sum over k in [ptr[r], ptr[r+1]) of ecol[cols[k]][n] (in
+// that order), samples [n0, n1): receivers spread over several nodes.
+cudaError_t launch_combine(const float* ecol, const int* ptr, const int* cols, int n_rec, int n0,
+                           int n1, int nt, float* seis, cudaStream_t s);
 int data_in_blocks(int nt, int ncol);
 cudaError_t launch_data_in(const float* src, const int* colmap, int nt, int ncol,
                            const float* d_int, float sign, float* r_int, double* partial,

@@ -28,8 +28,10 @@ struct VolDesc {
   int pitch;             // floats per row of the shot's wavefield arrays
   int cx0, cy0;          // origin of the window in the global padded grid
   int gx_off, gy_off;    // offsets of the shot's x / y sponge profiles
-  int src_x, src_y, src_z;  // source node, local padded coordinates
-  float src_scale;       // dt^2 / (h^3 sqrt(rho(x_s)))
+  int src_x, src_y, src_z;  // source cell corner (0,0,0), local padded coordinates
+  // dt^2 w_e / (h^3 sqrt(rho_e)) for the corners e = dx + 2 dy + 4 dz of the
+  // source cell (nearest node: corner 0 only; trilinear: the 8 weights w_e)
+  float src_sc[8];
   int border;            // sponge cells on each face
   int nxi, nyi, nzi;     // interior (model) extent of the window
   int txoff, tpitch;     // term store rows: local x in [txoff, txoff + tpitch)
@@ -50,9 +52,10 @@ struct RecEntry {
   int lxy;        // lx + TX * ly inside the tile
   int col;        // column in the internal [nt][n_col] data layout
   int group;      // number of entries sharing this node if first of its group, else 0
-  float fscale;   // forward sampling scale sqrt(rho(x_r))
-  float ascale;   // adjoint injection scale c^2 dt^2 g sqrt(rho) at x_r
-  int pad0, pad1, pad2;
+  float fscale;   // forward sampling scale w sqrt(rho) at the node
+  float ascale;   // adjoint injection scale w c^2 dt^2 g sqrt(rho) at the node
+  float wgt;      // interpolation weight w of the node (1 for the nearest node)
+  int pad1, pad2;
 };
 
 // Tensor maps of one shot (array of these in device memory).  Halo boxes are
