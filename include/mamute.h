@@ -61,7 +61,18 @@ typedef struct mamute_ctx mamute_ctx;
 /* Grid and time axis (Table 2: nx, ny, nz, dx=dy=dz, border, ox, oy, oz, ns,
  * dt).  cerjan is the Cerjan damping constant alpha of the sponge profile
  * g(d) = exp(-(alpha d)^2), d = depth into the sponge in cells (Sec. 2.1,
- * damping boundary); 0 disables damping.  free_surface must be 0. */
+ * damping boundary); 0 disables damping.
+ * free_surface (Sec. 2, modelling options): 1 makes the top model plane
+ * (z = oz) a pressure-release surface by the image method: the field is odd
+ * about that plane (the planes above it read as the negated planes below it)
+ * and zero on it, and the top face has no sponge; needs nz >= 5, and sources
+ * and receivers must lie below the surface.  0: sponge on all six faces.
+ * xyz_interp: 0 puts sources and receivers at their nearest node; 1 uses
+ * the trilinear weights w_e of the 8 nodes of the cell holding the point:
+ * the source adds w_e dt^2 w[n] / (h^3 sqrt(rho_e)) at each node and a
+ * receiver records sum_e w_e sqrt(rho_e) u_e (nodes with zero weight or on a
+ * free surface are skipped; every node with non-zero weight must lie in the
+ * model, or the shot's aperture). */
 typedef struct {
   int nx, ny, nz;
   int border;
@@ -71,6 +82,7 @@ typedef struct {
   float ox, oy, oz;
   float cerjan;
   int free_surface;
+  int xyz_interp;
 } mamute_grid;
 
 /* Options (Table 4 check_mem; Sec. 3 zeroes_nplanes_gradient).

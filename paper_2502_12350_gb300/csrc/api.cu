@@ -736,6 +736,7 @@ StepArgs fwd_args(mamute_ctx* ctx, const Plan& P, int n, const float* wavelet, f
   a.dout = dout;
   a.rin = nullptr;
   a.status = ctx->status;
+  a.zs = P.zs;
   return a;
 }
 
@@ -1125,6 +1126,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     a.dout = nullptr;
     a.rin = (const float*)ctx->rint.p + (size_t)i * P.ncol;
     a.status = ctx->status;
+    a.zs = P.zs;
     CK(step_launch(ctx, a, (int)P.aitems.size(), P.atx, P.aty, P.dens,
                    all_mode ? MODE_ADJ_STORED : MODE_ADJ));
     return MAMUTE_OK;
@@ -1378,6 +1380,7 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
       a.rec = (const RecEntry*)ctx->arec.p;
       a.rin = (j == 0) ? imp_row : zero_row;
       a.status = ctx->status;
+      a.zs = P.zs;
       CK(step_launch(ctx, a, ie - ib, P.atx, P.aty, P.dens, MODE_ADJ_TERM));
       if ((j + 1) % kT == 0) TRY(flush(j + 1));
     }

@@ -41,6 +41,7 @@ struct StepArgs {
   float* dout;            // forward: data row of this step (internal columns), may be null
   const float* rin;       // adjoint: residual row injected at this step
   int* status;            // error flags
+  int zs;                 // padded plane of a free surface (odd image above it), -1 if none
 };
 
 bool tile_supported(int tx, int ty);

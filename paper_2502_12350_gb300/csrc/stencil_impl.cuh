@@ -238,7 +238,10 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
           drain();
           return;
         }
-        const int p = zb - kHalo + i;
+        // Above a free surface at plane zs the plane is the image of plane
+        // 2 zs - p (the consumers negate it).
+        const int p0 = zb - kHalo + i;
+        const int p = (a.zs >= 0 && p0 < a.zs) ? 2 * a.zs - p0 : p0;
         mbar_arrive_expect_tx(&fullF[s], NHALO * HS * 4);
         float* dst = ring + s * NHALO * HS;
         tma_load_3d(dst, mapF, x0 - kHalo, y0 - kHalo, p, &fullF[s]);
@@ -287,12 +290,22 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
     if (!dead && !mbar_wait(bar, parity, a.status)) dead = true;
   };
   F4 q[9], qu[9];
+  // z column entry of plane p from its ring stage (negated above a free
+  // surface, where the stage holds the image plane).
+  auto zload = [&](const float* st, int p) {
+    F4 v = ld4s(st);
+    if (a.zs >= 0 && p < a.zs) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v.v[e] = -v.v[e];
+    }
+    return v;
+  };
   // Priming: planes zb-4 .. zb+3 fill queue slots 0..7.
   for (int i = 0; i < 2 * kHalo; ++i) {
     const int s = i % NSU;
     wait(&fullF[s], (i / NSU) & 1);
-    q[i] = ld4s(ring + s * NHALO * HS + my_off);
-    if (RECOMP) qu[i] = ld4s(ring + s * NHALO * HS + HS + my_off);
+    q[i] = zload(ring + s * NHALO * HS + my_off, zb - kHalo + i);
+    if (RECOMP) qu[i] = zload(ring + s * NHALO * HS + HS + my_off, zb - kHalo + i);
     if (i < kHalo || zb - kHalo + i >= ze) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyF[s]);
@@ -304,8 +317,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
     {  // queue slot 8 <- plane z + 4
       const int i = j + 2 * kHalo, s = i % NSU;
       wait(&fullF[s], (i / NSU) & 1);
-      q[8] = ld4s(ring + s * NHALO * HS + my_off);
-      if (RECOMP) qu[8] = ld4s(ring + s * NHALO * HS + HS + my_off);
+      q[8] = zload(ring + s * NHALO * HS + my_off, z + kHalo);
+      if (RECOMP) qu[8] = zload(ring + s * NHALO * HS + HS + my_off, z + kHalo);
       if (z + kHalo >= ze) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&emptyF[s]);
@@ -331,11 +344,20 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
       const float g = __fmul_rn(gxv[e], gyz);
       out.v[e] = update(q[4].v[e], prev.v[e], Av.v[e], Mv.v[e], g, lap[e], DENS);
     }
-    // Source injection (forward only): u^{n+1}(x_s) += dt^2 w[n] / (h^3 sqrt rho).
-    if (!ADJ && z == V.src_z && gyl == V.src_y && V.src_x >= gxl && V.src_x < gxl + 4) {
+    // Source injection (forward only): u^{n+1} += w_e dt^2 w[n] / (h^3 sqrt rho_e)
+    // at the corners e of the source cell (one corner for the nearest node).
+    if (!ADJ) {
+      const int dz = z - V.src_z, dy = gyl - V.src_y;
+      if ((unsigned)dz < 2u && (unsigned)dy < 2u) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (gxl + e == V.src_x) out.v[e] += V.src_scale * a.wn;
+        for (int e = 0; e < 4; ++e) {
+          const int dx = gxl + e - V.src_x;
+          if ((unsigned)dx < 2u) {
+            const float sc = V.src_sc[dx + 2 * dy + 4 * dz];
+            if (sc != 0.0f) out.v[e] += sc * a.wn;
+          }
+        }
+      }
     }
     // Receivers of this tile on this plane.
     {

@@ -33,7 +33,8 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("border", ctypes.c_int), ("h", ctypes.c_float), ("dt", ctypes.c_float),
                 ("nt", ctypes.c_int), ("ox", ctypes.c_float), ("oy", ctypes.c_float),
-                ("oz", ctypes.c_float), ("cerjan", ctypes.c_float), ("free_surface", ctypes.c_int)]
+                ("oz", ctypes.c_float), ("cerjan", ctypes.c_float), ("free_surface", ctypes.c_int),
+                ("xyz_interp", ctypes.c_int)]
 
 
 class Opts(ctypes.Structure):
@@ -212,10 +213,13 @@ class Context:
                                                 _ptr(hdiag)))
 
 
-def make_grid(nx, ny, nz, border, h, dt, nt, origin=(0.0, 0.0, 0.0), cerjan=0.015) -> Grid:
-    return Grid(nx, ny, nz, border, h, dt, nt, origin[0], origin[1], origin[2], cerjan, 0)
+def make_grid(nx, ny, nz, border, h, dt, nt, origin=(0.0, 0.0, 0.0), cerjan=0.015,
+              free_surface=0, xyz_interp=0) -> Grid:
+    return Grid(nx, ny, nz, border, h, dt, nt, origin[0], origin[1], origin[2], cerjan,
+                int(free_surface), int(xyz_interp))
 
 
-def grid_of(w, cerjan=0.015) -> Grid:
+def grid_of(w, cerjan=0.015, free_surface=0, xyz_interp=0) -> Grid:
     """Grid of a synthetic workload (see synth.Workload)."""
-    return make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, cerjan=cerjan)
+    return make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, cerjan=cerjan,
+                     free_surface=free_surface, xyz_interp=xyz_interp)
