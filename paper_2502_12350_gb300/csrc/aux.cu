@@ -100,10 +100,10 @@ __global__ void geometry_kernel(GeomArgs a) {
 __global__ void combine_kernel(const float* __restrict__ ecol, const int* __restrict__ ptr,
                                const int* __restrict__ cols, int n_rec, int n0, int n1, int nt,
                                float* __restrict__ seis) {
-  const int r = blockIdx.y;
+  const int r = blockIdx.x;  // receivers on x (more than 65535 of them)
   if (r >= n_rec) return;
   const int b = ptr[r], e = ptr[r + 1];
-  for (int n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += gridDim.x * blockDim.x) {
+  for (int n = n0 + blockIdx.y * blockDim.x + threadIdx.x; n < n1; n += gridDim.y * blockDim.x) {
     float v = 0.0f;
     for (int k = b; k < e; ++k) v += ecol[(long long)cols[k] * nt + n];
     seis[(long long)r * nt + n] = v;
@@ -283,8 +283,8 @@ cudaError_t launch_data_out_range(const float* d_int, const int* colmap, int n0,
 cudaError_t launch_combine(const float* ecol, const int* ptr, const int* cols, int n_rec, int n0,
                            int n1, int nt, float* seis, cudaStream_t s) {
   if (n_rec == 0 || n1 <= n0) return cudaSuccess;
-  const int bx = (n1 - n0 + 127) / 128;
-  dim3 g(bx < 8 ? bx : 8, n_rec);
+  const int by = (n1 - n0 + 127) / 128;
+  dim3 g(n_rec, by < 8 ? by : 8);
   combine_kernel<<<g, 128, 0, s>>>(ecol, ptr, cols, n_rec, n0, n1, nt, seis);
   return cudaGetLastError();
 }
