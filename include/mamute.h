@@ -109,6 +109,18 @@ typedef struct {
  *                   blocks}; 0 entries are chosen by the library's cost model
  *                   (an autotuner may pass measured choices; the result does
  *                   not depend on them).  An unsupported shape is EINVAL.
+ *   smooth_mode     gradient preconditioning (Sec. 2, FWI parameters; Algorithm
+ *                   3 GradientPreconditioning, applied after MultiplyAdjoint and
+ *                   before ZeroesNearSurface): 0 none, 1 Bessel filter, 2
+ *                   Laplace filter (see mamute_smooth).
+ *   smooth_len      filter lengths lx, ly, lz in metres; 0 entries mean 2 h.
+ *   time_interp     0: data (seis, d_obs, d_res) are on the modelling time axis
+ *                   [n_rec][nt]; 1 (nearest) or 2 (sinc): they are on a data
+ *                   axis of nt_data samples of dt_data seconds, and the
+ *                   modelled traces are resampled to it (Sec. 2, time
+ *                   interpolation; see mamute_resample); the residual is
+ *                   brought back by the transposed resampling.
+ *   nt_data, dt_data  the data time axis when time_interp != 0.
  * A NULL options pointer means all defaults. */
 typedef struct {
   float check_mem;
@@ -117,7 +129,18 @@ typedef struct {
   const int* aperture;
   float* phess;
   int tiles[6];
+  int smooth_mode;
+  float smooth_len[3];
+  int time_interp;
+  int nt_data;
+  float dt_data;
 } mamute_opts;
+
+#define MAMUTE_SMOOTH_NONE 0
+#define MAMUTE_SMOOTH_BESSEL 1
+#define MAMUTE_SMOOTH_LAPLACE 2
+#define MAMUTE_INTERP_NEAREST 1
+#define MAMUTE_INTERP_SINC 2
 
 /* Creates a context on `device` issuing work on `cuda_stream` (a cudaStream_t;
  * NULL = the legacy default stream).  Returns MAMUTE_EARCH unless the device
@@ -319,6 +342,38 @@ int mamute_ctx_dft_timing(const mamute_ctx* ctx, double* dft_ms, long long* dft_
 #define MAMUTE_MISFIT_NOALLOC_MAX_SAMPLES (16384LL * 16384LL)
 int mamute_misfit_noalloc(const float* d, const float* d_obs, long long n, void* cuda_stream,
                           double* misfit);
+
+/* Gradient smoothing (Sec. 2, FWI: gradient preconditioning by a Bessel or a
+ * Laplace filter with lengths bessel_filter_l{x,y,z}; Algorithm 3
+ * GradientPreconditioning).  With D_aa the 3-point second difference along
+ * axis a on the model grid of spacing h, reflecting at the ends (the value
+ * beyond the last cell repeats it):
+ *   mode 1 (Bessel)   out = (I - lx^2 Dxx - ly^2 Dyy - lz^2 Dzz)^-1 in
+ *   mode 2 (Laplace)  out = (I - lx^2 Dxx)^-1 (I - ly^2 Dyy)^-1 (I - lz^2 Dzz)^-1 in
+ *   mode 0            out = in.
+ * Solved exactly in the DCT-II basis, which diagonalises both operators
+ * (FP32 transforms).  lengths: host [3] (lx, ly, lz, metres; 0 means 2 h) or
+ * NULL for all 2 h.  in, out: device [nz][ny][nx]; they may be the same
+ * array.  Errors: EINVAL (sizes, NULL, bad mode or negative length), ENOMEM,
+ * ECUDA. */
+int mamute_smooth(mamute_ctx* ctx, int nx, int ny, int nz, float h, int mode,
+                  const float* lengths, const float* in, float* out);
+
+/* Time resampling of traces (Sec. 2: time interpolation by nearest neighbour
+ * or sinc; Table 1 Interpolate).  Sample n of an input trace is at time
+ * n dt_in, output sample m at m dt_out.
+ *   mode 1 (nearest)  y[m] = x[floor(m dt_out / dt_in + 1/2)], 0 past the end
+ *   mode 2 (sinc)     y[m] = sum_n x[n] (dt_in / D) sinc((m dt_out - n dt_in) / D)
+ *                      hann((m dt_out - n dt_in) / (8 D)), D = max(dt_in, dt_out),
+ *                      hann(u) = (1 + cos(pi u)) / 2 for |u| < 1, else 0
+ *                      (interpolation when dt_out <= dt_in; low-pass below the
+ *                      output Nyquist frequency, then decimation, otherwise).
+ * adjoint = 0: x device [n_traces][nt_in] -> y device [n_traces][nt_out];
+ * adjoint = 1: the transpose, x device [n_traces][nt_out] -> y device
+ * [n_traces][nt_in].  The weights are formed in FP64 on the host, the sums in
+ * FP32 on the device, in a fixed order.  Errors: EINVAL, ENOMEM, ECUDA. */
+int mamute_resample(mamute_ctx* ctx, int n_traces, int nt_in, float dt_in, int nt_out,
+                    float dt_out, int mode, int adjoint, const float* x, float* y);
 
 /* Stability bound used by the CFL check (max(c) dt / h must not exceed it). */
 double mamute_cfl_limit(void);

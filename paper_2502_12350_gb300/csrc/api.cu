@@ -17,6 +17,7 @@
 #include "conv.h"
 #include "gn.h"
 #include "common.cuh"
+#include "postproc.h"
 #include "revolve.h"
 #include "stencil.h"
 
@@ -81,6 +82,8 @@ struct mamute_ctx {
   // scratch (grow-only)
   DevBuf coefA, coefM, srho, pool[2], psi[2], acc, slots, tstore, dint, rint, dtmp, partial, misfit;
   DevBuf ident, rcolptr, rcols, ecol, srcw;  // receiver-node combination (trilinear)
+  DevBuf smA, smMat, smLam;                  // gradient smoothing scratch
+  DevBuf rsPtr, rsCol, rsW, dmod, ddat;      // time resampling: matrix, model- and data-axis traces
   DevBuf items, vols, maps, cmaps, recptr, rec, colmap, gx, gy, gz, cells, gvals, srccell,
       aitems, arecptr, arec, acolmap, acells, agvals;
   DevBuf hvel, hrho, hseis, hobs, hgrad, hphess;  // staging for the *_host calls
@@ -772,6 +775,158 @@ int check_common(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     if (rc_ != MAMUTE_OK) return rc_; \
   } while (0)
 
+// Gradient smoothing by the DCT-II diagonalisation of the Bessel / Laplace
+// operators (see postproc.cu): forward transforms along x, y, z, the
+// spectral multiplier, transposed transforms along z, y, x.
+int do_smooth(mamute_ctx* ctx, int nx, int ny, int nz, double h, int mode, const float* lengths,
+              const float* in, float* out) {
+  const long long n = (long long)nx * ny * nz;
+  if (mode == 0) {
+    if (in != out) CK(cudaMemcpyAsync(out, in, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    return MAMUTE_OK;
+  }
+  const int dims[3] = {nx, ny, nz};
+  double L[3];
+  for (int a = 0; a < 3; ++a) {
+    const double l = lengths ? (double)lengths[a] : 0.0;
+    if (!(l >= 0.0)) return fail(ctx, MAMUTE_EINVAL, "smoothing length %d is negative", a);
+    L[a] = l > 0.0 ? l : 2.0 * h;
+  }
+  // C_a (orthonormal DCT-II, rows = modes) and its transpose, per axis, and
+  // the eigenvalues of -l_a^2 D_aa.
+  std::vector<float> mats, lam;
+  size_t off[3][2];
+  for (int a = 0; a < 3; ++a) {
+    const int m = dims[a];
+    off[a][0] = mats.size();
+    mats.resize(mats.size() + (size_t)m * m);
+    off[a][1] = mats.size();
+    mats.resize(mats.size() + (size_t)m * m);
+    for (int k = 0; k < m; ++k)
+      for (int i = 0; i < m; ++i) {
+        const double sc = k == 0 ? std::sqrt(1.0 / m) : std::sqrt(2.0 / m);
+        const float c = (float)(sc * std::cos(M_PI * k * (i + 0.5) / m));
+        mats[off[a][0] + (size_t)k * m + i] = c;
+        mats[off[a][1] + (size_t)i * m + k] = c;
+      }
+    for (int k = 0; k < m; ++k) {
+      const double sn = std::sin(M_PI * k / (2.0 * m));
+      lam.push_back((float)(4.0 * (L[a] / h) * (L[a] / h) * sn * sn));
+    }
+  }
+  CK(upload(ctx->smMat, mats, ctx->stream));
+  CK(upload(ctx->smLam, lam, ctx->stream));
+  CK(ensure(ctx->smA, (size_t)n * 4));
+  const float* M = (const float*)ctx->smMat.p;
+  float* A = (float*)ctx->smA.p;
+  // axis geometry: lines, inner, outer, stride
+  const long long g[3][4] = {{(long long)ny * nz, 1, nx, 1},
+                             {(long long)nz * nx, nx, (long long)nx * ny, nx},
+                             {(long long)nx * ny, (long long)nx * ny, 0, (long long)nx * ny}};
+  auto pass = [&](int a, int inv, const float* src, float* dst) -> cudaError_t {
+    ++ctx->launches;
+    return launch_axis(src, dst, M + off[a][inv], dims[a], g[a][0], g[a][1], g[a][2], g[a][3],
+                       ctx->stream);
+  };
+  CK(pass(0, 0, in, A));
+  CK(pass(1, 0, A, out));
+  CK(pass(2, 0, out, A));
+  ++ctx->launches;
+  CK(launch_spectral_scale(A, nx, ny, nz, (const float*)ctx->smLam.p, mode, ctx->stream));
+  CK(pass(2, 1, A, out));
+  CK(pass(1, 1, out, A));
+  CK(pass(0, 1, A, out));
+  return MAMUTE_OK;
+}
+
+// Rows of the resampling matrix (or of its transpose) as CSR, weights in
+// FP64 (see mamute_resample in the header for the definitions).
+void resample_csr(int nt_in, double dt_in, int nt_out, double dt_out, int mode, bool transpose,
+                  std::vector<int>& ptr, std::vector<int>& col, std::vector<float>& w) {
+  std::vector<std::vector<std::pair<int, double>>> rows(nt_out);
+  if (mode == MAMUTE_INTERP_NEAREST) {
+    for (int m = 0; m < nt_out; ++m) {
+      const long long nn = (long long)std::floor(m * dt_out / dt_in + 0.5);
+      if (nn >= 0 && nn < nt_in) rows[m].push_back({(int)nn, 1.0});
+    }
+  } else {
+    const int W = 8;
+    const double D = std::max(dt_in, dt_out);
+    for (int m = 0; m < nt_out; ++m) {
+      const double c = m * dt_out / dt_in, half = W * D / dt_in;
+      const long long lo = std::max(0LL, (long long)std::floor(c - half) - 1);
+      const long long hi = std::min((long long)nt_in - 1, (long long)std::ceil(c + half) + 1);
+      for (long long nn = lo; nn <= hi; ++nn) {
+        const double u = (m * dt_out - nn * dt_in) / D;
+        if (!(std::fabs(u) < W)) continue;
+        const double sinc = u == 0.0 ? 1.0 : std::sin(M_PI * u) / (M_PI * u);
+        const double hann = 0.5 * (1.0 + std::cos(M_PI * u / W));
+        rows[m].push_back({(int)nn, dt_in / D * sinc * hann});
+      }
+    }
+  }
+  ptr.clear();
+  col.clear();
+  w.clear();
+  if (!transpose) {
+    ptr.push_back(0);
+    for (int m = 0; m < nt_out; ++m) {
+      for (auto& e : rows[m]) {
+        col.push_back(e.first);
+        w.push_back((float)e.second);
+      }
+      ptr.push_back((int)col.size());
+    }
+    return;
+  }
+  std::vector<std::vector<std::pair<int, double>>> cols(nt_in);
+  for (int m = 0; m < nt_out; ++m)
+    for (auto& e : rows[m]) cols[e.first].push_back({m, e.second});
+  ptr.push_back(0);
+  for (int nn = 0; nn < nt_in; ++nn) {
+    for (auto& e : cols[nn]) {
+      col.push_back(e.first);
+      w.push_back((float)e.second);
+    }
+    ptr.push_back((int)col.size());
+  }
+}
+
+int do_resample(mamute_ctx* ctx, int ntr, int nt_in, double dt_in, int nt_out, double dt_out,
+                int mode, int adjoint, const float* x, float* y) {
+  if (ntr < 0 || nt_in < 1 || nt_out < 1 || !(dt_in > 0.0) || !(dt_out > 0.0) ||
+      (mode != MAMUTE_INTERP_NEAREST && mode != MAMUTE_INTERP_SINC))
+    return fail(ctx, MAMUTE_EINVAL, "resample: bad sizes, steps or mode");
+  if (ntr == 0) return MAMUTE_OK;
+  if (!x || !y) return fail(ctx, MAMUTE_EINVAL, "resample: NULL trace array");
+  std::vector<int> ptr, col;
+  std::vector<float> w;
+  resample_csr(nt_in, dt_in, nt_out, dt_out, mode, adjoint != 0, ptr, col, w);
+  CK(upload(ctx->rsPtr, ptr, ctx->stream));
+  CK(upload(ctx->rsCol, col, ctx->stream));
+  CK(upload(ctx->rsW, w, ctx->stream));
+  ++ctx->launches;
+  const int n_src = adjoint ? nt_out : nt_in, n_dst = adjoint ? nt_in : nt_out;
+  CK(launch_csr_rows(x, n_src, (const int*)ctx->rsPtr.p, (const int*)ctx->rsCol.p,
+                     (const float*)ctx->rsW.p, n_dst, ntr, y, ctx->stream));
+  return MAMUTE_OK;
+}
+
+// Data time axis of a call: nt_data samples of dt_data (time_interp != 0),
+// else the modelling axis.
+int check_interp(mamute_ctx* ctx, const mamute_grid* g, const mamute_opts* opts, int* ti,
+                 int* ntd) {
+  *ti = opts ? opts->time_interp : 0;
+  *ntd = g->nt;
+  if (*ti == 0) return MAMUTE_OK;
+  if (*ti != MAMUTE_INTERP_NEAREST && *ti != MAMUTE_INTERP_SINC)
+    return fail(ctx, MAMUTE_EINVAL, "time_interp must be 0, 1 or 2");
+  if (opts->nt_data < 1 || !(opts->dt_data > 0.f))
+    return fail(ctx, MAMUTE_EINVAL, "time_interp needs nt_data >= 1 and dt_data > 0");
+  *ntd = opts->nt_data;
+  return MAMUTE_OK;
+}
+
 // Samples [n0, n1) of the recorded data (internal [nt][ncol] layout) into
 // the user's seis[n_rec][nt]: a transpose when every receiver is one node,
 // else a transpose to per-node rows followed by the fixed-order sum of each
@@ -801,6 +956,8 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
                  opts ? opts->aperture : nullptr, P, opts ? opts->tiles : nullptr));
   ctx->max_planes = P.Nz;
   if (P.ncol > 0 && !seis) return fail(ctx, MAMUTE_EINVAL, "seis is NULL");
+  int ti = 0, ntd = P.nt;
+  TRY(check_interp(ctx, g, opts, &ti, &ntd));
   TRY(check_cfl(ctx, P, vel));
   const bool ph = opts && opts->phess;
   TRY(setup(ctx, P, vel, rho, false, ph));
@@ -813,7 +970,9 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   // The time loop is captured into a CUDA graph and replayed while the plan,
   // the buffers and the wavelet stay the same (MAMUTE_GRAPHS=0 disables).
   std::vector<unsigned long long> key;
-  const bool stream_out = host_seis != nullptr && P.ncol > 0;
+  // Seismograms stream to the host during the loop unless they are resampled
+  // to a data time axis first.
+  const bool stream_out = host_seis != nullptr && P.ncol > 0 && ti == 0;
   const bool use_graph = env_int("MAMUTE_GRAPHS", 1) != 0 && P.nt >= 8;
   if (use_graph) {
     auto push = [&](const void* p) { key.push_back((unsigned long long)(uintptr_t)p); };
@@ -920,8 +1079,19 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
     ctx->step_launches = P.nt;
     ctx->launches += P.nt + (stream_out ? std::min(P.nt, 8) * (P.one_node ? 1 : 2) : 0);
   }
-  if (!stream_out)
-    TRY(data_to_user(ctx, P, 0, P.nt, seis, ctx->stream));
+  if (!stream_out) {
+    if (ti == 0) {
+      TRY(data_to_user(ctx, P, 0, P.nt, seis, ctx->stream));
+    } else if (P.ncol > 0) {
+      CK(ensure(ctx->dmod, (size_t)P.nrec * P.nt * 4));
+      TRY(data_to_user(ctx, P, 0, P.nt, (float*)ctx->dmod.p, ctx->stream));
+      TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 0,
+                      (const float*)ctx->dmod.p, seis));
+    }
+    if (host_seis && P.ncol > 0)
+      CK(cudaMemcpyAsync(host_seis, seis, (size_t)P.nrec * ntd * 4, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  }
   if (ph) {
     FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
                     P.nx, P.ny, P.nz, P.b, P.dt, 1, 0, opts->phess};
@@ -942,6 +1112,10 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
                  opts ? opts->aperture : nullptr, P, opts ? opts->tiles : nullptr));
   ctx->max_planes = P.Nz;
   if (P.ncol > 0 && !d_in) return fail(ctx, MAMUTE_EINVAL, "data is NULL");
+  int ti = 0, ntd = P.nt;
+  TRY(check_interp(ctx, g, opts, &ti, &ntd));
+  const int smode = opts ? opts->smooth_mode : 0;
+  if (smode < 0 || smode > 2) return fail(ctx, MAMUTE_EINVAL, "smooth_mode must be 0, 1 or 2");
   TRY(check_cfl(ctx, P, vel));
   const bool ph = opts && opts->phess;
   TRY(setup(ctx, P, vel, rho, true, true));
@@ -949,7 +1123,7 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   const size_t ncol = std::max(P.ncol, 1);
   CK(ensure(ctx->dint, (size_t)P.nt * ncol * 4));
   CK(ensure(ctx->rint, (size_t)P.nt * ncol * 4));
-  CK(ensure(ctx->partial, (size_t)std::max(misfit_blocks((long long)P.nt * P.nrec), 1) * 8));
+  CK(ensure(ctx->partial, (size_t)std::max(misfit_blocks((long long)ntd * P.nrec), 1) * 8));
   for (int i = 0; i < 2; ++i) {
     CK(cudaMemsetAsync(ctx->pool[i].p, 0, pool, ctx->stream));
     CK(cudaMemsetAsync(ctx->psi[i].p, 0, pool, ctx->stream));
@@ -1081,8 +1255,29 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   // go through the user layout: seis (scratch) = data_out(d_int), then
   // r_int = data_in(seis - d_obs) in the adjoint order.
   auto make_residual = [&]() -> int {
+    CK(ensure(ctx->dtmp, (size_t)P.nt * ncol * 4));
+    if (ti != 0) {
+      // Data on their own time axis: d = K d_model, r = d - d_obs, and the
+      // adjoint source on the modelling axis is K^T r.
+      CK(ensure(ctx->ddat, (size_t)std::max(P.nrec, 1) * ntd * 4));
+      float* dmodel = (float*)ctx->dtmp.p;
+      float* ddata = (float*)ctx->ddat.p;
+      if (residual_mode) {
+        TRY(data_to_user(ctx, P, 0, P.nt, dmodel, ctx->stream));
+        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 0, dmodel, ddata));
+        ctx->launches += 3;
+        CK(launch_misfit(ddata, d_in, (long long)ntd * P.nrec, (double*)ctx->partial.p,
+                         (double*)ctx->misfit.p, ctx->stream));
+        CK(launch_sub(ddata, d_in, (long long)ntd * P.nrec, ddata, ctx->stream));
+        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 1, ddata, dmodel));
+      } else {
+        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 1, d_in, dmodel));
+      }
+      CK(aux_count(ctx, launch_data_in(dmodel, (const int*)ctx->acolmap.p, P.nt, P.ncol, nullptr,
+                                       -1.0f, (float*)ctx->rint.p, nullptr, nullptr, ctx->stream)));
+      return MAMUTE_OK;
+    }
     if (residual_mode) {
-      CK(ensure(ctx->dtmp, (size_t)P.nt * ncol * 4));
       TRY(data_to_user(ctx, P, 0, P.nt, (float*)ctx->dtmp.p, ctx->stream));
       // r = seis - d_obs: first r_int = -(-seis) then subtract d_obs.
       CK(aux_count(ctx, launch_data_in((const float*)ctx->dtmp.p, (const int*)ctx->acolmap.p, P.nt, P.ncol,
@@ -1189,9 +1384,16 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
       }
     }
   }
+  // MultiplyAdjoint, GradientPreconditioning, ZeroesNearSurface (Algorithm 3).
+  const int ztop = opts ? std::max(0, std::min(opts->zero_top_planes, P.nz)) : 0;
   FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
-                  P.nx, P.ny, P.nz, P.b, P.dt, 0, opts ? opts->zero_top_planes : 0, grad};
+                  P.nx, P.ny, P.nz, P.b, P.dt, 0, smode ? 0 : ztop, grad};
   CK(aux_count(ctx, launch_finalize(fa, ctx->stream)));
+  if (smode) {
+    TRY(do_smooth(ctx, P.nx, P.ny, P.nz, P.h, smode, opts->smooth_len, grad, grad));
+    if (ztop > 0)
+      CK(cudaMemsetAsync(grad, 0, (size_t)ztop * P.nx * P.ny * 4, ctx->stream));
+  }
   if (misfit) {
     double J = 0.0;
     CK(cudaMemcpyAsync(&J, ctx->misfit.p, sizeof J, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1494,7 +1696,8 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
                    &ctx->gnV, &ctx->gnRe, &ctx->gnIm, &ctx->gnS, &ctx->gnR, &ctx->gnW,
                    &ctx->gnBins, &ctx->gnWts, &ctx->gnRow, &ctx->nnPartial, &ctx->nnLoss,
                    &ctx->slotmaps, &ctx->ident, &ctx->rcolptr, &ctx->rcols, &ctx->ecol,
-                   &ctx->srcw};
+                   &ctx->srcw, &ctx->smA, &ctx->smMat, &ctx->smLam, &ctx->rsPtr, &ctx->rsCol,
+                   &ctx->rsW, &ctx->dmod, &ctx->ddat};
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);
@@ -1534,8 +1737,10 @@ int mamute_model_host(mamute_ctx* ctx, const mamute_grid* g, const float* vel, c
                       const float* rec_xyz, const mamute_opts* opts, float* seis) {
   if (!ctx || !g || !vel || !rec_offset || n_src < 1) return MAMUTE_EINVAL;
   TRY(check_common(ctx, g, vel, wavelet));
+  int ti = 0, ntd = g->nt;
+  TRY(check_interp(ctx, g, opts, &ti, &ntd));
   const size_t nm = (size_t)g->nx * g->ny * g->nz * 4;
-  const size_t ns = (size_t)rec_offset[n_src] * g->nt * 4;
+  const size_t ns = (size_t)rec_offset[n_src] * ntd * 4;
   CK(ensure(ctx->hvel, nm));
   CK(cudaMemcpyAsync(ctx->hvel.p, vel, nm, cudaMemcpyHostToDevice, ctx->stream));
   if (rho) {
@@ -1565,8 +1770,10 @@ int mamute_gradient_host(mamute_ctx* ctx, const mamute_grid* g, const float* vel
                          const mamute_opts* opts, double* misfit, float* grad) {
   if (!ctx || !g || !vel || !rec_offset || n_src < 1 || !grad) return MAMUTE_EINVAL;
   TRY(check_common(ctx, g, vel, wavelet));
+  int ti = 0, ntd = g->nt;
+  TRY(check_interp(ctx, g, opts, &ti, &ntd));
   const size_t nm = (size_t)g->nx * g->ny * g->nz * 4;
-  const size_t ns = (size_t)rec_offset[n_src] * g->nt * 4;
+  const size_t ns = (size_t)rec_offset[n_src] * ntd * 4;
   CK(ensure(ctx->hvel, nm));
   CK(cudaMemcpyAsync(ctx->hvel.p, vel, nm, cudaMemcpyHostToDevice, ctx->stream));
   if (rho) {
@@ -1725,6 +1932,22 @@ int mamute_nn_features(mamute_ctx* ctx, long long n, const float* vel, const flo
     std::memcpy(pmax, &bits, 4);
     return MAMUTE_OK;
   }
+  return nn_end(ctx);
+}
+
+int mamute_smooth(mamute_ctx* ctx, int nx, int ny, int nz, float h, int mode,
+                  const float* lengths, const float* in, float* out) {
+  TRY(nn_begin(ctx));
+  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.f) || mode < 0 || mode > 2 || !in || !out)
+    return fail(ctx, MAMUTE_EINVAL, "smooth: bad arguments");
+  TRY(do_smooth(ctx, nx, ny, nz, h, mode, lengths, in, out));
+  return nn_end(ctx);
+}
+
+int mamute_resample(mamute_ctx* ctx, int n_traces, int nt_in, float dt_in, int nt_out,
+                    float dt_out, int mode, int adjoint, const float* x, float* y) {
+  TRY(nn_begin(ctx));
+  TRY(do_resample(ctx, n_traces, nt_in, dt_in, nt_out, dt_out, mode, adjoint, x, y));
   return nn_end(ctx);
 }
 

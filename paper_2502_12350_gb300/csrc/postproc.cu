@@ -1,0 +1,154 @@
+// Gradient smoothing filters and seismic-data time resampling.
+//
+// Smoothing (Sec. 2, FWI gradient preconditioning: Bessel or Laplace filter
+// with lengths lx, ly, lz; Algorithm 3: GradientPreconditioning).  Both
+// filters are inverses of constant-coefficient operators built from the
+// 3-point second difference with reflecting ends, which the orthonormal
+// DCT-II diagonalises along each axis with eigenvalues
+//   lambda_a(k) = 4 (l_a / h)^2 sin^2(pi k / (2 n_a)).
+// The Bessel filter (I - sum_a l_a^2 D_aa)^-1 multiplies mode k by
+// 1 / (1 + sum_a lambda_a), the Laplace filter prod_a (I - l_a^2 D_aa)^-1 by
+// prod_a 1 / (1 + lambda_a).  The transform along an axis is a dense
+// n x n contraction applied to every line of the volume (axis_kernel, a
+// shared-memory tiled FP32 product); forward along x, y, z, the spectral
+// scaling, and the transposed transforms along z, y, x give the exact solve.
+//
+// Resampling (Sec. 2: time interpolation by nearest neighbour or sinc;
+// Table 1 Interpolate).  The resampling of every trace is the same sparse
+// matrix, built on the host in FP64 (see api.cu) and applied as CSR rows to
+// each trace (csr_rows_kernel); its transpose is another CSR matrix.
+#include "postproc.h"
+
+namespace mamute {
+
+namespace {
+
+constexpr int kTL = 64, kTI = 64, kTK = 16;
+
+// out[L, i] = sum_j M[i][j] in[L, j] for the lines L of one axis:
+// element (L, j) sits at (L / inner) * outer + (L % inner) + j * astride.
+__global__ void __launch_bounds__(256) axis_kernel(const float* __restrict__ in,
+                                                   float* __restrict__ out,
+                                                   const float* __restrict__ M, int n,
+                                                   long long lines, long long inner,
+                                                   long long outer, long long astride) {
+  __shared__ float As[kTK][kTL + 1];
+  __shared__ float Bs[kTK][kTI + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const long long L0 = (long long)blockIdx.x * kTL;
+  const int i0 = blockIdx.y * kTI;
+  float acc[4][4] = {};
+  for (int j0 = 0; j0 < n; j0 += kTK) {
+    for (int e = threadIdx.x; e < kTL * kTK; e += 256) {
+      const int l = e % kTL, jj = e / kTL;
+      const long long L = L0 + l;
+      const int j = j0 + jj;
+      float v = 0.0f;
+      if (L < lines && j < n) v = in[(L / inner) * outer + (L % inner) + (long long)j * astride];
+      As[jj][l] = v;
+    }
+    for (int e = threadIdx.x; e < kTI * kTK; e += 256) {
+      const int jj = e % kTK, ii = e / kTK;
+      const int i = i0 + ii, j = j0 + jj;
+      Bs[jj][ii] = (i < n && j < n) ? M[(long long)i * n + j] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kTK; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        a[r] = As[k][ty * 4 + r];
+        b[r] = Bs[k][tx * 4 + r];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const long long L = L0 + ty * 4 + r;
+    if (L >= lines) continue;
+    const long long base = (L / inner) * outer + (L % inner);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + tx * 4 + c;
+      if (i < n) out[base + (long long)i * astride] = acc[r][c];
+    }
+  }
+}
+
+// Spectral multiplier of the filter on DCT coefficients [nz][ny][nx].
+__global__ void scale_kernel(float* __restrict__ u, int nx, int ny, int nz,
+                             const float* __restrict__ lam, int mode) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = (int)(p / ((long long)nx * ny));
+    const float lx = lam[x], ly = lam[nx + y], lz = lam[nx + ny + z];
+    const float m = mode == 1 ? 1.0f / (1.0f + lx + ly + lz)
+                              : 1.0f / ((1.0f + lx) * (1.0f + ly) * (1.0f + lz));
+    u[p] *= m;
+  }
+}
+
+__global__ void csr_rows_kernel(const float* __restrict__ x, int n_in, const int* __restrict__ ptr,
+                                const int* __restrict__ col, const float* __restrict__ w,
+                                int n_out, int n_traces, float* __restrict__ y) {
+  const int r = blockIdx.x;  // trace
+  if (r >= n_traces) return;
+  const float* xr = x + (long long)r * n_in;
+  for (int m = blockIdx.y * blockDim.x + threadIdx.x; m < n_out; m += gridDim.y * blockDim.x) {
+    float v = 0.0f;
+    for (int k = ptr[m]; k < ptr[m + 1]; ++k) v = fmaf(w[k], xr[col[k]], v);
+    y[(long long)r * n_out + m] = v;
+  }
+}
+
+__global__ void sub_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                           float* __restrict__ out) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x)
+    out[p] = a[p] - b[p];
+}
+
+}  // namespace
+
+cudaError_t launch_sub(const float* a, const float* b, long long n, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blk = (n + 255) / 256;
+  if (blk > 152 * 16) blk = 152 * 16;
+  sub_kernel<<<(unsigned)blk, 256, 0, s>>>(a, b, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axis(const float* in, float* out, const float* M, int n, long long lines,
+                        long long inner, long long outer, long long astride, cudaStream_t s) {
+  if (lines <= 0 || n <= 0) return cudaSuccess;
+  dim3 g((unsigned)((lines + kTL - 1) / kTL), (unsigned)((n + kTI - 1) / kTI));
+  axis_kernel<<<g, 256, 0, s>>>(in, out, M, n, lines, inner, outer, astride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectral_scale(float* u, int nx, int ny, int nz, const float* lam, int mode,
+                                  cudaStream_t s) {
+  const long long n = (long long)nx * ny * nz;
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  scale_kernel<<<(unsigned)b, 256, 0, s>>>(u, nx, ny, nz, lam, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_rows(const float* x, int n_in, const int* ptr, const int* col,
+                            const float* w, int n_out, int n_traces, float* y, cudaStream_t s) {
+  if (n_traces <= 0 || n_out <= 0) return cudaSuccess;
+  const int by = (n_out + 127) / 128;
+  dim3 g((unsigned)n_traces, (unsigned)(by < 16 ? by : 16));
+  csr_rows_kernel<<<g, 128, 0, s>>>(x, n_in, ptr, col, w, n_out, n_traces, y);
+  return cudaGetLastError();
+}
+
+}  // namespace mamute

@@ -40,7 +40,13 @@ class Grid(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("check_mem", ctypes.c_float), ("n_snapshots", ctypes.c_int),
                 ("zero_top_planes", ctypes.c_int), ("aperture", ctypes.c_void_p),
-                ("phess", ctypes.c_void_p), ("tiles", ctypes.c_int * 6)]
+                ("phess", ctypes.c_void_p), ("tiles", ctypes.c_int * 6),
+                ("smooth_mode", ctypes.c_int), ("smooth_len", ctypes.c_float * 3),
+                ("time_interp", ctypes.c_int), ("nt_data", ctypes.c_int),
+                ("dt_data", ctypes.c_float)]
+
+SMOOTH_NONE, SMOOTH_BESSEL, SMOOTH_LAPLACE = 0, 1, 2
+INTERP_NEAREST, INTERP_SINC = 1, 2
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -69,6 +75,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             lib.mamute_gn_diagonal.argtypes = common + [F, P]
             lib.mamute_revolve_plan.argtypes = [I, I, ctypes.POINTER(ctypes.c_longlong),
                                                 ctypes.POINTER(I), P]
+            lib.mamute_smooth.argtypes = [P, I, I, I, F, I, P, P, P]
+            lib.mamute_resample.argtypes = [P, I, I, F, I, F, I, I, P, P]
             _lib = lib
     return _lib
 
@@ -151,12 +159,15 @@ class Context:
 
     @staticmethod
     def _opts(check_mem=0.8, n_snapshots=0, zero_top_planes=0, aperture=None, phess=None,
-              tiles=None):
+              tiles=None, smooth_mode=0, smooth_len=(0.0, 0.0, 0.0), time_interp=0, nt_data=0,
+              dt_data=0.0):
         ap = None if aperture is None else np.ascontiguousarray(aperture, np.int32)
         o = Opts(check_mem, n_snapshots, zero_top_planes,
                  None if ap is None else ap.ctypes.data, None if phess is None else phess.data_ptr()
                  if not isinstance(phess, np.ndarray) else phess.ctypes.data,
-                 (ctypes.c_int * 6)(*(list(tiles) if tiles is not None else [0] * 6)))
+                 (ctypes.c_int * 6)(*(list(tiles) if tiles is not None else [0] * 6)),
+                 int(smooth_mode), (ctypes.c_float * 3)(*[float(v) for v in smooth_len]),
+                 int(time_interp), int(nt_data), float(dt_data))
         return o, ap
 
     def model(self, grid: Grid, vel, rho, src_xyz, wavelet, rec_offset, rec_xyz, seis, **opts):
@@ -203,6 +214,27 @@ class Context:
                                             len(src), _ptr(src), _ptr(wav), _ptr(off), _ptr(rec),
                                             _ptr(d_res), ctypes.byref(o), _ptr(grad)))
 
+
+    def smooth(self, h: float, mode: int, inp, out, lengths=None):
+        """Bessel (mode 1) or Laplace (mode 2) filter of a [nz][ny][nx] tensor."""
+        nz, ny, nx = inp.shape
+        ln = None if lengths is None else np.ascontiguousarray(lengths, np.float32)
+        self._check(self.lib.mamute_smooth(self._h, nx, ny, nz, ctypes.c_float(h), int(mode),
+                                           _ptr(ln), _ptr(inp), _ptr(out)))
+
+    def resample(self, x, dt_in: float, nt_out: int, dt_out: float, mode: int, y,
+                 adjoint: bool = False, nt_in: int | None = None):
+        """Resamples the rows of x [n][nt_in] into y [n][nt_out] (mode 1
+        nearest, 2 sinc); adjoint=True applies the transpose (x [n][nt_out]
+        -> y [n][nt_in])."""
+        n = x.shape[0]
+        if adjoint:
+            nt_in = y.shape[1]
+        else:
+            nt_in = x.shape[1]
+        self._check(self.lib.mamute_resample(self._h, n, nt_in, ctypes.c_float(dt_in), nt_out,
+                                             ctypes.c_float(dt_out), int(mode), int(adjoint),
+                                             _ptr(x), _ptr(y)))
 
     def gn_diagonal(self, grid: Grid, vel, rho, src_xyz, wavelet, rec_offset, rec_xyz, hdiag,
                     band_rel: float = 1e-4):
