@@ -31,7 +31,7 @@ def cosine(a, b):
     return a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("shape", [(18, 20, 24), (40, 66, 70), (5, 3, 130)])
+@pytest.mark.parametrize("shape", [(18, 20, 24), (20, 36, 70), (5, 3, 130)])
 @pytest.mark.parametrize("mode", [1, 2])
 def test_smooth_matches_oracle(ctx, shape, mode):
     rng = np.random.default_rng(sum(shape) + mode)
@@ -53,6 +53,9 @@ def test_smooth_matches_oracle(ctx, shape, mode):
 @pytest.mark.parametrize("mode", [1, 2])
 def test_resample_matches_oracle(ctx, case, mode):
     nt_in, dt_in, nt_out, dt_out = case
+    # the library takes FP32 steps; the oracle gets the same values, so both
+    # take the nearest-sample decisions on the same numbers (in FP64)
+    dt_in, dt_out = float(np.float32(dt_in)), float(np.float32(dt_out))
     rng = np.random.default_rng(nt_in + mode)
     x = rng.standard_normal((37, nt_in)).astype(np.float32)
     name = {1: "nearest", 2: "sinc"}[mode]
@@ -118,7 +121,8 @@ def test_model_and_gradient_on_a_data_time_axis(ctx, oracle, mode):
     from paper_2502_12350_gb300 import mamute
     w = _case()
     name = {1: "nearest", 2: "sinc"}[mode]
-    dt_data, nt_data = 2.5 * w.dt, 25
+    dt_data, nt_data = float(np.float32(2.5 * w.dt)), 25
+    w.dt = float(np.float32(w.dt))
     og = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
     d = oracle.model(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho)
     Kd = postproc.resample(d, w.dt, nt_data, dt_data, name)
