@@ -73,10 +73,10 @@ def test_resample_matches_oracle(ctx, case, mode):
     refT = postproc.resample(r, dt_in, None, dt_out, name, adjoint=True, nt_in=nt_in)
     yt = torch.full((37, nt_in), float("nan"), device=dev)
     ctx.resample(torch.from_numpy(r).to(dev), dt_in, nt_out, dt_out, mode, yt, adjoint=True)
-    if mode == 1:
-        np.testing.assert_array_equal(yt.cpu().numpy(), refT.astype(np.float32))
-    else:
-        assert rel(yt.cpu().numpy(), refT) <= 1e-5
+    # (nearest: several outputs may share a sample, whose transpose sums them in FP32)
+    assert rel(yt.cpu().numpy(), refT) <= (1e-6 if mode == 1 else 1e-5)
+    if mode == 1:  # the index decisions themselves: the same support exactly
+        np.testing.assert_array_equal(yt.cpu().numpy() != 0, refT != 0)
 
 
 def _case():
