@@ -46,6 +46,16 @@ struct DevBuf {
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+// A receiver's node with non-zero weight (nearest node: one per receiver;
+// trilinear: up to 8), in the shot window's local padded coordinates.
+struct NodeEntry {
+  int lx, ly, lz;
+  long long cell;  // model cell of the node
+  int r;           // receiver
+  int shot;
+  float w;         // interpolation weight
+};
+
 struct Plan {
   int nx, ny, nz, b, Nx, Ny, Nz, pitchG, nt;
   double h, dt;
@@ -70,6 +80,17 @@ struct Plan {
   long long pool_elems = 0, term_elems = 0;
   int ncol = 0;   // internal data columns (receiver nodes)
   int nrec = 0;   // receivers
+  std::vector<NodeEntry> ent;      // receiver nodes (input of the receiver tables)
+  std::vector<int> fwd_col_of_ent; // forward-table column of each receiver node
+  // two-level (temporal blocking) forward launches
+  bool pairs = false;
+  int ptx = 0, pty = 0;
+  std::vector<WorkItem> pitems;
+  std::vector<int4> pnbr;
+  std::vector<int> prec_ptr;
+  std::vector<RecEntry> prec;
+  std::vector<long long> prec_cell;
+  std::vector<float> prec_g;
 };
 
 }  // namespace
@@ -83,6 +104,8 @@ struct mamute_ctx {
   DevBuf coefA, coefM, srho, pool[2], psi[2], acc, slots, tstore, dint, rint, dtmp, partial, misfit;
   DevBuf ident, rcolptr, rcols, ecol, srcw;  // receiver-node combination (trilinear)
   DevBuf smA, smMat, smLam;                  // gradient smoothing scratch
+  DevBuf pitems, pnbr, precptr, prec, pcells, pgvals, pmaps, pflags;  // two-level launches
+  bool pair_graph_failed = false;  // cooperative launches could not be captured
   DevBuf rsPtr, rsCol, rsW, dmod, ddat;      // time resampling: matrix, model- and data-axis traces
   DevBuf items, vols, maps, cmaps, recptr, rec, colmap, gx, gy, gz, cells, gvals, srccell,
       aitems, arecptr, arec, acolmap, acells, agvals;
@@ -203,22 +226,15 @@ int max_piece(const std::vector<int>& b) {
   return m;
 }
 
-// A receiver's node with non-zero weight (nearest node: one per receiver;
-// trilinear: up to 8), in the shot window's local padded coordinates.
-struct NodeEntry {
-  int lx, ly, lz;
-  long long cell;  // model cell of the node
-  int r;           // receiver
-  int shot;
-  float w;         // interpolation weight
-};
+
 
 // Receiver tables for one tiling (items ordered z block, row, column).
 void build_receivers(Plan& P, int TX, int zsplit, const std::vector<NodeEntry>& ent,
                      const std::vector<int>& item_base, const std::vector<Tiling>& tilings,
                      std::vector<WorkItem>& items, std::vector<int>& rec_ptr,
                      std::vector<RecEntry>& rec, std::vector<long long>& cells,
-                     std::vector<float>& gvals, std::vector<int>& colmap) {
+                     std::vector<float>& gvals, std::vector<int>& colmap,
+                     std::vector<int>* ent_of_col = nullptr) {
   struct Tmp {
     int item, z, lxy, r;
   };
@@ -275,6 +291,10 @@ void build_receivers(Plan& P, int TX, int zsplit, const std::vector<NodeEntry>& 
     cells[i] = E.cell;
     const VolDesc& V = P.vols[E.shot];
     gvals[i] = P.gx[V.gx_off + E.lx] * P.gy[V.gy_off + E.ly] * P.gz[E.lz];
+  }
+  if (ent_of_col) {
+    ent_of_col->assign(t.size(), 0);
+    for (size_t i = 0; i < t.size(); ++i) (*ent_of_col)[i] = t[i].r;
   }
   for (size_t i = 0; i < t.size();) {
     size_t j = i;
@@ -520,8 +540,12 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   };
   std::vector<int> base;
   make_items(fc, P.items, base);
+  std::vector<int> ent_of_col;
   build_receivers(P, P.tx, fc.zsplit, ent, base, fc.tilings, P.items, P.rec_ptr, P.rec,
-                  P.rec_cell, P.rec_g, P.colmap);
+                  P.rec_cell, P.rec_g, P.colmap, &ent_of_col);
+  P.fwd_col_of_ent.assign(ent.size(), 0);
+  for (size_t c = 0; c < ent_of_col.size(); ++c) P.fwd_col_of_ent[ent_of_col[c]] = (int)c;
+  P.ent = ent;
   // receiver -> internal columns of the forward tables, ascending
   P.rcol_ptr.assign(n_rec + 1, 0);
   for (int c = 0; c < P.ncol; ++c) ++P.rcol_ptr[P.colmap[c] + 1];
@@ -775,6 +799,97 @@ int check_common(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     if (rc_ != MAMUTE_OK) return rc_; \
   } while (0)
 
+// Two-level forward launches (stencil_pair.cu): one shot, no free surface,
+// every tile resident at once (one CTA per SM).  Columns of the x split are
+// multiples of 4 and at most TX wide; the rows are split as finely as the
+// SMs allow (at least 8 rows per tile), so that all SMs get a tile.
+bool plan_pairs(mamute_ctx* ctx, Plan& P) {
+  if (env_int("MAMUTE_PAIRS", 1) == 0 || P.vols.size() != 1 || P.zs >= 0 || P.nt < 2) return false;
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  const VolDesc& V = P.vols[0];
+  static const int shapes[][2] = {{72, 32}, {64, 32}, {32, 16}};
+  for (const auto& sh : shapes) {
+    const int TX = sh[0], TY = sh[1];
+    if (!pair_tile_supported(TX, TY)) continue;
+    int occ = 0;
+    PairArgs dummy{};
+    if (launch_pair(dummy, 0, V.Nz, TX, TY, P.dens, nullptr, &occ) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const int ncols = (V.Nx + TX - 1) / TX;
+    const long long slots = (long long)occ * n_sm;
+    const int need_rows = (V.Ny + TY - 1) / TY;
+    if ((long long)ncols * need_rows > slots) continue;
+    int nrows = (int)std::min<long long>(slots / ncols, (V.Ny + 7) / 8);
+    nrows = std::max(nrows, need_rows);
+    Tiling T;
+    T.xs = split(V.Nx, ncols, 4);
+    T.ys = split(V.Ny, nrows, 1);
+    if (max_piece(T.xs) > TX || max_piece(T.ys) > TY) continue;
+    const int nc = (int)T.xs.size() - 1, nr = (int)T.ys.size() - 1;
+    P.pitems.clear();
+    P.pnbr.clear();
+    for (int tj = 0; tj < nr; ++tj)
+      for (int ti = 0; ti < nc; ++ti) {
+        P.pitems.push_back(WorkItem{0, T.xs[ti], T.ys[tj], 0, V.Nz, T.xs[ti + 1] - T.xs[ti],
+                                    T.ys[tj + 1] - T.ys[tj], -1});
+        auto id = [&](int a, int b) { return (a < 0 || a >= nc || b < 0 || b >= nr) ? -1 : b * nc + a; };
+        P.pnbr.push_back(make_int4(id(ti - 1, tj), id(ti + 1, tj), id(ti, tj - 1), id(ti, tj + 1)));
+      }
+    std::vector<int> base(1, 0);
+    std::vector<Tiling> tl(1, T);
+    std::vector<int> colmap, ent_of_col;
+    build_receivers(P, TX, 1, P.ent, base, tl, P.pitems, P.prec_ptr, P.prec, P.prec_cell,
+                    P.prec_g, colmap, &ent_of_col);
+    // the same internal data columns as the one-step tables
+    for (size_t c = 0; c < P.prec.size(); ++c) P.prec[c].col = P.fwd_col_of_ent[ent_of_col[c]];
+    P.ptx = TX;
+    P.pty = TY;
+    P.pairs = true;
+    if (env_int("MAMUTE_VERBOSE", 0))
+      fprintf(stderr, "mamute pairs: tile %dx%d, %d x %d tiles\n", TX, TY, nc, nr);
+    return true;
+  }
+  return false;
+}
+
+// Tables, tensor maps and progress flags of the two-level launches.
+int setup_pairs(mamute_ctx* ctx, const Plan& P, const float* vel, const float* rho) {
+  CK(upload(ctx->pitems, P.pitems, ctx->stream));
+  CK(upload(ctx->pnbr, P.pnbr, ctx->stream));
+  CK(upload(ctx->precptr, P.prec_ptr, ctx->stream));
+  CK(upload(ctx->prec, P.prec, ctx->stream));
+  CK(upload(ctx->pcells, P.prec_cell, ctx->stream));
+  CK(upload(ctx->pgvals, P.prec_g, ctx->stream));
+  GeomArgs ga{vel, rho, (int)P.prec.size(), 0, (const long long*)ctx->pcells.p,
+              (const float*)ctx->pgvals.p, (RecEntry*)ctx->prec.p, nullptr, nullptr, nullptr,
+              P.h, P.dt};
+  CK(aux_count(ctx, launch_geometry(ga, ctx->stream)));
+  const VolDesc& V = P.vols[0];
+  std::vector<PairMaps> pm(1);
+  bool ok = true;
+  for (int b = 0; b < 2; ++b) {
+    const float* base = (const float*)ctx->pool[b].p + V.off;
+    ok = ok && encode3d(ctx, &pm[0].m[b], base, V.Nx, V.Ny, V.Nz, V.pitch, P.ptx + 8, P.pty + 8) ==
+                   CUDA_SUCCESS;
+    ok = ok && encode3d(ctx, &pm[0].m[2 + b], base, V.Nx, V.Ny, V.Nz, V.pitch, P.ptx, P.pty) ==
+                   CUDA_SUCCESS;
+  }
+  ok = ok && encode3d(ctx, &pm[0].m[4], (const float*)ctx->coefA.p, P.Nx, P.Ny, P.Nz, P.pitchG,
+                      P.ptx, P.pty) == CUDA_SUCCESS;
+  if (P.dens)
+    ok = ok && encode3d(ctx, &pm[0].m[5], (const float*)ctx->coefM.p, P.Nx, P.Ny, P.Nz, P.pitchG,
+                        P.ptx, P.pty) == CUDA_SUCCESS;
+  else
+    pm[0].m[5] = pm[0].m[4];
+  if (!ok) return fail(ctx, MAMUTE_ECUDA, "cuTensorMapEncodeTiled failed (two-level maps)");
+  CK(upload(ctx->pmaps, pm, ctx->stream));
+  CK(ensure(ctx->pflags, P.pitems.size() * 4));
+  return MAMUTE_OK;
+}
+
 // Gradient smoothing by the DCT-II diagonalisation of the Bessel / Laplace
 // operators (see postproc.cu): forward transforms along x, y, z, the
 // spectral multiplier, transposed transforms along z, y, x.
@@ -967,13 +1082,20 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   if (ph) CK(cudaMemsetAsync(ctx->acc.p, 0, pool, ctx->stream));
   CK(ensure(ctx->dint, (size_t)P.nt * std::max(P.ncol, 1) * 4));
   const int mode = ph ? MODE_FWD_PH : MODE_FWD;
+  // Two time levels per launch where the problem allows it.
+  const bool pairs = !ph && plan_pairs(ctx, P);
+  if (pairs) {
+    TRY(setup_pairs(ctx, P, vel, rho));
+    CK(cudaMemsetAsync(ctx->pflags.p, 0, P.pitems.size() * 4, ctx->stream));
+  }
   // The time loop is captured into a CUDA graph and replayed while the plan,
   // the buffers and the wavelet stay the same (MAMUTE_GRAPHS=0 disables).
   std::vector<unsigned long long> key;
   // Seismograms stream to the host during the loop unless they are resampled
   // to a data time axis first.
   const bool stream_out = host_seis != nullptr && P.ncol > 0 && ti == 0;
-  const bool use_graph = env_int("MAMUTE_GRAPHS", 1) != 0 && P.nt >= 8;
+  const bool use_graph = env_int("MAMUTE_GRAPHS", 1) != 0 && P.nt >= 8 &&
+                         !(pairs && ctx->pair_graph_failed);
   if (use_graph) {
     auto push = [&](const void* p) { key.push_back((unsigned long long)(uintptr_t)p); };
     key.push_back((unsigned long long)P.nt);
@@ -991,30 +1113,71 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
       std::memcpy(&u, &wavelet[n], 4);
       key.push_back(u);
     }
+    key.push_back(pairs ? (((unsigned long long)P.ptx << 32) | (unsigned)P.pty) : 0);
+    for (const DevBuf* b : {&ctx->pitems, &ctx->pnbr, &ctx->precptr, &ctx->prec, &ctx->pmaps,
+                            &ctx->pflags})
+      push(pairs ? b->p : nullptr);
     key.push_back(stream_out ? 1 : 0);
     if (stream_out) {
       push(seis);
       push(host_seis);
     }
   }
-  auto launch_all = [&]() -> int {
-    if (!stream_out) {
-      for (int n = 0; n < P.nt; ++n) {
-        StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
+  // Steps [t0, t1): pairs of steps (n even) by the two-level kernel, the
+  // rest one at a time.
+  auto run_steps = [&](int t0, int t1) -> int {
+    int n = t0;
+    while (n < t1) {
+      float* drow = (float*)ctx->dint.p + (size_t)n * P.ncol;
+      if (pairs && n % 2 == 0 && n + 1 < t1) {
+        PairArgs a{};
+        a.items = (const WorkItem*)ctx->pitems.p;
+        a.nbrs = (const int4*)ctx->pnbr.p;
+        a.vols = (const VolDesc*)ctx->vols.p;
+        a.pmaps = (const PairMaps*)ctx->pmaps.p;
+        a.gx = (const float*)ctx->gx.p;
+        a.gy = (const float*)ctx->gy.p;
+        a.gz = (const float*)ctx->gz.p;
+        a.wn0 = wavelet[n];
+        a.wn1 = wavelet[n + 1];
+        a.fout1 = (float*)ctx->pool[1].p;
+        a.fout2 = (float*)ctx->pool[0].p;
+        a.rec_ptr = (const int*)ctx->precptr.p;
+        a.rec = (const RecEntry*)ctx->prec.p;
+        a.dout0 = P.ncol > 0 ? drow : nullptr;
+        a.dout1 = P.ncol > 0 ? drow + P.ncol : nullptr;
+        a.flags = (int*)ctx->pflags.p;
+        a.epoch = (n / 2) * P.Nz;
+        a.status = ctx->status;
+        if (ctx->timing && !ctx->ev0_set) {
+          CK(cudaEventRecord(ctx->ev0, ctx->stream));
+          ctx->ev0_set = true;
+        }
+        ++ctx->step_launches;
+        ++ctx->launches;
+        CK(launch_pair(a, (int)P.pitems.size(), P.Nz, P.ptx, P.pty, P.dens, ctx->stream, nullptr));
+        if (ctx->timing) CK(cudaEventRecord(ctx->ev1, ctx->stream));
+        n += 2;
+      } else {
+        StepArgs a = fwd_args(ctx, P, n, wavelet, drow, mode);
         CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+        n += 1;
       }
-      return MAMUTE_OK;
     }
-    // In 8 segments: after each, the copy stream transposes that segment's
-    // samples and copies them to the host while the next segment runs.
+    return MAMUTE_OK;
+  };
+  auto launch_all = [&]() -> int {
+    if (!stream_out) return run_steps(0, P.nt);
+    // In 8 segments (even boundaries, so pairs do not straddle them): after
+    // each, the copy stream transposes that segment's samples and copies them
+    // to the host while the next segment runs.
     const int nseg = std::min(P.nt, 8);
     int t0 = 0;
     for (int k = 0; k < nseg; ++k) {
-      const int t1 = (int)((long long)P.nt * (k + 1) / nseg);
-      for (int n = t0; n < t1; ++n) {
-        StepArgs a = fwd_args(ctx, P, n, wavelet, (float*)ctx->dint.p + (size_t)n * P.ncol, mode);
-        CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
-      }
+      int t1 = (int)((long long)P.nt * (k + 1) / nseg);
+      if (k + 1 < nseg) t1 -= t1 % 2;
+      if (t1 <= t0) continue;
+      TRY(run_steps(t0, t1));
       CK(cudaEventRecord(ctx->seg_ev[k], ctx->stream));
       CK(cudaStreamWaitEvent(ctx->copy, ctx->seg_ev[k], 0));
       TRY(data_to_user(ctx, P, t0, t1, seis, ctx->copy));
@@ -1060,13 +1223,22 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
       ctx->timing = timing;
       ctx->step_launches = sl0;
       ctx->launches = l0;
-      if (rc != MAMUTE_OK) {
-        if (gr) cudaGraphDestroy(gr);
-        return rc;
+      if (e == cudaSuccess && rc == MAMUTE_OK) e = cudaGraphInstantiate(&ctx->graph, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+      if (pairs && (rc != MAMUTE_OK || e != cudaSuccess)) {
+        // Cooperative launches that cannot be captured: run them directly
+        // from now on.
+        cudaGetLastError();
+        if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+        ctx->graph_key.clear();
+        ctx->pair_graph_failed = true;
+        ctx->err.clear();
+        CK(cudaStreamSynchronize(ctx->stream));
+        TRY(launch_all());
+        goto loop_done;
       }
-      CK(e);
-      e = cudaGraphInstantiate(&ctx->graph, gr, 0);
-      cudaGraphDestroy(gr);
+      if (rc != MAMUTE_OK) return rc;
       CK(e);
       ctx->graph_key = key;
     }
@@ -1076,9 +1248,11 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
       CK(cudaEventRecord(ctx->ev1, ctx->stream));
       ctx->ev0_set = true;
     }
-    ctx->step_launches = P.nt;
-    ctx->launches += P.nt + (stream_out ? std::min(P.nt, 8) * (P.one_node ? 1 : 2) : 0);
+    const int loop = pairs ? (P.nt / 2 + P.nt % 2) : P.nt;
+    ctx->step_launches = loop;
+    ctx->launches += loop + (stream_out ? std::min(P.nt, 8) * (P.one_node ? 1 : 2) : 0);
   }
+loop_done:
   if (!stream_out) {
     if (ti == 0) {
       TRY(data_to_user(ctx, P, 0, P.nt, seis, ctx->stream));
@@ -1697,7 +1871,8 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
                    &ctx->gnBins, &ctx->gnWts, &ctx->gnRow, &ctx->nnPartial, &ctx->nnLoss,
                    &ctx->slotmaps, &ctx->ident, &ctx->rcolptr, &ctx->rcols, &ctx->ecol,
                    &ctx->srcw, &ctx->smA, &ctx->smMat, &ctx->smLam, &ctx->rsPtr, &ctx->rsCol,
-                   &ctx->rsW, &ctx->dmod, &ctx->ddat};
+                   &ctx->rsW, &ctx->dmod, &ctx->ddat, &ctx->pitems, &ctx->pnbr, &ctx->precptr,
+                   &ctx->prec, &ctx->pcells, &ctx->pgvals, &ctx->pmaps, &ctx->pflags};
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);

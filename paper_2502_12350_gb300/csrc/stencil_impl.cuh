@@ -353,7 +353,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
         for (int e = 0; e < 4; ++e) {
           const int dx = gxl + e - V.src_x;
           if ((unsigned)dx < 2u) {
-            const float sc = V.src_sc[dx + 2 * dy + 4 * dz];
+            const float sc = a.vols[it.vol].src_sc[dx + 2 * dy + 4 * dz];  // global: dynamic index
             if (sc != 0.0f) out.v[e] += sc * a.wn;
           }
         }
