@@ -276,7 +276,9 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
   for (int r = 0; r < 2; ++r) {
     const int y = y0 + ly0 + r;
     row_ok[r] = ly0 + r < it.h && y < V.Ny;
-    gyv[r] = row_ok[r] ? a.gy[V.gy_off + y] : 0.0f;
+    // Rows past the tile (but inside the window) are computed too, though not
+    // stored: the partner row of a thread is a y neighbour read from registers.
+    gyv[r] = y < V.Ny ? a.gy[V.gy_off + y] : 0.0f;
   }
   float gxv[4];
 #pragma unroll
