@@ -826,8 +826,15 @@ bool plan_pairs(mamute_ctx* ctx, Plan& P) {
     nrows = std::max(nrows, need_rows);
     Tiling T;
     T.xs = split(V.Nx, ncols, 4);
-    T.ys = split(V.Ny, nrows, 1);
+    // Row boundaries are even: a thread's two rows then lie in the same tile,
+    // so the rows it computes past its tile (from halo data that the next
+    // tile may already have overwritten) are never used as neighbours.
+    T.ys = split(V.Ny, nrows, 2);
     if (max_piece(T.xs) > TX || max_piece(T.ys) > TY) continue;
+    // a tile's 4-row halo must stay within its neighbours
+    bool thin = false;
+    for (size_t k = 1; k + 1 < T.ys.size(); ++k) thin = thin || T.ys[k] - T.ys[k - 1] < kHalo;
+    if (thin) continue;
     const int nc = (int)T.xs.size() - 1, nr = (int)T.ys.size() - 1;
     P.pitems.clear();
     P.pnbr.clear();

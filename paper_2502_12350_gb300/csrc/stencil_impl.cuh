@@ -354,7 +354,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
           const int dx = gxl + e - V.src_x;
           if ((unsigned)dx < 2u) {
             const float sc = a.vols[it.vol].src_sc[dx + 2 * dy + 4 * dz];  // global: dynamic index
-            if (sc != 0.0f) out.v[e] += sc * a.wn;
+            if (sc != 0.0f) out.v[e] = __fmaf_rn(sc, a.wn, out.v[e]);
           }
         }
       }

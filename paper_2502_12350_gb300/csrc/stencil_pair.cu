@@ -276,8 +276,9 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
   for (int r = 0; r < 2; ++r) {
     const int y = y0 + ly0 + r;
     row_ok[r] = ly0 + r < it.h && y < V.Ny;
-    // Rows past the tile (but inside the window) are computed too, though not
-    // stored: the partner row of a thread is a y neighbour read from registers.
+    // Tile rows start on even rows, so both rows of a thread are in the tile
+    // or both past it (then computed from halo data but neither stored nor
+    // used); past the window the field is zero.
     gyv[r] = y < V.Ny ? a.gy[V.gy_off + y] : 0.0f;
   }
   float gxv[4];
@@ -306,7 +307,7 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
           const int dx = gxl + e - V.src_x;
           if ((unsigned)dx < 2u) {
             const float sc = a.vols[it.vol].src_sc[dx + 2 * dy + 4 * dz];  // global: dynamic index
-            if (sc != 0.0f) out[r].v[e] += sc * wn;
+            if (sc != 0.0f) out[r].v[e] = __fmaf_rn(sc, wn, out[r].v[e]);
           }
         }
       }
