@@ -33,11 +33,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gpt-updates/s"
 UNIT = "Gpt/s"
-BYTES_PER_PT = 20  # read u^n, u^{n-1}, A, A m2; write u^{n+1}
+
 
 
 KERNEL_SOURCES = ["paper_2502_12350_gb300/csrc/stencil_impl.cuh",
                   "paper_2502_12350_gb300/csrc/stencil_fwd.cu",
+                  "paper_2502_12350_gb300/csrc/stencil_pair.cu",
                   "paper_2502_12350_gb300/csrc/common.cuh"]
 
 
@@ -50,10 +51,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_traffic(w):
-    """DRAM bytes per launch of the forward step from the committed ncu
+def kernel_traffic(w, kernel="step_kernel_forward"):
+    """DRAM bytes per launch of the forward kernel from the committed ncu
     summary of this workload, or None if the kernel source changed since."""
-    path = os.path.join(ROOT, "profiles", f"step_kernel_forward_{w.name}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{w.name}.md")
     try:
         fields = {}
         with open(path) as f:
@@ -582,9 +583,16 @@ def main():
 
     peak, peak_kind = _peaks()
     kernel_ms = statistics.median(loop_ms) / max(step_launches, 1)
-    bpp = BYTES_PER_PT if w.rho is not None else 16
+    # Algorithmic bytes per point and launch: u^n, u^{n-1}, A (and A m2) read
+    # once, one new level written per time step the launch advances (two on
+    # the two-level kernel).
+    steps_per_launch = nt / max(step_launches, 1)
+    two_level = steps_per_launch > 1.5
+    reads = 16 if w.rho is not None else 12
+    bpp = reads + 4 * (2 if two_level else 1)
     achieved = bpp * w.n_padded / (kernel_ms / 1e3) / 1e9
-    traffic = kernel_traffic(w)
+    kname = "pair_kernel_forward" if two_level else "step_kernel_forward"
+    traffic = kernel_traffic(w, kname)
 
     clocks = clk.summary()
     line = {
@@ -603,8 +611,10 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "step_kernel<forward>",
-                     "bytes_per_point": bpp, "kernel_ms": kernel_ms},
+                     "kernel": ("pair_kernel (two time steps per launch)" if two_level
+                                else "step_kernel<forward>"),
+                     "bytes_per_point": bpp, "steps_per_launch": steps_per_launch,
+                     "kernel_ms": kernel_ms},
         "clocks": clocks,
     }
     ctx.close()
