@@ -814,7 +814,11 @@ bool plan_pairs(mamute_ctx* ctx, Plan& P) {
     if (!pair_tile_supported(TX, TY)) continue;
     int occ = 0;
     PairArgs dummy{};
-    if (launch_pair(dummy, 0, V.Nz, TX, TY, P.dens, nullptr, &occ) != cudaSuccess || occ < 1) {
+    const cudaError_t oe = launch_pair(dummy, 0, V.Nz, TX, TY, P.dens, nullptr, &occ);
+    if (env_int("MAMUTE_VERBOSE", 0))
+      fprintf(stderr, "mamute pairs: tile %dx%d: %s, %d CTA(s) per SM\n", TX, TY,
+              cudaGetErrorString(oe), occ);
+    if (oe != cudaSuccess || occ < 1) {
       cudaGetLastError();
       continue;
     }

@@ -109,7 +109,7 @@ struct PairLayout {
   static constexpr int NW = NCT / 32;
   static constexpr int HS = (TX + 2 * kHalo) * (TY + 2 * kHalo);
   static constexpr int CS = TX * TY;
-  static constexpr int NSU = 7;  // u^n halo ring: 5 planes in use, 2 ahead
+  static constexpr int NSU = 6;  // u^n halo ring: 5 planes in use, 1 ahead
   static constexpr int NSC = 2;  // u^{n-1}, A, A m2 of step A
   static constexpr int NSV = 2;  // u^{n+1} halo + A, A m2 of step B
   static constexpr int NCA = DENS ? 3 : 2;  // centre arrays of step A
@@ -142,7 +142,6 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
   uint64_t* emptyC = fullC + NSC;
   uint64_t* fullV = emptyC + NSC;
   uint64_t* emptyV = fullV + NSV;
-  PlaneInfo* pinfo = reinterpret_cast<PlaneInfo*>(emptyV + NSV);
 
   const WorkItem it = a.items[blockIdx.x];
   const int4 nb = a.nbrs[blockIdx.x];
@@ -152,7 +151,9 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
   const int Nz = V.Nz;
   const int tid = threadIdx.x;
 
-  for (int j = tid; j < Nz; j += blockDim.x) {
+  // Per-plane data (sponge factor, receiver-entry range) straight from
+  // global memory: shared memory is taken up by the rings.
+  auto plane_info = [&](int j) {
     PlaneInfo pi;
     pi.gz = a.gz[j];
     pi.rb = pi.re = 0;
@@ -161,8 +162,8 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
       pi.re = a.rec_ptr[it.rec_tab + j + 1];
     }
     pi.pad = 0;
-    pinfo[j] = pi;
-  }
+    return pi;
+  };
   if (tid == 0) {
     for (int s = 0; s < NSU; ++s) {
       mbar_init(&fullU[s], 1);
@@ -312,7 +313,7 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
         }
       }
     }
-    const PlaneInfo pi = pinfo[z];
+    const PlaneInfo pi = plane_info(z);
     if (pi.rb < pi.re) {
 #pragma unroll
       for (int r = 0; r < 2; ++r)
@@ -368,7 +369,7 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
       float la[4], lb[4];
       lap8<TX>(ringU + su * HS, lx, ly0, qa, qb, la, lb);
       const float* cs = ringC + c * NCA * CS + ly0 * TX + lx;
-      const float gz = pinfo[j].gz;
+      const float gz = a.gz[j];
       F4 out[2];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -419,7 +420,7 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
       float la[4], lb[4];
       lap8<TX>(ringV + s * VS, lx, ly0, va, vb, la, lb);
       const float* cs = ringV + s * VS + HS + ly0 * TX + lx;
-      const float gz = pinfo[z].gz;
+      const float gz = a.gz[z];
       F4 out[2];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -447,8 +448,8 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
 }
 
 template <int TX, int TY, bool DENS>
-static size_t pair_smem(int nz) {
-  return PairLayout<TX, TY, DENS>::base_bytes + sizeof(PlaneInfo) * (size_t)nz;
+static size_t pair_smem(int) {
+  return PairLayout<TX, TY, DENS>::base_bytes;
 }
 
 template <int TX, int TY, bool DENS>
