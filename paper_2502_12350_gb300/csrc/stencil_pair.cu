@@ -48,6 +48,102 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Tensor memory (TMEM) holds step B's z column of u^{n+1}: 9 planes x 8
+// points per thread, in the 32 lanes of the warp's subpartition.
+__device__ __forceinline__ void tm_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tm_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tm_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// 8 consecutive columns of this thread's lane: the 8 points of one plane.
+__device__ __forceinline__ void tm_st8(uint32_t taddr, const F4& r0, const F4& r1) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "f"(r0.v[0]), "f"(r0.v[1]), "f"(r0.v[2]), "f"(r0.v[3]), "f"(r1.v[0]), "f"(r1.v[1]),
+      "f"(r1.v[2]), "f"(r1.v[3])
+      : "memory");
+}
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, F4& r0, F4& r1) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(r0.v[0]), "=f"(r0.v[1]), "=f"(r0.v[2]), "=f"(r0.v[3]), "=f"(r1.v[0]), "=f"(r1.v[1]),
+        "=f"(r1.v[2]), "=f"(r1.v[3])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Step B's lap for the 8 points of a thread, with the z column streamed from
+// TMEM one pair of planes (z - 1 - m, z + 1 + m) at a time; the operations
+// and their order are lap25's, so the values are bitwise the one-step
+// kernel's.  slot(p) is the TMEM column address of plane p; c0, c1 are the
+// centre rows (plane z).
+template <int TX, typename Slot>
+__device__ __forceinline__ void lap8_tm(const float* st, int lx, int ly0, const F4& c0,
+                                        const F4& c1, Slot slot, int z, float (&oa)[4],
+                                        float (&ob)[4]) {
+  constexpr int RP = TX + 2 * kHalo;
+  const float cw[4] = {MAMUTE_C1, MAMUTE_C2, MAMUTE_C3, MAMUTE_C4};
+  const float* r0 = st + (ly0 + kHalo) * RP + lx;
+  const float* r1 = r0 + RP;
+  const F4 L0 = ld4s(r0), R0 = ld4s(r0 + 8), L1 = ld4s(r1), R1 = ld4s(r1 + 8);
+  float xa[12], xb[12];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    xa[k] = L0.v[k];
+    xa[4 + k] = c0.v[k];
+    xa[8 + k] = R0.v[k];
+    xb[k] = L1.v[k];
+    xb[4 + k] = c1.v[k];
+    xb[8 + k] = R1.v[k];
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    oa[e] = __fmul_rn(3.0f * MAMUTE_C0, c0.v[e]);
+    ob[e] = __fmul_rn(3.0f * MAMUTE_C0, c1.v[e]);
+  }
+  F4 upp = c0, dnp = c1;  // rows at distance m from the pair (m = 0: the pair itself)
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const F4 up = ld4s(r0 + kHalo - (m + 1) * RP);  // row ly0 - 1 - m
+    const F4 dn = ld4s(r1 + kHalo + (m + 1) * RP);  // row ly0 + 2 + m
+    F4 zm0, zm1, zp0, zp1;
+    tm_ld8(slot(z - 1 - m), zm0, zm1);
+    tm_ld8(slot(z + 1 + m), zp0, zp1);
+    tm_wait_ld();
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      // row ly0: y- = row ly0 - 1 - m, y+ = row ly0 + 1 + m
+      float sa = __fadd_rn(__fadd_rn(__fadd_rn(xa[4 + e - (m + 1)], xa[4 + e + (m + 1)]),
+                                     __fadd_rn(up.v[e], m == 0 ? c1.v[e] : dnp.v[e])),
+                           __fadd_rn(zm0.v[e], zp0.v[e]));
+      oa[e] = __fmaf_rn(cw[m], sa, oa[e]);
+      // row ly0 + 1: y- = row ly0 - m, y+ = row ly0 + 2 + m
+      float sb = __fadd_rn(__fadd_rn(__fadd_rn(xb[4 + e - (m + 1)], xb[4 + e + (m + 1)]),
+                                     __fadd_rn(m == 0 ? c0.v[e] : upp.v[e], dn.v[e])),
+                           __fadd_rn(zm1.v[e], zp1.v[e]));
+      ob[e] = __fmaf_rn(cw[m], sb, ob[e]);
+    }
+    upp = up;
+    dnp = dn;
+  }
+}
+
 // lap for the 8 points of a thread (rows ly0 and ly0 + 1, columns lx..lx+3):
 // halo stage `st` with row pitch TX + 8; z columns from q0 / q1 (one queue
 // per row).  Operands reach lap25 in the same order as in lap4, so each
@@ -113,7 +209,7 @@ struct PairLayout {
   static constexpr int NSC = 2;  // u^{n-1}, A, A m2 of step A
   static constexpr int NSV = 2;  // u^{n+1} halo + A, A m2 of step B
   static constexpr int NCA = DENS ? 3 : 2;  // centre arrays of step A
-  static constexpr int NCB = DENS ? 2 : 1;  // centre arrays of step B
+  static constexpr int NCB = DENS ? 2 : 1;  // centre arrays of step B (A, A m2)
   static constexpr int VS = HS + NCB * CS;  // floats per step-B stage
   static constexpr size_t base_bytes =
       sizeof(float) * ((size_t)NSU * HS + (size_t)NSC * NCA * CS + (size_t)NSV * VS + CS) +
@@ -123,10 +219,10 @@ struct PairLayout {
 }  // namespace
 
 template <int TX, int TY, bool DENS>
-__global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
+__global__ void __launch_bounds__((TX / 4) * (TY / 2) + 32, 1) pair_kernel(const PairArgs a) {
   using LY = PairLayout<TX, TY, DENS>;
   constexpr int NCT = LY::NCT, NW = LY::NW, HS = LY::HS, CS = LY::CS;
-  constexpr int NSU = LY::NSU, NSC = LY::NSC, NSV = LY::NSV, NCA = LY::NCA, NCB = LY::NCB;
+  constexpr int NSU = LY::NSU, NSC = LY::NSC, NSV = LY::NSV, NCA = LY::NCA;
   constexpr int VS = LY::VS;
   static_assert(NCT % 32 == 0, "whole compute warps");
 
@@ -179,7 +275,16 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
     }
     fence_barrier_init();
   }
+  __shared__ uint32_t tmem_base;
+  constexpr uint32_t kTmCols = 256;  // 9 planes x 8 points per warp, 3 warps per lane group
+  static_assert(((NW + 3) / 4) * 72 <= (int)kTmCols, "TMEM columns");
+  if (tid < 32) {
+    tm_alloc(&tmem_base, kTmCols);
+    tm_relinquish();
+  }
+  tm_fence_before();
   __syncthreads();
+  tm_fence_after();
 
   const int cx = V.cx0 + x0, cy = V.cy0 + y0;
   if (tid >= NCT) {
@@ -338,12 +443,15 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
     }
   };
 
-  F4 qa[9], qb[9], va[9], vb[9];  // u^n and u^{n+1} z columns of rows ly0, ly0 + 1
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    va[k] = F4{{0.f, 0.f, 0.f, 0.f}};
-    vb[k] = va[k];
-  }
+  F4 qa[9], qb[9];  // u^n z columns of rows ly0, ly0 + 1 (registers)
+  // u^{n+1} z columns in TMEM: plane p at columns wcol + 8 (p mod 9)
+  const int warp = tid >> 5;
+  const uint32_t tm_lane = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t wcol = tmem_base + (uint32_t)((warp >> 2) * 72);
+  auto slot = [&](int p) { return tm_lane | (wcol + (uint32_t)(8 * ((p + 18) % 9))); };
+  const F4 zero4 = {{0.f, 0.f, 0.f, 0.f}};
+  for (int k = 0; k < 9; ++k) tm_st8(tm_lane | (wcol + 8 * k), zero4, zero4);  // planes < 0
+  tm_wait_st();
   // Priming: u^n planes -4 .. 3.
   for (int i = 0; i < 2 * kHalo; ++i) {
     const int s = i % NSU;
@@ -388,37 +496,32 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
       release(&emptyU[su]);
       release(&emptyC[c]);
       finish(out, j, a.wn0, a.dout0, a.fout1);
+      __syncwarp();  // tcgen05.st is a warp-wide (.sync.aligned) instruction
+      tm_st8(slot(j), out[0], out[1]);
       // Publish plane j of u^{n+1}: every compute warp has stored it.
       compute_sync(NCT);
       if (tid == 0) {
         __threadfence();
         st_release(a.flags + blockIdx.x, a.epoch + j + 1);
       }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        va[k] = va[k + 1];
-        vb[k] = vb[k + 1];
-      }
-      va[8] = out[0];
-      vb[8] = out[1];
     } else {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        va[k] = va[k + 1];
-        vb[k] = vb[k + 1];
-      }
-      va[8] = F4{{0.f, 0.f, 0.f, 0.f}};
-      vb[8] = va[8];
-      qa[8] = va[8];
-      qb[8] = va[8];
+      __syncwarp();
+      tm_st8(slot(j), zero4, zero4);  // u^{n+1} is zero past the last plane
+      qa[8] = zero4;
+      qb[8] = zero4;
     }
+    tm_wait_st();
     if (j >= kHalo) {
       // ---------------------------------------------- step B, plane j - 4
       const int z = j - kHalo;
       const int s = z % NSV;
       wait(&fullV[s], (z / NSV) & 1);
+      F4 c0, c1;  // u^{n+1} on plane z
+      __syncwarp();
+      tm_ld8(slot(z), c0, c1);
+      tm_wait_ld();
       float la[4], lb[4];
-      lap8<TX>(ringV + s * VS, lx, ly0, va, vb, la, lb);
+      lap8_tm<TX>(ringV + s * VS, lx, ly0, c0, c1, slot, z, la, lb);
       const float* cs = ringV + s * VS + HS + ly0 * TX + lx;
       const float gz = a.gz[z];
       F4 out[2];
@@ -428,7 +531,7 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
         F4 Mv = {{0.f, 0.f, 0.f, 0.f}};
         if (DENS) Mv = ld4s(cs + CS + r * TX);
         const float gyz = __fmul_rn(gyv[r], gz);
-        const F4& u = r ? vb[4] : va[4];
+        const F4& u = r ? c1 : c0;
         const F4& prev = r ? qb[0] : qa[0];  // u^n on plane j - 4
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -444,6 +547,13 @@ __global__ void __maxnreg__(200) pair_kernel(const PairArgs a) {
       qa[k] = qa[k + 1];
       qb[k] = qb[k + 1];
     }
+  }
+  // Every compute warp is done with TMEM: warp 0 returns the columns.
+  tm_fence_before();
+  compute_sync(NCT);
+  if (warp == 0) {
+    tm_fence_after();
+    tm_dealloc(tmem_base, kTmCols);
   }
 }
 
