@@ -40,6 +40,16 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -211,9 +221,10 @@ struct PairLayout {
   static constexpr int NCA = DENS ? 3 : 2;  // centre arrays of step A
   static constexpr int NCB = DENS ? 2 : 1;  // centre arrays of step B (A, A m2)
   static constexpr int VS = HS + NCB * CS;  // floats per step-B stage
+  static constexpr int NST = 8;  // "plane stored" barriers between the warps and the publisher
   static constexpr size_t base_bytes =
       sizeof(float) * ((size_t)NSU * HS + (size_t)NSC * NCA * CS + (size_t)NSV * VS + CS) +
-      sizeof(uint64_t) * (2 * NSU + 2 * NSC + 2 * NSV);
+      sizeof(uint64_t) * (2 * NSU + 2 * NSC + 2 * NSV + NST);
 };
 
 }  // namespace
@@ -238,6 +249,8 @@ __global__ void __launch_bounds__((TX / 4) * (TY / 2) + 32, 1) pair_kernel(const
   uint64_t* emptyC = fullC + NSC;
   uint64_t* fullV = emptyC + NSC;
   uint64_t* emptyV = fullV + NSV;
+  uint64_t* stored = emptyV + NSV;  // plane j of u^{n+1} stored by every compute warp
+  constexpr int NST = LY::NST;
 
   const WorkItem it = a.items[blockIdx.x];
   const int4 nb = a.nbrs[blockIdx.x];
@@ -273,6 +286,7 @@ __global__ void __launch_bounds__((TX / 4) * (TY / 2) + 32, 1) pair_kernel(const
       mbar_init(&fullV[s], 1);
       mbar_init(&emptyV[s], NW);
     }
+    for (int s = 0; s < NST; ++s) mbar_init(&stored[s], NW);
     fence_barrier_init();
   }
   __shared__ uint32_t tmem_base;
@@ -338,11 +352,20 @@ __global__ void __launch_bounds__((TX / 4) * (TY / 2) + 32, 1) pair_kernel(const
         for (int s = 0; s < NSV && s < nV; ++s)
           mbar_wait(&fullV[s], (uint32_t)(((nV - 1 - s) / NSV) & 1), a.status);
       };
-      // Waits (bounded) until tile t has published plane z; false on timeout.
-      auto published = [&](int t, int target) {
-        if (t < 0) return true;
-        for (long long spin = 0; spin < kSpinLimit; ++spin)
-          if (ld_acquire(a.flags + t) >= target) return true;
+      // Waits (bounded) until this tile and its neighbours have published
+      // plane z: the five flags are polled together, then one acquire fence.
+      auto published = [&](int target) {
+        const int t[5] = {(int)blockIdx.x, nb.x, nb.y, nb.z, nb.w};
+        for (long long spin = 0; spin < kSpinLimit; ++spin) {
+          bool ok = true;
+#pragma unroll
+          for (int k = 0; k < 5; ++k)
+            if (t[k] >= 0 && ld_relaxed(a.flags + t[k]) < target) ok = false;
+          if (ok) {
+            fence_acq_rel_gpu();
+            return true;
+          }
+        }
         atomicOr(a.status, kErrTimeout);
         return false;
       };
@@ -352,9 +375,7 @@ __global__ void __launch_bounds__((TX / 4) * (TY / 2) + 32, 1) pair_kernel(const
           drain();
           return;
         }
-        const int target = a.epoch + z + 1;
-        if (!published((int)blockIdx.x, target) || !published(nb.x, target) ||
-            !published(nb.y, target) || !published(nb.z, target) || !published(nb.w, target)) {
+        if (!published(a.epoch + z + 1)) {
           drain();
           return;
         }
@@ -365,6 +386,15 @@ __global__ void __launch_bounds__((TX / 4) * (TY / 2) + 32, 1) pair_kernel(const
         tma_load_3d(vd + HS, &pm->m[4], cx, cy, z, &fullV[s]);
         if (DENS) tma_load_3d(vd + HS + CS, &pm->m[5], cx, cy, z, &fullV[s]);
         ++nV;
+      }
+    } else if (lane == 2) {
+      // Publisher: once every compute warp has stored plane j of u^{n+1},
+      // make the stores visible at GPU scope and advance this tile's flag
+      // (off the compute warps' path).
+      for (int j = 0; j < Nz; ++j) {
+        if (!mbar_wait(&stored[j % NST], (uint32_t)((j / NST) & 1), a.status)) return;
+        __threadfence();
+        st_release(a.flags + blockIdx.x, a.epoch + j + 1);
       }
     }
     return;
@@ -496,14 +526,10 @@ __global__ void __launch_bounds__((TX / 4) * (TY / 2) + 32, 1) pair_kernel(const
       release(&emptyU[su]);
       release(&emptyC[c]);
       finish(out, j, a.wn0, a.dout0, a.fout1);
-      __syncwarp();  // tcgen05.st is a warp-wide (.sync.aligned) instruction
-      tm_st8(slot(j), out[0], out[1]);
-      // Publish plane j of u^{n+1}: every compute warp has stored it.
-      compute_sync(NCT);
-      if (tid == 0) {
-        __threadfence();
-        st_release(a.flags + blockIdx.x, a.epoch + j + 1);
-      }
+      // Plane j of u^{n+1} is stored by this warp; the publisher lane waits
+      // for all of them.
+      release(&stored[j % NST]);
+      tm_st8(slot(j), out[0], out[1]);  // after release()'s __syncwarp: warp-wide
     } else {
       __syncwarp();
       tm_st8(slot(j), zero4, zero4);  // u^{n+1} is zero past the last plane
