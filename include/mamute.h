@@ -121,6 +121,11 @@ typedef struct {
  *                   interpolation; see mamute_resample); the residual is
  *                   brought back by the transposed resampling.
  *   nt_data, dt_data  the data time axis when time_interp != 0.
+ *   time_blocking   mamute_model only: 2 advances two time steps per launch
+ *                   with the two-level kernel (one shot, no free surface, no
+ *                   pseudo-Hessian, every tile resident on its own SM; the
+ *                   seismograms are bitwise those of one step per launch);
+ *                   0 or 1: one step per launch.
  * A NULL options pointer means all defaults. */
 typedef struct {
   float check_mem;
@@ -134,6 +139,7 @@ typedef struct {
   int time_interp;
   int nt_data;
   float dt_data;
+  int time_blocking;
 } mamute_opts;
 
 #define MAMUTE_SMOOTH_NONE 0

@@ -799,12 +799,14 @@ int check_common(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     if (rc_ != MAMUTE_OK) return rc_; \
   } while (0)
 
-// Two-level forward launches (stencil_pair.cu): one shot, no free surface,
-// every tile resident at once (one CTA per SM).  Columns of the x split are
+// Two-level forward launches (stencil_pair.cu), on request (time_blocking =
+// 2, or MAMUTE_PAIRS=1): one shot, no free surface, every tile resident at
+// once (one CTA per SM).  Columns of the x split are
 // multiples of 4 and at most TX wide; the rows are split as finely as the
 // SMs allow (at least 8 rows per tile), so that all SMs get a tile.
-bool plan_pairs(mamute_ctx* ctx, Plan& P) {
-  if (env_int("MAMUTE_PAIRS", 1) == 0 || P.vols.size() != 1 || P.zs >= 0 || P.nt < 2) return false;
+bool plan_pairs(mamute_ctx* ctx, Plan& P, const mamute_opts* opts) {
+  const int want = env_int("MAMUTE_PAIRS", opts && opts->time_blocking == 2 ? 1 : 0);
+  if (want == 0 || P.vols.size() != 1 || P.zs >= 0 || P.nt < 2) return false;
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   const VolDesc& V = P.vols[0];
@@ -1094,7 +1096,7 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   CK(ensure(ctx->dint, (size_t)P.nt * std::max(P.ncol, 1) * 4));
   const int mode = ph ? MODE_FWD_PH : MODE_FWD;
   // Two time levels per launch where the problem allows it.
-  const bool pairs = !ph && plan_pairs(ctx, P);
+  const bool pairs = !ph && plan_pairs(ctx, P, opts);
   if (pairs) {
     TRY(setup_pairs(ctx, P, vel, rho));
     CK(cudaMemsetAsync(ctx->pflags.p, 0, P.pitems.size() * 4, ctx->stream));

@@ -43,7 +43,7 @@ class Opts(ctypes.Structure):
                 ("phess", ctypes.c_void_p), ("tiles", ctypes.c_int * 6),
                 ("smooth_mode", ctypes.c_int), ("smooth_len", ctypes.c_float * 3),
                 ("time_interp", ctypes.c_int), ("nt_data", ctypes.c_int),
-                ("dt_data", ctypes.c_float)]
+                ("dt_data", ctypes.c_float), ("time_blocking", ctypes.c_int)]
 
 SMOOTH_NONE, SMOOTH_BESSEL, SMOOTH_LAPLACE = 0, 1, 2
 INTERP_NEAREST, INTERP_SINC = 1, 2
@@ -160,14 +160,14 @@ class Context:
     @staticmethod
     def _opts(check_mem=0.8, n_snapshots=0, zero_top_planes=0, aperture=None, phess=None,
               tiles=None, smooth_mode=0, smooth_len=(0.0, 0.0, 0.0), time_interp=0, nt_data=0,
-              dt_data=0.0):
+              dt_data=0.0, time_blocking=0):
         ap = None if aperture is None else np.ascontiguousarray(aperture, np.int32)
         o = Opts(check_mem, n_snapshots, zero_top_planes,
                  None if ap is None else ap.ctypes.data, None if phess is None else phess.data_ptr()
                  if not isinstance(phess, np.ndarray) else phess.ctypes.data,
                  (ctypes.c_int * 6)(*(list(tiles) if tiles is not None else [0] * 6)),
                  int(smooth_mode), (ctypes.c_float * 3)(*[float(v) for v in smooth_len]),
-                 int(time_interp), int(nt_data), float(dt_data))
+                 int(time_interp), int(nt_data), float(dt_data), int(time_blocking))
         return o, ap
 
     def model(self, grid: Grid, vel, rho, src_xyz, wavelet, rec_offset, rec_xyz, seis, **opts):

@@ -40,7 +40,7 @@ def _model(ctx, w, xi=0):
     rho = None if w.rho is None else torch.from_numpy(np.ascontiguousarray(w.rho)).to(dev)
     seis = torch.full((int(w.rec_offset[-1]), w.nt), float("nan"), device=dev)
     ctx.model(mamute.grid_of(w, xyz_interp=xi), vel, rho, w.src_xyz, w.wavelet, w.rec_offset,
-              w.rec_xyz, seis)
+              w.rec_xyz, seis, time_blocking=2)
     sl = ctypes.c_longlong()
     ctx.lib.mamute_ctx_last_timing(ctx._h, None, ctypes.byref(sl), None)
     return seis.cpu().numpy(), sl.value
@@ -78,7 +78,7 @@ def test_pairs_with_offgrid_points_and_host_copies(ctx, monkeypatch):
     host = np.zeros_like(two)
     ctx.model_host(mamute.grid_of(w, xyz_interp=1), np.ascontiguousarray(w.vel),
                    np.ascontiguousarray(w.rho), w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
-                   host)
+                   host, time_blocking=2)
     np.testing.assert_array_equal(host, two)
     monkeypatch.setenv("MAMUTE_PAIRS", "0")
     one, _ = _model(ctx, w, xi=1)
