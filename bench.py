@@ -136,6 +136,8 @@ def workload(nt=None, kind="model"):
     from paper_2502_12350_gb300 import synth
     if kind == "model_small":
         return synth.forward_small() if nt is None else synth.forward_small(nt=nt)
+    if kind == "model_mid":  # 256x256x128 with density: arrays still larger than L2
+        return synth.forward_density(nt=nt or 4000, nx=256, ny=256, nz=128)
     return synth.forward_density() if nt is None else synth.forward_density(nt=nt)
 
 
@@ -477,8 +479,8 @@ def main():
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the 256^3 FWI gradient object of the headline line")
     ap.add_argument("--workload", default="model",
-                    choices=["model", "model_small", "gradient_single", "gradient_batched", "cnn",
-                             "gn_labels"],
+                    choices=["model", "model_small", "model_mid", "gradient_single",
+                             "gradient_batched", "cnn", "gn_labels"],
                     help="model: the headline modelling benchmark; gradient_*: FWI gradient "
                          "shots/s on the 256^3 single-shot or the 64-shot aperture workload")
     ap.add_argument("--autotune", action="store_true",
