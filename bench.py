@@ -476,6 +476,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--nt", type=int, default=None, help="time steps (default: the workload's 4000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-blocking", type=int, default=0, choices=[0, 2],
+                    help="model workloads: 2 = two time steps per launch (two-level kernel)")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the 256^3 FWI gradient object of the headline line")
     ap.add_argument("--workload", default="model",
@@ -532,7 +534,8 @@ def main():
     seis = torch.empty((n_rec, nt), device=dev)
 
     def step():
-        ctx.model(g, vel, rho, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, seis)
+        ctx.model(g, vel, rho, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, seis,
+                  time_blocking=args.time_blocking)
 
     for _ in range(args.warmup):
         step()
@@ -572,7 +575,8 @@ def main():
 
     def host_step():
         ctx.model_host(g, vel_h.numpy(), None if rho_h is None else rho_h.numpy(), w.src_xyz,
-                       w.wavelet, w.rec_offset, w.rec_xyz, seis_h.numpy())
+                       w.wavelet, w.rec_offset, w.rec_xyz, seis_h.numpy(),
+                       time_blocking=args.time_blocking)
 
     host_step()
     torch.cuda.synchronize()
