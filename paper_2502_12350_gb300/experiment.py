@@ -10,7 +10,18 @@ back to the pseudo-Hessian step when the learned step fails Armijo) and the
 exact GN diagonal recomputed at every iterate.  Writes a JSON report with
 misfit against wall time for every arm.
 
+With --test-models and --waters the comparison is made on several inverted
+models: each arm's water level (the floor of its preconditioning diagonal,
+as a fraction of its maximum) is first chosen on a validation model by the
+lowest final misfit, then every test model is inverted by every arm at its
+chosen level, and the report gives, per model, each arm's final misfit, wall
+time and the wall time at which it reached the plain (pseudo-Hessian) run's
+final misfit.
+
     python -m paper_2502_12350_gb300.experiment --out report.json
+    python -m paper_2502_12350_gb300.experiment --out report.json --train-models 80 \
+        --heldout-models 20 --arms pseudo,learned --waters 0.002,0.01,0.05 \
+        --val-model 5100 --test-models 5420,5421,5422
 """
 from __future__ import annotations
 
@@ -41,6 +52,10 @@ def main(argv=None):
     ap.add_argument("--load-net", default=None,
                     help="use a trained network (.npz) instead of labelling and training")
     ap.add_argument("--arms", default="none,pseudo,learned,exact")
+    ap.add_argument("--waters", default=None,
+                    help="comma list: choose each arm's water level on --val-model")
+    ap.add_argument("--val-model", type=int, default=5100)
+    ap.add_argument("--test-models", default=None, help="comma list of inverted models")
     args = ap.parse_args(argv)
 
     from . import build, cnn, fwi, learned, mamute, synth
@@ -90,30 +105,63 @@ def main(argv=None):
             np.savez(args.save_net, offset=net.offset, **{f"w{l}": ws[l] for l in range(cnn.LAYERS)},
                      **{f"b{l}": bs[l] for l in range(cnn.LAYERS)})
 
-    w = wl(args.test_model)
-    g = mamute.grid_of(w)
-    vt = torch.from_numpy(w.vel).to(dev)
-    dobs = torch.empty((int(w.rec_offset[-1]), w.nt), device=dev)
-    ctx.model(g, vt, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs)
-    vmin, vmax = float(w.vel.min()) * 0.9, float(w.vel.max()) * 1.1
-    report["initial_model_rms_error"] = float(np.sqrt(np.mean((w.vel_init - w.vel) ** 2)))
-    runs = {}
-    for kind in args.arms.split(","):
+    def invert(mid, kind, water):
+        w = wl(mid)
+        g = mamute.grid_of(w)
+        vt = torch.from_numpy(w.vel).to(dev)
+        dobs = torch.empty((int(w.rec_offset[-1]), w.nt), device=dev)
+        ctx.model(g, vt, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs)
+        vmin, vmax = float(w.vel.min()) * 0.9, float(w.vel.max()) * 1.1
         prob = fwi.Problem(ctx, w, dobs, vmin, vmax)
         res = fwi.run(prob, w.vel_init.astype(np.float64), args.iters, precond=kind, net=net,
-                      water=args.water)
+                      water=water)
         err = float(np.sqrt(np.mean((res.vel - w.vel) ** 2)))
-        runs[kind] = {"history": [(t, J, k) for t, J, k in res.history],
-                      "model_rms_error": err, "gradients": res.n_gradients,
-                      "forward_models": res.n_forward}
-        print(kind, "final misfit", res.history[-1][1], "model error", err,
-              "time", res.history[-1][0])
+        print(mid, kind, water, "final misfit", res.history[-1][1], "model error", err,
+              "time", res.history[-1][0], flush=True)
+        return {"history": [(t, J, k) for t, J, k in res.history], "model_rms_error": err,
+                "gradients": res.n_gradients, "forward_models": res.n_forward, "water": water,
+                "initial_model_rms_error": float(np.sqrt(np.mean((w.vel_init - w.vel) ** 2)))}
+
+    def time_to(runs, target):
+        for kind in runs:
+            runs[kind]["seconds_to_plain_final_misfit"] = None if target is None else next(
+                (t for t, J, _ in runs[kind]["history"] if J <= target), None)
+
+    arms = args.arms.split(",")
+    if args.test_models:
+        assert args.val_model not in train_ids + test_ids
+        water = {k: args.water for k in arms}
+        if args.waters:
+            levels = [float(v) for v in args.waters.split(",")]
+            val = {k: {str(lv): invert(args.val_model, k, lv) for lv in levels} for k in arms}
+            report["validation"] = {k: {lv: r["history"][-1][1] for lv, r in v.items()}
+                                    for k, v in val.items()}
+            water = {k: float(min(v, key=lambda lv: v[lv]["history"][-1][1]))
+                     for k, v in val.items()}
+        report["chosen_water"] = water
+        models = {}
+        for mid in [int(v) for v in args.test_models.split(",")]:
+            assert mid not in train_ids + test_ids + [args.val_model]
+            runs = {k: invert(mid, k, water[k]) for k in arms}
+            time_to(runs, runs["pseudo"]["history"][-1][1] if "pseudo" in runs else None)
+            models[str(mid)] = runs
+        report["fwi_models"] = models
+        summary = {}
+        for mid, runs in models.items():
+            summary[mid] = {k: {"final_misfit": r["history"][-1][1], "seconds": r["history"][-1][0],
+                                "seconds_to_plain_final_misfit": r["seconds_to_plain_final_misfit"],
+                                "model_rms_error": r["model_rms_error"]} for k, r in runs.items()}
+        report["summary"] = summary
+        with open(args.out, "w") as f:
+            json.dump(report, f, indent=1)
+        ctx.close()
+        return
+
+    w = wl(args.test_model)
+    report["initial_model_rms_error"] = float(np.sqrt(np.mean((w.vel_init - w.vel) ** 2)))
+    runs = {kind: invert(args.test_model, kind, args.water) for kind in arms}
     # wall time for each run to reach the plain run's final misfit
-    target = runs["pseudo"]["history"][-1][1] if "pseudo" in runs else None
-    for kind in runs:
-        t_hit = None if target is None else next(
-            (t for t, J, _ in runs[kind]["history"] if J <= target), None)
-        runs[kind]["seconds_to_plain_final_misfit"] = t_hit
+    time_to(runs, runs["pseudo"]["history"][-1][1] if "pseudo" in runs else None)
     report["fwi"] = runs
     with open(args.out, "w") as f:
         json.dump(report, f, indent=1)
