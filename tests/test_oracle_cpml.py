@@ -1,0 +1,95 @@
+"""Pins of the CPML oracle (the paper's convolutional PML boundary).
+
+* With no damping and no frequency shift the memory variables stay zero and
+  the scheme is the main one without sponge: the main oracle's traces, to
+  rounding.
+* The gradient is the transpose of the modelling map: dot-product identity
+  for wavelet -> traces, and central finite differences of the misfit.
+* It absorbs: on a small grid, the error against a grid so large that no
+  reflection reaches the receivers in the window is far below that of the
+  Cerjan sponge of the same thickness.
+"""
+import numpy as np
+import pytest
+
+from oracle import cpml
+from paper_2502_12350_gb300 import synth
+
+
+def _tiny(density, nt=40, seed=3):
+    return synth.small_case(seed=seed, nx=10, ny=9, nz=8, border=5, nt=nt, density=density,
+                            n_src=2, n_rec=4, fpeak=30.0)
+
+
+@pytest.mark.parametrize("density", [False, True])
+def test_no_damping_is_the_main_scheme(oracle, density):
+    w = _tiny(density)
+    g = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, cerjan=0.0)
+    ref = oracle.model(g, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho)
+    got = cpml.model(oracle, g, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, f0=0.0,
+                     rho=w.rho, R=1.0)
+    assert np.abs(ref).max() > 0
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("density", [False, True])
+def test_dot_product(oracle, density):
+    w = _tiny(density, seed=4)
+    g = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
+    rng = np.random.default_rng(5)
+    wav = rng.standard_normal(w.nt)
+    r = rng.standard_normal((int(w.rec_offset[-1]), w.nt))
+    Fw = cpml.model(oracle, g, w.vel, w.src_xyz, wav, w.rec_offset, w.rec_xyz, f0=30.0, rho=w.rho)
+    _, _, FTr = cpml.gradient(oracle, g, w.vel, w.src_xyz, wav, w.rec_offset, w.rec_xyz, Fw - r,
+                              f0=30.0, rho=w.rho, return_dwav=True)
+    w2 = rng.standard_normal(w.nt)
+    Fw2 = cpml.model(oracle, g, w.vel, w.src_xyz, w2, w.rec_offset, w.rec_xyz, f0=30.0, rho=w.rho)
+    lhs, rhs = np.sum(Fw2 * r), np.sum(w2 * FTr)
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs))
+
+
+def test_gradient_matches_finite_differences(oracle):
+    w = _tiny(True, seed=6)
+    g = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
+    rng = np.random.default_rng(7)
+    vel = w.vel.astype(np.float64)
+    dobs = cpml.model(oracle, g, vel * (1 + 0.03 * rng.standard_normal(vel.shape)), w.src_xyz,
+                      w.wavelet, w.rec_offset, w.rec_xyz, f0=30.0, rho=w.rho)
+    _, grad = cpml.gradient(oracle, g, vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs,
+                            f0=30.0, rho=w.rho)
+    dc = np.zeros_like(vel)
+    dc[1:-1, 1:-1, 1:-1] = rng.standard_normal(tuple(s - 2 for s in vel.shape)) * 50.0
+
+    def J(v):
+        d = cpml.model(oracle, g, v, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, f0=30.0,
+                       rho=w.rho)
+        return 0.5 * np.sum((d - dobs) ** 2)
+
+    pred = np.sum(grad * dc)
+    eps = 1e-3
+    fd = (J(vel + eps * dc) - J(vel - eps * dc)) / (2 * eps)
+    assert abs(fd - pred) <= 1e-6 * abs(pred)
+
+
+def test_absorbs_better_than_the_sponge(oracle):
+    """Receivers 4 cells from the model edge, 10-cell boundaries; the
+    reference grid is 40 cells wider on every side (no reflection from it
+    reaches the receivers in the window)."""
+    n, b, h, dt, nt, cv, f = 24, 10, 10.0, 1e-3, 150, 2000.0, 25.0
+    wav = synth.ricker(nt, dt, f).astype(np.float64)
+    c = n // 2
+    src = np.array([[c * h, c * h, c * h]])
+    rec = np.array([[(n - 5) * h, c * h, c * h], [c * h, c * h, 4 * h], [3 * h, 3 * h, c * h]])
+    vel = np.full((n, n, n), cv)
+    g = oracle.make_grid(n, n, n, b, h, dt, nt)
+    sponge = oracle.model(g, vel, src, wav, [0, 3], rec)
+    pml = cpml.model(oracle, g, vel, src, wav, [0, 3], rec, f0=f)
+    big, pad = n + 80, 40
+    gb = oracle.make_grid(big, big, big, b, h, dt, nt, cerjan=0.0)
+    ref = oracle.model(gb, np.full((big, big, big), cv), src + pad * h, wav, [0, 3],
+                       rec + pad * h)
+    e_sponge = np.linalg.norm(sponge - ref) / np.linalg.norm(ref)
+    e_pml = np.linalg.norm(pml - ref) / np.linalg.norm(ref)
+    # measured: sponge 2.5e-3, CPML 2.8e-6 relative error
+    assert e_pml < 0.01 * e_sponge, (e_pml, e_sponge)
+    assert e_pml < 1e-4, e_pml
