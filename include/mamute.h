@@ -72,7 +72,19 @@ typedef struct mamute_ctx mamute_ctx;
  * the source adds w_e dt^2 w[n] / (h^3 sqrt(rho_e)) at each node and a
  * receiver records sum_e w_e sqrt(rho_e) u_e (nodes with zero weight or on a
  * free surface are skipped; every node with non-zero weight must lie in the
- * model, or the shot's aperture). */
+ * model, or the shot's aperture).
+ * pml (Sec. 2, the convolutional PML absorbing boundary): 1 replaces the
+ * sponge by a convolutional perfectly matched layer on the `border` cells of
+ * every face of each shot's window (cerjan is then ignored).  Each
+ * derivative d/dx_a is divided by s_a = 1 + d_a / (alpha_a + i w) in the
+ * layer, carried by two memory variables per axis updated by recursive
+ * convolution; at depth r = (cells into the layer) / border,
+ * d_a = -3 vmax ln(pml_r) r^2 / (2 border h) and alpha_a = pi pml_f0 (1 - r),
+ * vmax = max(vel).  pml_f0 is the source's dominant frequency in Hz (>= 0)
+ * and pml_r the nominal reflection coefficient in (0, 1) (0 selects 1e-3).
+ * A pml gradient keeps the imaging term of every step (n_snapshots 0 or -1;
+ * ENOMEM when that store does not fit) and takes no phess; pml with
+ * free_surface, and mamute_gn_diagonal with pml, are EINVAL.  0: the sponge. */
 typedef struct {
   int nx, ny, nz;
   int border;
@@ -83,6 +95,9 @@ typedef struct {
   float cerjan;
   int free_surface;
   int xyz_interp;
+  int pml;
+  float pml_f0;
+  float pml_r;
 } mamute_grid;
 
 /* Options (Table 4 check_mem; Sec. 3 zeroes_nplanes_gradient).

@@ -23,7 +23,10 @@ at depth r = dist / border (dist = 1 .. border cells):
 R = 1e-3 the nominal reflection coefficient and f0 the source's peak
 frequency.  No sponge factor is applied (g = 1).  Density enters as in the
 main scheme (A = c^2 dt^2, m2 = lap(sqrt rho) / sqrt rho, source / sqrt rho,
-receivers sqrt rho u); sources and receivers are at their nearest nodes.
+receivers sqrt rho u); sources and receivers are at their nearest nodes, or
+(g.xyz_interp = 1) spread over the 8 nodes of their cell with trilinear
+weights w_e, as in the main scheme: the source adds w_e dt^2 w[n] /
+(h^3 sqrt rho_e) at node e and a receiver records sum_e w_e sqrt(rho_e) u_e.
 
 The gradient is the exact transpose of this recursion (reverse mode, written
 out step by step below), with dJ/dA = sum_n lam^{n+1} (x^n - m2 u^n) and
@@ -113,34 +116,57 @@ class Operators:
         self.sr = sr.ravel()
         self.g = g
 
-    def node(self, xyz):
+    def _index(self, i, j, k):
         g = self.g
-        i = int(np.floor((xyz[0] - g.ox) / g.dx + 0.5))
-        j = int(np.floor((xyz[1] - g.oy) / g.dy + 0.5))
-        k = int(np.floor((xyz[2] - g.oz) / g.dz + 0.5))
         if not (0 <= i < g.nx and 0 <= j < g.ny and 0 <= k < g.nz):
             raise ValueError("point outside the model")
         b = g.border
         Nz, Ny, Nx = self.shape
         return ((k + b) * Ny + (j + b)) * Nx + (i + b)
 
+    def points(self, xyz):
+        """[(padded node, weight)]: the nearest node, or the trilinear
+        weights of the cell holding the point (zero weights dropped)."""
+        g = self.g
+        f = [(xyz[0] - g.ox) / g.dx, (xyz[1] - g.oy) / g.dy, (xyz[2] - g.oz) / g.dz]
+        if not getattr(g, "xyz_interp", 0):
+            return [(self._index(*[int(np.floor(v + 0.5)) for v in f]), 1.0)]
+        base = [int(np.floor(v)) for v in f]
+        t = [v - b for v, b in zip(f, base)]
+        out = []
+        for di in (0, 1):
+            for dj in (0, 1):
+                for dk in (0, 1):
+                    w = ((t[0] if di else 1 - t[0]) * (t[1] if dj else 1 - t[1]) *
+                         (t[2] if dk else 1 - t[2]))
+                    if w != 0.0:
+                        out.append((self._index(base[0] + di, base[1] + dj, base[2] + dk), w))
+        return out
+
 
 def _shot(op, src_xyz, s, rec_offset, rec_xyz):
+    """Source nodes and scales; receiver sampling matrix S (d = S u)."""
     g = op.g
-    sn = op.node(src_xyz[s])
-    scale = g.dt * g.dt / (g.dx * g.dy * g.dz * op.sr[sn])
-    recs = [op.node(rec_xyz[r]) for r in range(rec_offset[s], rec_offset[s + 1])]
-    return sn, scale, np.array(recs, dtype=np.int64)
+    src = op.points(src_xyz[s])
+    sn = np.array([n for n, _ in src], dtype=np.int64)
+    scale = np.array([w * g.dt * g.dt / (g.dx * g.dy * g.dz * op.sr[n]) for n, w in src])
+    nr = rec_offset[s + 1] - rec_offset[s]
+    S = sp.lil_matrix((nr, op.A.size))
+    for q, r in enumerate(range(rec_offset[s], rec_offset[s + 1])):
+        for n, w in op.points(rec_xyz[r]):
+            S[q, n] += w * op.sr[n]
+    return sn, scale, S.tocsr()
 
 
 def forward(op, wavelet, sn, scale, recs, keep=False):
-    """Traces [n_rec][nt]; with keep=True also x^n - m2 u^n for every step."""
+    """Traces [n_rec][nt] (recs: the sampling matrix); with keep=True also
+    x^n - m2 u^n for every step."""
     n = op.A.size
     nt = op.g.nt
     u, v = np.zeros(n), np.zeros(n)
     psi = [np.zeros(n) for _ in range(3)]
     zeta = [np.zeros(n) for _ in range(3)]
-    tr = np.zeros((len(recs), nt))
+    tr = np.zeros((recs.shape[0], nt))
     terms = []
     for it in range(nt):
         x = np.zeros(n)
@@ -153,9 +179,9 @@ def forward(op, wavelet, sn, scale, recs, keep=False):
         if keep:
             terms.append(x - op.m2 * u)
         un = op.Bc * u - v + op.A * x
-        un[sn] += scale * wavelet[it]
+        np.add.at(un, sn, scale * wavelet[it])
         v, u = u, un
-        tr[:, it] = op.sr[recs] * u[recs]
+        tr[:, it] = recs @ u
     return (tr, terms) if keep else tr
 
 
@@ -193,8 +219,8 @@ def gradient(oracle, g, vel, src_xyz, wavelet, rec_offset, rec_xyz, dobs, f0, rh
         psib = [np.zeros(n) for _ in range(3)]
         zetab = [np.zeros(n) for _ in range(3)]
         for it in range(nt - 1, -1, -1):
-            np.add.at(lam, recs, op.sr[recs] * res[:, it])  # d[n] = sqrt(rho) u^{n+1}
-            dwav[it] += scale * lam[sn]
+            lam += recs.T @ res[:, it]                       # d[n] = S u^{n+1}
+            dwav[it] += np.sum(scale * lam[sn])
             gA += lam * terms[it]                           # u^{n+1} = ... + A (x - m2 u)
             xb = op.A * lam                                  # adjoint of x^n
             ub = op.Bc * lam + mu                            # adjoint of u^n (so far)

@@ -21,7 +21,7 @@ NVFLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xco
                   "-diag-suppress", "177", "-I", INCLUDE]
 
 SOURCES = ["stencil_fwd.cu", "stencil_adj.cu", "stencil.cu", "aux.cu", "gn.cu", "conv.cu",
-           "api.cu", "revolve.cpp", "noalloc.cu", "postproc.cu", "stencil_pair.cu"]
+           "api.cu", "revolve.cpp", "noalloc.cu", "postproc.cu", "stencil_pair.cu", "cpml.cu"]
 
 
 def _nvcc() -> str:

@@ -17,6 +17,7 @@
 #include "conv.h"
 #include "gn.h"
 #include "common.cuh"
+#include "cpml.h"
 #include "postproc.h"
 #include "revolve.h"
 #include "stencil.h"
@@ -91,6 +92,10 @@ struct Plan {
   std::vector<RecEntry> prec;
   std::vector<long long> prec_cell;
   std::vector<float> prec_g;
+  // convolutional PML instead of the sponge
+  bool pml = false;
+  double pml_f0 = 0.0, pml_r = 1e-3;
+  float vmax = 0.f;  // max(vel), set by check_cfl
 };
 
 }  // namespace
@@ -107,6 +112,7 @@ struct mamute_ctx {
   DevBuf pitems, pnbr, precptr, prec, pcells, pgvals, pmaps, pflags;  // two-level launches
   bool pair_graph_failed = false;  // cooperative launches could not be captured
   DevBuf rsPtr, rsCol, rsW, dmod, ddat;      // time resampling: matrix, model- and data-axis traces
+  DevBuf cpml, cprof, cnode, crec, ccell, cgval, cunode, cuptr, cucol;  // convolutional PML
   DevBuf items, vols, maps, cmaps, recptr, rec, colmap, gx, gy, gz, cells, gvals, srccell,
       aitems, arecptr, arec, acolmap, acells, agvals;
   DevBuf hvel, hrho, hseis, hobs, hgrad, hphess;  // staging for the *_host calls
@@ -388,6 +394,15 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   if (g->xyz_interp != 0 && g->xyz_interp != 1)
     return fail(ctx, MAMUTE_EINVAL, "xyz_interp must be 0 or 1");
   if (!(g->cerjan >= 0.f)) return fail(ctx, MAMUTE_EINVAL, "cerjan must be >= 0");
+  if (g->pml != 0 && g->pml != 1) return fail(ctx, MAMUTE_EINVAL, "pml must be 0 or 1");
+  if (g->pml) {
+    if (g->free_surface) return fail(ctx, MAMUTE_EINVAL, "pml with a free surface is not supported");
+    if (!(g->pml_f0 >= 0.f)) return fail(ctx, MAMUTE_EINVAL, "pml_f0 must be >= 0");
+    if (!(g->pml_r >= 0.f && g->pml_r < 1.f)) return fail(ctx, MAMUTE_EINVAL, "pml_r must be in [0, 1)");
+    P.pml = true;
+    P.pml_f0 = g->pml_f0;
+    P.pml_r = g->pml_r > 0.f ? g->pml_r : 1e-3;
+  }
   if (n_src < 1 || !src_xyz || !rec_offset) return fail(ctx, MAMUTE_EINVAL, "no shots");
   if (rec_offset[0] != 0) return fail(ctx, MAMUTE_EINVAL, "rec_offset[0] must be 0");
   for (int s = 0; s < n_src; ++s)
@@ -586,7 +601,7 @@ cudaError_t aux_count(mamute_ctx* ctx, cudaError_t e) {
   return e;
 }
 
-int check_cfl(mamute_ctx* ctx, const Plan& P, const float* vel) {
+int check_cfl(mamute_ctx* ctx, Plan& P, const float* vel) {
   CK(cudaMemsetAsync(ctx->maxbits, 0, sizeof(unsigned int), ctx->stream));
   CK(aux_count(ctx, launch_max(vel, (long long)P.nx * P.ny * P.nz, ctx->maxbits, ctx->stream)));
   unsigned int bits = 0;
@@ -594,6 +609,7 @@ int check_cfl(mamute_ctx* ctx, const Plan& P, const float* vel) {
   CK(cudaStreamSynchronize(ctx->stream));
   float vmax;
   std::memcpy(&vmax, &bits, sizeof vmax);
+  P.vmax = vmax;
   const double courant = (double)vmax * P.dt / P.h;
   if (!(courant <= cfl_bound()))
     return fail(ctx, MAMUTE_ECFL, "max(c) dt / h = %.5f exceeds the stability bound %.5f", courant,
@@ -1072,6 +1088,306 @@ int data_to_user(mamute_ctx* ctx, const Plan& P, int n0, int n1, float* seis, cu
   return MAMUTE_OK;
 }
 
+// ---- Convolutional PML (Sec. 2, the second absorbing boundary) ----
+
+// Layer coefficients of one padded axis of N cells with `border` layer cells
+// at each end, appended to bo / co: b = exp(-(d + alpha) dt) and
+// c = d (b - 1) / (d + alpha) with, at depth r = dist / border,
+// d = d0 r^2, d0 = -3 vmax ln(R) / (2 border h), alpha = pi f0 (1 - r);
+// b = 1, c = 0 outside the layer.
+void cpml_profile(int N, int border, double h, double dt, double vmax, double f0, double R,
+                  std::vector<float>& bo, std::vector<float>& co) {
+  const double d0 = border > 0 ? -3.0 * vmax * std::log(R) / (2.0 * border * h) : 0.0;
+  for (int i = 0; i < N; ++i) {
+    int dist = 0;
+    if (i < border) dist = border - i;
+    else if (i > N - 1 - border) dist = i - (N - 1 - border);
+    double b = 1.0, c = 0.0;
+    if (dist > 0) {
+      const double r = (double)dist / border;
+      const double d = d0 * r * r, al = M_PI * f0 * (1.0 - r);
+      b = std::exp(-(d + al) * dt);
+      if (d + al > 0.0) c = d * (b - 1.0) / (d + al);
+    }
+    bo.push_back((float)b);
+    co.push_back((float)c);
+  }
+}
+
+// Pools of the PML calls, each P.pool_elems floats in ctx->cpml:
+//   0..2 psi (forward) / psib (reverse), 3..5 zeta / zetab, 6 xb, 7..9 y, 10..12 z.
+constexpr int kPmlPoolsModel = 6, kPmlPoolsGradient = 13;
+
+struct PmlTables {
+  CpmlProf pr;
+  long long max_pts = 0;
+  int n_unode = 0;
+};
+
+// Profiles, the data columns' nodes and scales, the receiver nodes of the
+// adjoint injection, and the pools (after setup()).
+int cpml_setup(mamute_ctx* ctx, const Plan& P, int n_pools, PmlTables& T) {
+  std::vector<float> bx, cx, by, cy, bz, cz;
+  for (const VolDesc& V : P.vols) {
+    cpml_profile(V.Nx, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bx, cx);
+    cpml_profile(V.Ny, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, by, cy);
+    T.max_pts = std::max(T.max_pts, (long long)V.Nx * V.Ny * V.Nz);
+  }
+  cpml_profile(P.Nz, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bz, cz);
+  std::vector<float> all;
+  size_t off[6];
+  const std::vector<float>* parts[6] = {&bx, &cx, &by, &cy, &bz, &cz};
+  for (int k = 0; k < 6; ++k) {
+    off[k] = all.size();
+    all.insert(all.end(), parts[k]->begin(), parts[k]->end());
+  }
+  CK(upload(ctx->cprof, all, ctx->stream));
+  const float* base = (const float*)ctx->cprof.p;
+  T.pr = CpmlProf{base + off[0], base + off[1], base + off[2], base + off[3], base + off[4],
+                  base + off[5]};
+  // Data columns in the forward tables' order (the layout data_to_user reads).
+  std::vector<int> ent_of_col(P.ncol, 0);
+  for (size_t e = 0; e < P.ent.size(); ++e) ent_of_col[P.fwd_col_of_ent[e]] = (int)e;
+  std::vector<long long> node(P.ncol), cell(P.ncol);
+  std::vector<RecEntry> rec(P.ncol);
+  std::vector<float> gval(P.ncol, 1.0f);
+  for (int c = 0; c < P.ncol; ++c) {
+    const NodeEntry& E = P.ent[ent_of_col[c]];
+    const VolDesc& V = P.vols[E.shot];
+    node[c] = V.off + ((long long)E.lz * V.Ny + E.ly) * V.pitch + E.lx;
+    cell[c] = E.cell;
+    rec[c] = RecEntry{};
+    rec[c].col = c;
+    rec[c].wgt = E.w;
+  }
+  // Distinct nodes, each with its columns in ascending order (one thread per
+  // node adds them in that order: no atomics, a fixed summation order).
+  std::vector<int> order(P.ncol);
+  for (int c = 0; c < P.ncol; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return node[a] < node[b]; });
+  std::vector<long long> unode;
+  std::vector<int> uptr, ucol;
+  for (int k = 0; k < P.ncol; ++k) {
+    const int c = order[k];
+    if (unode.empty() || unode.back() != node[c]) {
+      unode.push_back(node[c]);
+      uptr.push_back(k);
+    }
+    ucol.push_back(c);
+  }
+  uptr.push_back(P.ncol);
+  T.n_unode = (int)unode.size();
+  CK(upload(ctx->cnode, node, ctx->stream));
+  CK(upload(ctx->ccell, cell, ctx->stream));
+  CK(upload(ctx->crec, rec, ctx->stream));
+  CK(upload(ctx->cgval, gval, ctx->stream));
+  CK(upload(ctx->cunode, unode, ctx->stream));
+  CK(upload(ctx->cuptr, uptr, ctx->stream));
+  CK(upload(ctx->cucol, ucol, ctx->stream));
+  return MAMUTE_OK;
+}
+
+// fscale = w sqrt(rho) of the data columns (the velocity and density of this call).
+int cpml_scales(mamute_ctx* ctx, const Plan& P, const float* vel, const float* rho) {
+  if (P.ncol == 0) return MAMUTE_OK;
+  GeomArgs ga{vel, rho, P.ncol, 0, (const long long*)ctx->ccell.p, (const float*)ctx->cgval.p,
+              (RecEntry*)ctx->crec.p, nullptr, nullptr, nullptr, P.h, P.dt};
+  CK(aux_count(ctx, launch_geometry(ga, ctx->stream)));
+  return MAMUTE_OK;
+}
+
+float* cpml_pool(mamute_ctx* ctx, const Plan& P, int k) {
+  return (float*)ctx->cpml.p + (size_t)k * P.pool_elems;
+}
+
+// Forward time loop: u^0 = u^{-1} = 0 and zero memory variables (cleared by
+// the caller); the data sample of step n (sqrt(rho) u^{n+1} at the receiver
+// nodes) goes to row n of ctx->dint, the imaging term of step n to step n of
+// tstore when given.
+int cpml_forward(mamute_ctx* ctx, const Plan& P, const PmlTables& T, const float* wavelet,
+                 float* tstore) {
+  CpmlArgs a{};
+  a.vols = (const VolDesc*)ctx->vols.p;
+  a.pr = T.pr;
+  a.A = (const float*)ctx->coefA.p;
+  a.M = P.dens ? (const float*)ctx->coefM.p : nullptr;
+  a.pitchG = P.pitchG;
+  a.NyG = P.Ny;
+  for (int k = 0; k < 3; ++k) {
+    a.psi[k] = cpml_pool(ctx, P, k);
+    a.zeta[k] = cpml_pool(ctx, P, 3 + k);
+  }
+  float* u = (float*)ctx->pool[0].p;
+  float* v = (float*)ctx->pool[1].p;
+  const int nvol = (int)P.vols.size();
+  if (ctx->timing && !ctx->ev0_set) {
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    ctx->ev0_set = true;
+  }
+  for (int n = 0; n < P.nt; ++n) {
+    a.u = u;
+    a.v = v;
+    a.wn = wavelet[n];
+    a.tstore = tstore ? tstore + (size_t)n * P.term_elems : nullptr;
+    CK(launch_cpml_forward(a, nvol, T.max_pts, ctx->stream));
+    CK(launch_cpml_record(v, (const long long*)ctx->cnode.p, (const RecEntry*)ctx->crec.p, P.ncol,
+                          (float*)ctx->dint.p + (size_t)n * P.ncol, ctx->stream));
+    ctx->launches += 3;
+    ++ctx->step_launches;
+    std::swap(u, v);
+  }
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev1, ctx->stream));
+  return MAMUTE_OK;
+}
+
+int run_model_pml(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho,
+                  const float* wavelet, const mamute_opts* opts, int ti, int ntd, float* seis,
+                  float* host_seis) {
+  if (opts && opts->phess) return fail(ctx, MAMUTE_EINVAL, "phess is not available with pml");
+  TRY(setup(ctx, P, vel, rho, false, false));
+  PmlTables T;
+  TRY(cpml_setup(ctx, P, kPmlPoolsModel, T));
+  TRY(cpml_scales(ctx, P, vel, rho));
+  const size_t pool = (size_t)P.pool_elems * 4;
+  CK(ensure(ctx->cpml, kPmlPoolsModel * pool));
+  CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->cpml.p, 0, kPmlPoolsModel * pool, ctx->stream));
+  CK(ensure(ctx->dint, (size_t)P.nt * std::max(P.ncol, 1) * 4));
+  TRY(cpml_forward(ctx, P, T, wavelet, nullptr));
+  if (P.ncol > 0) {
+    if (ti == 0) {
+      TRY(data_to_user(ctx, P, 0, P.nt, seis, ctx->stream));
+    } else {
+      CK(ensure(ctx->dmod, (size_t)P.nrec * P.nt * 4));
+      TRY(data_to_user(ctx, P, 0, P.nt, (float*)ctx->dmod.p, ctx->stream));
+      TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 0,
+                      (const float*)ctx->dmod.p, seis));
+    }
+    if (host_seis)
+      CK(cudaMemcpyAsync(host_seis, seis, (size_t)P.nrec * ntd * 4, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+  }
+  return finish(ctx);
+}
+
+// Gradient of the PML scheme: the forward pass keeps the imaging term of
+// every step, the reverse pass runs the transposed recursion.
+int run_gradient_pml(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho,
+                     const float* wavelet, const float* d_in, bool residual_mode,
+                     const mamute_opts* opts, int ti, int ntd, int smode, double* misfit,
+                     float* grad) {
+  if (opts && opts->phess) return fail(ctx, MAMUTE_EINVAL, "phess is not available with pml");
+  if (opts && opts->n_snapshots > 0)
+    return fail(ctx, MAMUTE_EINVAL,
+                "a pml gradient keeps every step's imaging term: n_snapshots must be 0 or -1");
+  TRY(setup(ctx, P, vel, rho, false, true));
+  PmlTables T;
+  TRY(cpml_setup(ctx, P, kPmlPoolsGradient, T));
+  TRY(cpml_scales(ctx, P, vel, rho));
+  const size_t pool = (size_t)P.pool_elems * 4;
+  CK(ensure(ctx->cpml, kPmlPoolsGradient * pool));
+  release(ctx->slots);
+  if (ensure(ctx->tstore, (size_t)P.nt * P.term_elems * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, MAMUTE_ENOMEM, "the imaging terms of %d steps (%.2f GB) do not fit", P.nt,
+                (double)P.nt * P.term_elems * 4e-9);
+  }
+  const size_t ncol = std::max(P.ncol, 1);
+  CK(ensure(ctx->dint, (size_t)P.nt * ncol * 4));
+  CK(ensure(ctx->partial, (size_t)std::max(misfit_blocks((long long)ntd * P.nrec), 1) * 8));
+  CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->cpml.p, 0, kPmlPoolsGradient * pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->acc.p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->misfit.p, 0, 8, ctx->stream));
+  float* tst = (float*)ctx->tstore.p;
+  TRY(cpml_forward(ctx, P, T, wavelet, tst));
+  // Adjoint source on the modelling axis in the user layout [n_rec][nt].
+  const float* res = nullptr;
+  if (P.ncol > 0) {
+    CK(ensure(ctx->dtmp, (size_t)P.nrec * P.nt * 4));
+    float* r = (float*)ctx->dtmp.p;
+    res = r;
+    if (ti != 0) {
+      CK(ensure(ctx->ddat, (size_t)P.nrec * ntd * 4));
+      float* ddata = (float*)ctx->ddat.p;
+      if (residual_mode) {
+        TRY(data_to_user(ctx, P, 0, P.nt, r, ctx->stream));
+        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 0, r, ddata));
+        ctx->launches += 3;
+        CK(launch_misfit(ddata, d_in, (long long)ntd * P.nrec, (double*)ctx->partial.p,
+                         (double*)ctx->misfit.p, ctx->stream));
+        CK(launch_sub(ddata, d_in, (long long)ntd * P.nrec, ddata, ctx->stream));
+        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 1, ddata, r));
+      } else {
+        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 1, d_in, r));
+      }
+    } else if (residual_mode) {
+      TRY(data_to_user(ctx, P, 0, P.nt, r, ctx->stream));
+      ctx->launches += 3;
+      CK(launch_misfit(r, d_in, (long long)P.nt * P.nrec, (double*)ctx->partial.p,
+                       (double*)ctx->misfit.p, ctx->stream));
+      CK(launch_sub(r, d_in, (long long)P.nt * P.nrec, r, ctx->stream));
+    } else {
+      res = d_in;
+    }
+  }
+  // Reverse pass: lam (multiplier of u^{n+1}) and mu in the two working
+  // pools, the memory-variable multipliers in pools 0..5, scratch in 6..12.
+  CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
+  CK(cudaMemsetAsync(ctx->cpml.p, 0, kPmlPoolsGradient * pool, ctx->stream));
+  CpmlAdjArgs b{};
+  b.vols = (const VolDesc*)ctx->vols.p;
+  b.pr = T.pr;
+  b.A = (const float*)ctx->coefA.p;
+  b.M = P.dens ? (const float*)ctx->coefM.p : nullptr;
+  b.pitchG = P.pitchG;
+  b.NyG = P.Ny;
+  b.xb = cpml_pool(ctx, P, 6);
+  for (int k = 0; k < 3; ++k) {
+    b.psib[k] = cpml_pool(ctx, P, k);
+    b.zetab[k] = cpml_pool(ctx, P, 3 + k);
+    b.y[k] = cpml_pool(ctx, P, 7 + k);
+    b.z[k] = cpml_pool(ctx, P, 10 + k);
+  }
+  b.acc = (float*)ctx->acc.p;
+  float* lam = (float*)ctx->pool[0].p;
+  float* mu = (float*)ctx->pool[1].p;
+  const int nvol = (int)P.vols.size();
+  for (int n = P.nt - 1; n >= 0; --n) {
+    if (res)
+      CK(launch_cpml_inject(lam, (const long long*)ctx->cunode.p, (const int*)ctx->cuptr.p,
+                            (const int*)ctx->cucol.p, (const RecEntry*)ctx->crec.p,
+                            (const int*)ctx->colmap.p, res, P.nt, n, T.n_unode, ctx->stream));
+    b.lam = lam;
+    b.mu = mu;
+    b.tstore = tst + (size_t)n * P.term_elems;
+    CK(launch_cpml_adjoint(b, nvol, T.max_pts, ctx->stream));
+    ctx->launches += 4;
+    ++ctx->step_launches;
+    std::swap(lam, mu);
+  }
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev1, ctx->stream));
+  const int ztop = opts ? std::max(0, std::min(opts->zero_top_planes, P.nz)) : 0;
+  FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
+                  P.nx, P.ny, P.nz, P.b, P.dt, 2, smode ? 0 : ztop, grad, P.h};
+  CK(aux_count(ctx, launch_finalize(fa, ctx->stream)));
+  if (smode) {
+    TRY(do_smooth(ctx, P.nx, P.ny, P.nz, P.h, smode, opts->smooth_len, grad, grad));
+    if (ztop > 0) CK(cudaMemsetAsync(grad, 0, (size_t)ztop * P.nx * P.ny * 4, ctx->stream));
+  }
+  if (misfit) {
+    double J = 0.0;
+    CK(cudaMemcpyAsync(&J, ctx->misfit.p, sizeof J, cudaMemcpyDeviceToHost, ctx->stream));
+    TRY(finish(ctx));
+    *misfit = J;
+    return MAMUTE_OK;
+  }
+  return finish(ctx);
+}
+
 // host_seis (host, may be NULL): the seismograms also go to this host array,
 // segment by segment while later segments of the time loop run.
 int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float* rho,
@@ -1087,6 +1403,7 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   int ti = 0, ntd = P.nt;
   TRY(check_interp(ctx, g, opts, &ti, &ntd));
   TRY(check_cfl(ctx, P, vel));
+  if (P.pml) return run_model_pml(ctx, P, vel, rho, wavelet, opts, ti, ntd, seis, host_seis);
   const bool ph = opts && opts->phess;
   TRY(setup(ctx, P, vel, rho, false, ph));
   const size_t pool = (size_t)P.pool_elems * 4;
@@ -1304,6 +1621,9 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   const int smode = opts ? opts->smooth_mode : 0;
   if (smode < 0 || smode > 2) return fail(ctx, MAMUTE_EINVAL, "smooth_mode must be 0, 1 or 2");
   TRY(check_cfl(ctx, P, vel));
+  if (P.pml)
+    return run_gradient_pml(ctx, P, vel, rho, wavelet, d_in, residual_mode, opts, ti, ntd, smode,
+                            misfit, grad);
   const bool ph = opts && opts->phess;
   TRY(setup(ctx, P, vel, rho, true, true));
   const size_t pool = (size_t)P.pool_elems * 4;
@@ -1612,6 +1932,7 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   }
   Plan P;
   TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz, nullptr, P));
+  if (P.pml) return fail(ctx, MAMUTE_EINVAL, "the GN diagonal uses the sponge boundary (pml = 0)");
   if (!P.one_node)
     return fail(ctx, MAMUTE_EINVAL, "the Gauss-Newton diagonal needs receivers on grid nodes");
   ctx->max_planes = P.Nz;
@@ -1885,7 +2206,9 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
                    &ctx->slotmaps, &ctx->ident, &ctx->rcolptr, &ctx->rcols, &ctx->ecol,
                    &ctx->srcw, &ctx->smA, &ctx->smMat, &ctx->smLam, &ctx->rsPtr, &ctx->rsCol,
                    &ctx->rsW, &ctx->dmod, &ctx->ddat, &ctx->pitems, &ctx->pnbr, &ctx->precptr,
-                   &ctx->prec, &ctx->pcells, &ctx->pgvals, &ctx->pmaps, &ctx->pflags};
+                   &ctx->prec, &ctx->pcells, &ctx->pgvals, &ctx->pmaps, &ctx->pflags,
+                   &ctx->cpml, &ctx->cprof, &ctx->cnode, &ctx->crec, &ctx->ccell, &ctx->cgval,
+                   &ctx->cunode, &ctx->cuptr, &ctx->cucol};
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);

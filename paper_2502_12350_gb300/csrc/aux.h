@@ -38,9 +38,10 @@ struct FinalizeArgs {
   const float* vel;   // model [nz][ny][nx]
   int nx, ny, nz, border;
   double dt;
-  int kind;           // 0: gradient dJ/dc, 1: pseudo-Hessian
+  int kind;           // 0: gradient dJ/dc, 1: pseudo-Hessian, 2: dJ/dc of the PML scheme
   int zero_top;
   float* out;         // [nz][ny][nx]
+  double h;           // grid spacing (kind 2)
 };
 
 cudaError_t launch_prep_coef(const CoefPrepArgs& a, cudaStream_t s);

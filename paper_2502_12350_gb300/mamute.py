@@ -34,7 +34,8 @@ class Grid(ctypes.Structure):
                 ("border", ctypes.c_int), ("h", ctypes.c_float), ("dt", ctypes.c_float),
                 ("nt", ctypes.c_int), ("ox", ctypes.c_float), ("oy", ctypes.c_float),
                 ("oz", ctypes.c_float), ("cerjan", ctypes.c_float), ("free_surface", ctypes.c_int),
-                ("xyz_interp", ctypes.c_int)]
+                ("xyz_interp", ctypes.c_int), ("pml", ctypes.c_int), ("pml_f0", ctypes.c_float),
+                ("pml_r", ctypes.c_float)]
 
 
 class Opts(ctypes.Structure):
@@ -246,12 +247,15 @@ class Context:
 
 
 def make_grid(nx, ny, nz, border, h, dt, nt, origin=(0.0, 0.0, 0.0), cerjan=0.015,
-              free_surface=0, xyz_interp=0) -> Grid:
+              free_surface=0, xyz_interp=0, pml=0, pml_f0=0.0, pml_r=0.0) -> Grid:
     return Grid(nx, ny, nz, border, h, dt, nt, origin[0], origin[1], origin[2], cerjan,
-                int(free_surface), int(xyz_interp))
+                int(free_surface), int(xyz_interp), int(pml), float(pml_f0), float(pml_r))
 
 
-def grid_of(w, cerjan=0.015, free_surface=0, xyz_interp=0) -> Grid:
-    """Grid of a synthetic workload (see synth.Workload)."""
+def grid_of(w, cerjan=0.015, free_surface=0, xyz_interp=0, pml=0, pml_f0=None, pml_r=0.0) -> Grid:
+    """Grid of a synthetic workload (see synth.Workload); pml_f0 defaults to
+    the workload's peak frequency."""
+    f0 = getattr(w, "fpeak", 0.0) if pml_f0 is None else pml_f0
     return make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, cerjan=cerjan,
-                     free_surface=free_surface, xyz_interp=xyz_interp)
+                     free_surface=free_surface, xyz_interp=xyz_interp, pml=pml, pml_f0=f0,
+                     pml_r=pml_r)

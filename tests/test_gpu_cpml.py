@@ -1,0 +1,219 @@
+"""The convolutional-PML boundary through the C ABI against the CPML oracle.
+
+Tolerances as for the sponge path: seismogram relative L2 <= 1e-4 against
+the FP64 oracle; gradient cosine >= 0.9999, relative L2 <= 1e-3 and misfit
+within 1e-4 relative.  Absorption is checked at a larger size against a grid
+so wide that no reflection reaches the receivers in the window.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2502_12350_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEIS_TOL = 1e-4
+GRAD_COS = 0.9999
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_12350_gb300 import build, mamute
+    build.build()
+    c = mamute.Context(0)
+    lib = mamute.load()
+    lib.mamute_ctx_set_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mamute_ctx_last_timing.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_longlong)]
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def cosine(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+
+
+def _dev(x):
+    return None if x is None else torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+
+
+def _offgrid(w, seed):
+    rng = np.random.default_rng(seed)
+    hi = (np.array([w.nx, w.ny, w.nz]) - 1) * w.h - 1e-3
+    w.src_xyz = np.minimum(w.src_xyz + rng.uniform(0.1, 0.9, w.src_xyz.shape) * w.h,
+                           hi).astype(np.float32)
+    w.rec_xyz = np.minimum(w.rec_xyz + rng.uniform(0.1, 0.9, w.rec_xyz.shape) * w.h,
+                           hi).astype(np.float32)
+    return w
+
+
+def gpu_model(ctx, w, xi=0, **opts):
+    from paper_2502_12350_gb300 import mamute
+    nt_out = opts.get("nt_data", w.nt) if opts.get("time_interp", 0) else w.nt
+    seis = torch.full((int(w.rec_offset[-1]), nt_out), float("nan"), device="cuda:0")
+    ctx.model(mamute.grid_of(w, cerjan=0.0, xyz_interp=xi, pml=1), _dev(w.vel), _dev(w.rho),
+              w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, seis, **opts)
+    return seis.cpu().numpy()
+
+
+def gpu_gradient(ctx, w, dobs, xi=0, adjoint=False, **opts):
+    from paper_2502_12350_gb300 import mamute
+    grad = torch.full((w.nz, w.ny, w.nx), float("nan"), device="cuda:0")
+    g = mamute.grid_of(w, cerjan=0.0, xyz_interp=xi, pml=1)
+    args = (g, _dev(w.vel), _dev(w.rho), w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, _dev(dobs),
+            grad)
+    if adjoint:
+        ctx.adjoint(*args, **opts)
+        return grad.cpu().numpy()
+    J = ctx.gradient(*args, **opts)
+    return J, grad.cpu().numpy()
+
+
+def ogrid(oracle, w, xi=0):
+    return oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, xyz_interp=xi)
+
+
+CASES = [
+    dict(seed=30, nx=24, ny=20, nz=18, border=8, nt=60, density=True, n_src=2, n_rec=9),
+    dict(seed=31, nx=37, ny=29, nz=21, border=6, nt=70, density=False, n_src=3, n_rec=7),
+    dict(seed=32, nx=9, ny=5, nz=6, border=3, nt=30, density=True, n_src=1, n_rec=4),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("xi", [0, 1])
+def test_model_matches_oracle(ctx, oracle, case, xi):
+    from oracle import cpml
+    w = synth.small_case(**case)
+    if xi:
+        w = _offgrid(w, case["seed"])
+    got = gpu_model(ctx, w, xi)
+    ref = cpml.model(oracle, ogrid(oracle, w, xi), w.vel, w.src_xyz, w.wavelet, w.rec_offset,
+                     w.rec_xyz, f0=w.fpeak, rho=w.rho)
+    assert np.isfinite(got).all()
+    assert rel(got, ref) <= SEIS_TOL, rel(got, ref)
+
+
+@pytest.mark.parametrize("density,xi", [(True, 0), (False, 0), (True, 1)])
+def test_gradient_matches_oracle(ctx, oracle, density, xi):
+    from oracle import cpml
+    w = synth.small_case(seed=33, nx=22, ny=19, nz=17, border=7, nt=55, density=density, n_src=2,
+                         n_rec=8)
+    if xi:
+        w = _offgrid(w, 34)
+    og = ogrid(oracle, w, xi)
+    rng = np.random.default_rng(35)
+    vtrue = w.vel * (1 + 0.05 * rng.standard_normal(w.vel.shape))
+    dobs = cpml.model(oracle, og, vtrue, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                      f0=w.fpeak, rho=w.rho).astype(np.float32)
+    Jr, gr = cpml.gradient(oracle, og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs,
+                           f0=w.fpeak, rho=w.rho)
+    J, g = gpu_gradient(ctx, w, dobs, xi)
+    assert np.isfinite(g).all()
+    assert abs(J - Jr) <= 1e-4 * Jr, (J, Jr)
+    assert cosine(g, gr) >= GRAD_COS
+    assert rel(g, gr) <= 1e-3, rel(g, gr)
+
+
+def test_transposed_jacobian_matches_oracle(ctx, oracle):
+    """mamute_adjoint with a residual r is the gradient with d_obs = F(m) - r."""
+    from oracle import cpml
+    w = synth.small_case(seed=36, nx=20, ny=16, nz=15, border=6, nt=48, density=True, n_src=2,
+                         n_rec=6)
+    og = ogrid(oracle, w)
+    r = np.random.default_rng(37).standard_normal((int(w.rec_offset[-1]), w.nt)).astype(np.float32)
+    d = cpml.model(oracle, og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, f0=w.fpeak,
+                   rho=w.rho)
+    _, gr = cpml.gradient(oracle, og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                          d - r.astype(np.float64), f0=w.fpeak, rho=w.rho)
+    g = gpu_gradient(ctx, w, r, adjoint=True)
+    assert cosine(g, gr) >= GRAD_COS
+    assert rel(g, gr) <= 1e-3, rel(g, gr)
+
+
+def test_absorbs_better_than_the_sponge(ctx):
+    """48^3 model, 12-cell boundaries, receivers 4 cells from the edges; the
+    reference is the same source in a grid 60 cells wider on every side."""
+    from paper_2502_12350_gb300 import mamute
+    n, b, h, dt, nt, cv, f = 48, 12, 10.0, 1e-3, 300, 2000.0, 25.0
+    wav = synth.ricker(nt, dt, f).astype(np.float32)
+    c = n // 2
+    src = np.array([[c * h, c * h, c * h]], np.float32)
+    rec = np.array([[(n - 5) * h, c * h, c * h], [c * h, c * h, 4 * h], [3 * h, 3 * h, c * h],
+                    [c * h, (n - 5) * h, (n - 5) * h]], np.float32)
+    off = np.array([0, len(rec)], np.int32)
+    vel = torch.full((n, n, n), cv, device="cuda:0")
+
+    def run(grid, v, s, r):
+        out = torch.zeros((len(rec), nt), device="cuda:0")
+        ctx.model(grid, v, None, s, wav, off, r, out)
+        return out.cpu().numpy().astype(np.float64)
+
+    sponge = run(mamute.make_grid(n, n, n, b, h, dt, nt), vel, src, rec)
+    pml = run(mamute.make_grid(n, n, n, b, h, dt, nt, pml=1, pml_f0=f), vel, src, rec)
+    big, pad = n + 120, 60
+    ref = run(mamute.make_grid(big, big, big, b, h, dt, nt, cerjan=0.0),
+              torch.full((big, big, big), cv, device="cuda:0"), src + pad * h, rec + pad * h)
+    e_sponge, e_pml = rel(sponge, ref), rel(pml, ref)
+    assert e_pml < 0.05 * e_sponge, (e_pml, e_sponge)
+    assert e_pml < 1e-4, e_pml
+
+
+def test_host_entry_points_and_time_axis(ctx):
+    from paper_2502_12350_gb300 import mamute
+    w = synth.small_case(seed=38, nx=26, ny=18, nz=16, border=6, nt=64, density=True, n_src=2,
+                         n_rec=5)
+    dev = gpu_model(ctx, w)
+    host = np.zeros_like(dev)
+    ctx.model_host(mamute.grid_of(w, cerjan=0.0, pml=1), np.ascontiguousarray(w.vel),
+                   np.ascontiguousarray(w.rho), w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                   host)
+    np.testing.assert_array_equal(host, dev)
+    # data on a coarser axis: the modelled traces resampled by mamute_resample
+    ntd, dtd = 20, 3 * w.dt
+    ti = gpu_model(ctx, w, time_interp=mamute.INTERP_SINC, nt_data=ntd, dt_data=dtd)
+    y = torch.zeros((dev.shape[0], ntd), device="cuda:0")
+    ctx.resample(torch.from_numpy(dev).cuda(), w.dt, ntd, dtd, mamute.INTERP_SINC, y)
+    np.testing.assert_array_equal(ti, y.cpu().numpy())
+    # the gradient on that axis is J^T K^T (K d - d_obs)
+    dobs = np.random.default_rng(39).standard_normal((dev.shape[0], ntd)).astype(np.float32)
+    J, g = gpu_gradient(ctx, w, dobs, time_interp=mamute.INTERP_SINC, nt_data=ntd, dt_data=dtd)
+    r = torch.zeros((dev.shape[0], w.nt), device="cuda:0")
+    ctx.resample(torch.from_numpy(ti - dobs).cuda(), w.dt, ntd, dtd, mamute.INTERP_SINC, r,
+                 adjoint=True, nt_in=w.nt)
+    ga = gpu_gradient(ctx, w, r.cpu().numpy(), adjoint=True)
+    assert abs(J - 0.5 * np.sum((ti.astype(np.float64) - dobs) ** 2)) <= 1e-5 * J
+    np.testing.assert_array_equal(g, ga)
+
+
+def test_invalid_combinations(ctx):
+    from paper_2502_12350_gb300 import mamute
+    w = synth.small_case(seed=40, nx=16, ny=12, nz=12, border=4, nt=20, density=False, n_src=1,
+                         n_rec=3)
+    seis = torch.zeros((3, w.nt), device="cuda:0")
+    grad = torch.zeros((w.nz, w.ny, w.nx), device="cuda:0")
+    vel = _dev(w.vel)
+    geo = (w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz)
+    with pytest.raises(mamute.MamuteError) as e:
+        ctx.model(mamute.grid_of(w, pml=1, free_surface=1), vel, None, *geo, seis)
+    assert e.value.code == mamute.EINVAL
+    with pytest.raises(mamute.MamuteError) as e:
+        ctx.gradient(mamute.grid_of(w, pml=1), vel, None, *geo, seis, grad, n_snapshots=3)
+    assert e.value.code == mamute.EINVAL
+    with pytest.raises(mamute.MamuteError) as e:
+        ctx.model(mamute.grid_of(w, pml=1), vel, None, *geo, seis, phess=grad)
+    assert e.value.code == mamute.EINVAL
+    with pytest.raises(mamute.MamuteError) as e:
+        ctx.model(mamute.grid_of(w, pml=1, pml_r=1.5), vel, None, *geo, seis)
+    assert e.value.code == mamute.EINVAL

@@ -2,7 +2,7 @@
 
 * With no damping and no frequency shift the memory variables stay zero and
   the scheme is the main one without sponge: the main oracle's traces, to
-  rounding.
+  rounding (nearest-node and trilinear sources and receivers).
 * The gradient is the transpose of the modelling map: dot-product identity
   for wavelet -> traces, and central finite differences of the misfit.
 * It absorbs: on a small grid, the error against a grid so large that no
@@ -21,10 +21,22 @@ def _tiny(density, nt=40, seed=3):
                             n_src=2, n_rec=4, fpeak=30.0)
 
 
-@pytest.mark.parametrize("density", [False, True])
-def test_no_damping_is_the_main_scheme(oracle, density):
+def _offgrid(w, seed):
+    rng = np.random.default_rng(seed)
+    w.src_xyz = w.src_xyz + rng.uniform(0.1, 0.9, w.src_xyz.shape) * w.h
+    w.rec_xyz = w.rec_xyz + rng.uniform(0.1, 0.9, w.rec_xyz.shape) * w.h
+    hi = (np.array([w.nx, w.ny, w.nz]) - 1) * w.h - 1e-3
+    w.src_xyz = np.minimum(w.src_xyz, hi)
+    w.rec_xyz = np.minimum(w.rec_xyz, hi)
+    return w
+
+
+@pytest.mark.parametrize("density,xi", [(False, 0), (True, 0), (True, 1)])
+def test_no_damping_is_the_main_scheme(oracle, density, xi):
     w = _tiny(density)
-    g = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, cerjan=0.0)
+    if xi:
+        w = _offgrid(w, 8)
+    g = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, cerjan=0.0, xyz_interp=xi)
     ref = oracle.model(g, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho)
     got = cpml.model(oracle, g, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, f0=0.0,
                      rho=w.rho, R=1.0)
@@ -32,10 +44,12 @@ def test_no_damping_is_the_main_scheme(oracle, density):
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("density", [False, True])
-def test_dot_product(oracle, density):
+@pytest.mark.parametrize("density,xi", [(False, 0), (True, 0), (True, 1)])
+def test_dot_product(oracle, density, xi):
     w = _tiny(density, seed=4)
-    g = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
+    if xi:
+        w = _offgrid(w, 9)
+    g = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, xyz_interp=xi)
     rng = np.random.default_rng(5)
     wav = rng.standard_normal(w.nt)
     r = rng.standard_normal((int(w.rec_offset[-1]), w.nt))
