@@ -40,18 +40,20 @@ KERNEL_SOURCES = ["paper_2502_12350_gb300/csrc/stencil_impl.cuh",
                   "paper_2502_12350_gb300/csrc/stencil_fwd.cu",
                   "paper_2502_12350_gb300/csrc/stencil_pair.cu",
                   "paper_2502_12350_gb300/csrc/common.cuh"]
+PML_SOURCES = ["paper_2502_12350_gb300/csrc/cpml.cu", "paper_2502_12350_gb300/csrc/cpml.h",
+               "paper_2502_12350_gb300/csrc/common.cuh"]
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def kernel_traffic(w, kernel="step_kernel_forward"):
+def kernel_traffic(w, kernel="step_kernel_forward", sources=KERNEL_SOURCES):
     """DRAM bytes per launch of the forward kernel from the committed ncu
     summary of this workload, or None if the kernel source changed since."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{w.name}.md")
@@ -62,7 +64,7 @@ def kernel_traffic(w, kernel="step_kernel_forward"):
                 if ":" in line and line.startswith("- "):
                     k, v = line[2:].split(":", 1)
                     fields[k.strip()] = v.strip().strip("`")
-        if fields.get("source_sha256") != kernel_source_hash():
+        if fields.get("source_sha256") != kernel_source_hash(sources):
             return None
         return int(fields["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -468,6 +470,67 @@ def run_gn_bench(args):
     return 0
 
 
+def pml_bytes_per_step(w):
+    """Algorithmic DRAM bytes of one CPML time step: u^n, u^{n-1}, A (and
+    A m2) read and u^{n+1} written at every padded point, plus the two memory
+    variables of each axis read and written at the points in that axis's
+    layer."""
+    Nx, Ny, Nz = w.nx + 2 * w.border, w.ny + 2 * w.border, w.nz + 2 * w.border
+    base = (20 if w.rho is not None else 16) * Nx * Ny * Nz
+    layer = 2 * w.border * (Ny * Nz + Nx * Nz + Nx * Ny)  # (point, axis) pairs in a layer
+    return base + 16 * layer
+
+
+def pml_line(args, w, world, total_ms, value, e2e, vel_h, rho_h, seis_h, launches, step_ms, peak,
+             peak_kind, clocks):
+    alg = pml_bytes_per_step(w)
+    achieved = alg / (step_ms / 1e3) / 1e9
+    n_rec = int(w.rec_offset[-1])
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name + f"_{w.nt}steps_cpml", "boundary": "convolutional PML",
+                   "padded": list(w.padded)[::-1], "nt": w.nt, "shots": 1, "receivers": n_rec,
+                   "l2": "every array (%d MB) is larger than L2" % (w.n_padded * 4 // 2**20),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(vel_h.numel() * 4 + (0 if rho_h is None else rho_h.numel() * 4)),
+                "d2h_bytes_per_step": int(seis_h.numel() * 4)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak,
+                     "traffic": kernel_traffic(w, "cpml_step", PML_SOURCES),
+                     "peak_kind": peak_kind,
+                     "kernel": "CPML time step (psi_kernel + step_kernel_pml + record_kernel)",
+                     "bytes_per_step": alg, "step_ms": step_ms},
+        "clocks": clocks,
+    }
+
+
+def pml_cpu_baseline(w):
+    """The CPML oracle on a bounded sample: the model cropped to 64^3 (same
+    border), 6 time steps, operator assembly excluded."""
+    from oracle import cpml as ocpml
+    from oracle import oracle as orc
+    n, nt = 64, 6
+    vel = np.ascontiguousarray(w.vel[:n, :n, :n], np.float64)
+    rho = None if w.rho is None else np.ascontiguousarray(w.rho[:n, :n, :n], np.float64)
+    g = orc.make_grid(n, n, n, w.border, w.h, w.dt, nt)
+    src = np.array([[n // 2 * w.h] * 3])
+    rec = np.array([[n // 2 * w.h, n // 2 * w.h, 4 * w.h]])
+    op = ocpml.Operators(orc, g, vel, rho, w.fpeak)
+    sn, scale, S = ocpml._shot(op, src, 0, [0, 1], rec)
+    t0 = time.perf_counter()
+    ocpml.forward(op, w.wavelet[:nt].astype(np.float64), sn, scale, S)
+    dt = time.perf_counter() - t0
+    pts = (n + 2 * w.border) ** 3 * nt
+    return {"value": pts / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"CPML oracle (scipy sparse products, FP64, one thread) on the model "
+                      f"cropped to {n}^3 with border {w.border}, {nt} time steps after operator "
+                      f"assembly"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,6 +541,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-blocking", type=int, default=0, choices=[0, 2],
                     help="model workloads: 2 = two time steps per launch (two-level kernel)")
+    ap.add_argument("--boundary", default="sponge", choices=["sponge", "pml"],
+                    help="model workloads: absorbing boundary (pml: convolutional PML)")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the 256^3 FWI gradient object of the headline line")
     ap.add_argument("--workload", default="model",
@@ -518,7 +583,8 @@ def main():
 
     w = workload(args.nt, args.workload)
     nt = w.nt
-    g = mamute.grid_of(w)
+    pml = args.boundary == "pml"
+    g = mamute.grid_of(w, cerjan=0.0, pml=1) if pml else mamute.grid_of(w)
     stream = torch.cuda.current_stream(dev)
     ctx = mamute.Context(local, stream.cuda_stream)
     lib = mamute.load()
@@ -589,6 +655,17 @@ def main():
 
     peak, peak_kind = _peaks()
     kernel_ms = statistics.median(loop_ms) / max(step_launches, 1)
+    if pml:
+        line = pml_line(args, w, world, total_ms, value, e2e, vel_h, rho_h, seis_h, launches,
+                        kernel_ms, peak, peak_kind, clk.summary())
+        ctx.close()
+        if rank == 0 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = pml_cpu_baseline(w)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
     # Algorithmic bytes per point and launch: u^n, u^{n-1}, A (and A m2) read
     # once, one new level written per time step the launch advances (two on
     # the two-level kernel).
