@@ -112,7 +112,7 @@ struct mamute_ctx {
   DevBuf pitems, pnbr, precptr, prec, pcells, pgvals, pmaps, pflags;  // two-level launches
   bool pair_graph_failed = false;  // cooperative launches could not be captured
   DevBuf rsPtr, rsCol, rsW, dmod, ddat;      // time resampling: matrix, model- and data-axis traces
-  DevBuf cpml, cprof, cnode, crec, ccell, cgval, cunode, cuptr, cucol;  // convolutional PML
+  DevBuf cpml, cprof, cnode, crec, ccell, cgval;  // convolutional PML
   DevBuf items, vols, maps, cmaps, recptr, rec, colmap, gx, gy, gz, cells, gvals, srccell,
       aitems, arecptr, arec, acolmap, acells, agvals;
   DevBuf hvel, hrho, hseis, hobs, hgrad, hphess;  // staging for the *_host calls
@@ -417,7 +417,9 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   if ((long long)P.Nz * P.Ny * P.pitchG >= nmax * 4)
     return fail(ctx, MAMUTE_EINVAL, "grid too large");
   P.zs = g->free_surface ? P.b : -1;
-  P.gz = sponge(P.Nz, P.b, g->cerjan, P.zs);
+  // The CPML replaces the sponge: damping factor 1 in the main step.
+  const double alpha = P.pml ? 0.0 : (double)g->cerjan;
+  P.gz = sponge(P.Nz, P.b, alpha, P.zs);
   // Model cells and weights of a point: its nearest node, or the trilinear
   // weights of the cell that holds it (zero weights dropped).  Nodes on a
   // free surface are dropped too (the field is zero there); false if the
@@ -479,15 +481,20 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
     V.cx0 = a0; V.cy0 = a2;
     V.Nx = (a1 - a0) + 2 * P.b; V.Ny = (a3 - a2) + 2 * P.b; V.Nz = P.Nz;
     V.pitch = (int)round_up(V.Nx, 8);
-    V.border = P.b; V.nxi = a1 - a0; V.nyi = a3 - a2; V.nzi = P.nz;
+    V.border = P.b; V.nzi = P.nz;
+    // imaging region: window cells inside the model (model x = a0 - b + local x)
+    V.ix0 = std::max(0, P.b - a0);
+    V.nxi = std::min(V.Nx, P.nx + P.b - a0) - V.ix0;
+    V.iy0 = std::max(0, P.b - a2);
+    V.nyi = std::min(V.Ny, P.ny + P.b - a2) - V.iy0;
     V.slab = round_up((long long)V.Nz * V.Ny * V.pitch, 64);
     V.off = off; off += V.slab;
     // Term-store rows start on a 16-byte boundary of the local x axis (TMA).
-    V.txoff = P.b & ~3;
-    V.tpitch = (int)round_up(P.b - V.txoff + V.nxi, 4);
+    V.txoff = V.ix0 & ~3;
+    V.tpitch = (int)round_up(V.ix0 - V.txoff + V.nxi, 4);
     V.toff = toff; toff += (long long)V.tpitch * V.nyi * V.nzi;
     V.gx_off = (int)P.gx.size(); V.gy_off = (int)P.gy.size();
-    std::vector<float> px = sponge(V.Nx, P.b, g->cerjan), py = sponge(V.Ny, P.b, g->cerjan);
+    std::vector<float> px = sponge(V.Nx, P.b, alpha), py = sponge(V.Ny, P.b, alpha);
     P.gx.insert(P.gx.end(), px.begin(), px.end());
     P.gy.insert(P.gy.end(), py.begin(), py.end());
     const int lo[2] = {a0, a2}, hi[2] = {a1, a3};
@@ -1114,24 +1121,26 @@ void cpml_profile(int N, int border, double h, double dt, double vmax, double f0
   }
 }
 
-// Pools of the PML calls, each P.pool_elems floats in ctx->cpml:
-//   0..2 psi (forward) / psib (reverse), 3..5 zeta / zetab, 6 xb, 7..9 y, 10..12 z.
-constexpr int kPmlPoolsModel = 6, kPmlPoolsGradient = 13;
+// Pools of the CPML memory variables, each P.pool_elems floats in ctx->cpml:
+// 0..2 Psi_a, 3..5 Zeta_a (their multipliers in the reverse pass), 6..8 y_a,
+// 9..11 z_a (reverse scratch).
+constexpr int kPmlPoolsModel = 6, kPmlPoolsGradient = 12;
 
 struct PmlTables {
-  CpmlProf pr;
-  long long max_pts = 0;
-  int n_unode = 0;
+  CpmlArgs base{};          // buffers and profiles; u, out, tstore, acc set per launch
+  long long max_layer = 0;  // shell points of width border (largest window)
+  long long max_shell = 0;  // shell points of width border + 4
 };
 
-// Profiles, the data columns' nodes and scales, the receiver nodes of the
-// adjoint injection, and the pools (after setup()).
-int cpml_setup(mamute_ctx* ctx, const Plan& P, int n_pools, PmlTables& T) {
+// Profiles, the data columns' nodes and scales, and the pools (after setup()).
+int cpml_setup(mamute_ctx* ctx, const Plan& P, const float* vel, const float* rho, int n_pools,
+               PmlTables& T) {
   std::vector<float> bx, cx, by, cy, bz, cz;
   for (const VolDesc& V : P.vols) {
     cpml_profile(V.Nx, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bx, cx);
     cpml_profile(V.Ny, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, by, cy);
-    T.max_pts = std::max(T.max_pts, (long long)V.Nx * V.Ny * V.Nz);
+    T.max_layer = std::max(T.max_layer, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b));
+    T.max_shell = std::max(T.max_shell, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b + 4));
   }
   cpml_profile(P.Nz, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bz, cz);
   std::vector<float> all;
@@ -1143,9 +1152,8 @@ int cpml_setup(mamute_ctx* ctx, const Plan& P, int n_pools, PmlTables& T) {
   }
   CK(upload(ctx->cprof, all, ctx->stream));
   const float* base = (const float*)ctx->cprof.p;
-  T.pr = CpmlProf{base + off[0], base + off[1], base + off[2], base + off[3], base + off[4],
-                  base + off[5]};
-  // Data columns in the forward tables' order (the layout data_to_user reads).
+  // Data columns in the forward tables' order (the layout data_to_user
+  // reads), sampled after the memory-variable correction of each step.
   std::vector<int> ent_of_col(P.ncol, 0);
   for (size_t e = 0; e < P.ent.size(); ++e) ent_of_col[P.fwd_col_of_ent[e]] = (int)e;
   std::vector<long long> node(P.ncol), cell(P.ncol);
@@ -1160,232 +1168,58 @@ int cpml_setup(mamute_ctx* ctx, const Plan& P, int n_pools, PmlTables& T) {
     rec[c].col = c;
     rec[c].wgt = E.w;
   }
-  // Distinct nodes, each with its columns in ascending order (one thread per
-  // node adds them in that order: no atomics, a fixed summation order).
-  std::vector<int> order(P.ncol);
-  for (int c = 0; c < P.ncol; ++c) order[c] = c;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return node[a] < node[b]; });
-  std::vector<long long> unode;
-  std::vector<int> uptr, ucol;
-  for (int k = 0; k < P.ncol; ++k) {
-    const int c = order[k];
-    if (unode.empty() || unode.back() != node[c]) {
-      unode.push_back(node[c]);
-      uptr.push_back(k);
-    }
-    ucol.push_back(c);
-  }
-  uptr.push_back(P.ncol);
-  T.n_unode = (int)unode.size();
   CK(upload(ctx->cnode, node, ctx->stream));
   CK(upload(ctx->ccell, cell, ctx->stream));
   CK(upload(ctx->crec, rec, ctx->stream));
   CK(upload(ctx->cgval, gval, ctx->stream));
-  CK(upload(ctx->cunode, unode, ctx->stream));
-  CK(upload(ctx->cuptr, uptr, ctx->stream));
-  CK(upload(ctx->cucol, ucol, ctx->stream));
-  return MAMUTE_OK;
-}
-
-// fscale = w sqrt(rho) of the data columns (the velocity and density of this call).
-int cpml_scales(mamute_ctx* ctx, const Plan& P, const float* vel, const float* rho) {
-  if (P.ncol == 0) return MAMUTE_OK;
-  GeomArgs ga{vel, rho, P.ncol, 0, (const long long*)ctx->ccell.p, (const float*)ctx->cgval.p,
-              (RecEntry*)ctx->crec.p, nullptr, nullptr, nullptr, P.h, P.dt};
-  CK(aux_count(ctx, launch_geometry(ga, ctx->stream)));
-  return MAMUTE_OK;
-}
-
-float* cpml_pool(mamute_ctx* ctx, const Plan& P, int k) {
-  return (float*)ctx->cpml.p + (size_t)k * P.pool_elems;
-}
-
-// Forward time loop: u^0 = u^{-1} = 0 and zero memory variables (cleared by
-// the caller); the data sample of step n (sqrt(rho) u^{n+1} at the receiver
-// nodes) goes to row n of ctx->dint, the imaging term of step n to step n of
-// tstore when given.
-int cpml_forward(mamute_ctx* ctx, const Plan& P, const PmlTables& T, const float* wavelet,
-                 float* tstore) {
-  CpmlArgs a{};
-  a.vols = (const VolDesc*)ctx->vols.p;
-  a.pr = T.pr;
-  a.A = (const float*)ctx->coefA.p;
-  a.M = P.dens ? (const float*)ctx->coefM.p : nullptr;
-  a.pitchG = P.pitchG;
-  a.NyG = P.Ny;
-  for (int k = 0; k < 3; ++k) {
-    a.psi[k] = cpml_pool(ctx, P, k);
-    a.zeta[k] = cpml_pool(ctx, P, 3 + k);
+  if (P.ncol > 0) {  // fscale = w sqrt(rho) of the columns
+    GeomArgs ga{vel, rho, P.ncol, 0, (const long long*)ctx->ccell.p, (const float*)ctx->cgval.p,
+                (RecEntry*)ctx->crec.p, nullptr, nullptr, nullptr, P.h, P.dt};
+    CK(aux_count(ctx, launch_geometry(ga, ctx->stream)));
   }
-  float* u = (float*)ctx->pool[0].p;
-  float* v = (float*)ctx->pool[1].p;
+  const size_t pool = (size_t)P.pool_elems * 4;
+  CK(ensure(ctx->cpml, (size_t)n_pools * pool));
+  CK(cudaMemsetAsync(ctx->cpml.p, 0, (size_t)n_pools * pool, ctx->stream));
+  CpmlArgs& c = T.base;
+  c.vols = (const VolDesc*)ctx->vols.p;
+  c.pr = CpmlProf{base + off[0], base + off[1], base + off[2], base + off[3], base + off[4],
+                  base + off[5]};
+  c.A = (const float*)ctx->coefA.p;
+  c.pitchG = P.pitchG;
+  c.NyG = P.Ny;
+  for (int k = 0; k < 3; ++k) {
+    c.m1[k] = (float*)ctx->cpml.p + (size_t)k * P.pool_elems;
+    c.m2[k] = (float*)ctx->cpml.p + (size_t)(3 + k) * P.pool_elems;
+    c.y[k] = n_pools > 6 ? (float*)ctx->cpml.p + (size_t)(6 + k) * P.pool_elems : nullptr;
+    c.z[k] = n_pools > 6 ? (float*)ctx->cpml.p + (size_t)(9 + k) * P.pool_elems : nullptr;
+  }
+  return MAMUTE_OK;
+}
+
+// One forward CPML step around the main step launch `main` (u^n in u, the
+// main kernel writes u^{n+1} to out): the Psi update before it, the Zeta
+// update and the correction of u^{n+1} (and of the stored term) after it,
+// then the data sample of the step into drow (may be null).
+template <typename Main>
+int cpml_fwd_step(mamute_ctx* ctx, const Plan& P, const PmlTables& T, const float* u, float* out,
+                  float* tstore, float* drow, Main main) {
+  CpmlArgs c = T.base;
+  c.u = u;
+  c.out = out;
+  c.tstore = tstore;
   const int nvol = (int)P.vols.size();
   if (ctx->timing && !ctx->ev0_set) {
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     ctx->ev0_set = true;
   }
-  for (int n = 0; n < P.nt; ++n) {
-    a.u = u;
-    a.v = v;
-    a.wn = wavelet[n];
-    a.tstore = tstore ? tstore + (size_t)n * P.term_elems : nullptr;
-    CK(launch_cpml_forward(a, nvol, T.max_pts, ctx->stream));
-    CK(launch_cpml_record(v, (const long long*)ctx->cnode.p, (const RecEntry*)ctx->crec.p, P.ncol,
-                          (float*)ctx->dint.p + (size_t)n * P.ncol, ctx->stream));
-    ctx->launches += 3;
-    ++ctx->step_launches;
-    std::swap(u, v);
-  }
+  CK(aux_count(ctx, launch_cpml_psi(c, nvol, T.max_layer, ctx->stream)));
+  TRY(main());
+  CK(aux_count(ctx, launch_cpml_fcorr(c, nvol, T.max_shell, ctx->stream)));
+  if (drow)
+    CK(aux_count(ctx, launch_cpml_record(out, (const long long*)ctx->cnode.p,
+                                         (const RecEntry*)ctx->crec.p, P.ncol, drow, ctx->stream)));
   if (ctx->timing) CK(cudaEventRecord(ctx->ev1, ctx->stream));
   return MAMUTE_OK;
-}
-
-int run_model_pml(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho,
-                  const float* wavelet, const mamute_opts* opts, int ti, int ntd, float* seis,
-                  float* host_seis) {
-  if (opts && opts->phess) return fail(ctx, MAMUTE_EINVAL, "phess is not available with pml");
-  TRY(setup(ctx, P, vel, rho, false, false));
-  PmlTables T;
-  TRY(cpml_setup(ctx, P, kPmlPoolsModel, T));
-  TRY(cpml_scales(ctx, P, vel, rho));
-  const size_t pool = (size_t)P.pool_elems * 4;
-  CK(ensure(ctx->cpml, kPmlPoolsModel * pool));
-  CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
-  CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
-  CK(cudaMemsetAsync(ctx->cpml.p, 0, kPmlPoolsModel * pool, ctx->stream));
-  CK(ensure(ctx->dint, (size_t)P.nt * std::max(P.ncol, 1) * 4));
-  TRY(cpml_forward(ctx, P, T, wavelet, nullptr));
-  if (P.ncol > 0) {
-    if (ti == 0) {
-      TRY(data_to_user(ctx, P, 0, P.nt, seis, ctx->stream));
-    } else {
-      CK(ensure(ctx->dmod, (size_t)P.nrec * P.nt * 4));
-      TRY(data_to_user(ctx, P, 0, P.nt, (float*)ctx->dmod.p, ctx->stream));
-      TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 0,
-                      (const float*)ctx->dmod.p, seis));
-    }
-    if (host_seis)
-      CK(cudaMemcpyAsync(host_seis, seis, (size_t)P.nrec * ntd * 4, cudaMemcpyDeviceToHost,
-                         ctx->stream));
-  }
-  return finish(ctx);
-}
-
-// Gradient of the PML scheme: the forward pass keeps the imaging term of
-// every step, the reverse pass runs the transposed recursion.
-int run_gradient_pml(mamute_ctx* ctx, Plan& P, const float* vel, const float* rho,
-                     const float* wavelet, const float* d_in, bool residual_mode,
-                     const mamute_opts* opts, int ti, int ntd, int smode, double* misfit,
-                     float* grad) {
-  if (opts && opts->phess) return fail(ctx, MAMUTE_EINVAL, "phess is not available with pml");
-  if (opts && opts->n_snapshots > 0)
-    return fail(ctx, MAMUTE_EINVAL,
-                "a pml gradient keeps every step's imaging term: n_snapshots must be 0 or -1");
-  TRY(setup(ctx, P, vel, rho, false, true));
-  PmlTables T;
-  TRY(cpml_setup(ctx, P, kPmlPoolsGradient, T));
-  TRY(cpml_scales(ctx, P, vel, rho));
-  const size_t pool = (size_t)P.pool_elems * 4;
-  CK(ensure(ctx->cpml, kPmlPoolsGradient * pool));
-  release(ctx->slots);
-  if (ensure(ctx->tstore, (size_t)P.nt * P.term_elems * 4) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(ctx, MAMUTE_ENOMEM, "the imaging terms of %d steps (%.2f GB) do not fit", P.nt,
-                (double)P.nt * P.term_elems * 4e-9);
-  }
-  const size_t ncol = std::max(P.ncol, 1);
-  CK(ensure(ctx->dint, (size_t)P.nt * ncol * 4));
-  CK(ensure(ctx->partial, (size_t)std::max(misfit_blocks((long long)ntd * P.nrec), 1) * 8));
-  CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
-  CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
-  CK(cudaMemsetAsync(ctx->cpml.p, 0, kPmlPoolsGradient * pool, ctx->stream));
-  CK(cudaMemsetAsync(ctx->acc.p, 0, pool, ctx->stream));
-  CK(cudaMemsetAsync(ctx->misfit.p, 0, 8, ctx->stream));
-  float* tst = (float*)ctx->tstore.p;
-  TRY(cpml_forward(ctx, P, T, wavelet, tst));
-  // Adjoint source on the modelling axis in the user layout [n_rec][nt].
-  const float* res = nullptr;
-  if (P.ncol > 0) {
-    CK(ensure(ctx->dtmp, (size_t)P.nrec * P.nt * 4));
-    float* r = (float*)ctx->dtmp.p;
-    res = r;
-    if (ti != 0) {
-      CK(ensure(ctx->ddat, (size_t)P.nrec * ntd * 4));
-      float* ddata = (float*)ctx->ddat.p;
-      if (residual_mode) {
-        TRY(data_to_user(ctx, P, 0, P.nt, r, ctx->stream));
-        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 0, r, ddata));
-        ctx->launches += 3;
-        CK(launch_misfit(ddata, d_in, (long long)ntd * P.nrec, (double*)ctx->partial.p,
-                         (double*)ctx->misfit.p, ctx->stream));
-        CK(launch_sub(ddata, d_in, (long long)ntd * P.nrec, ddata, ctx->stream));
-        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 1, ddata, r));
-      } else {
-        TRY(do_resample(ctx, P.nrec, P.nt, P.dt, ntd, opts->dt_data, ti, 1, d_in, r));
-      }
-    } else if (residual_mode) {
-      TRY(data_to_user(ctx, P, 0, P.nt, r, ctx->stream));
-      ctx->launches += 3;
-      CK(launch_misfit(r, d_in, (long long)P.nt * P.nrec, (double*)ctx->partial.p,
-                       (double*)ctx->misfit.p, ctx->stream));
-      CK(launch_sub(r, d_in, (long long)P.nt * P.nrec, r, ctx->stream));
-    } else {
-      res = d_in;
-    }
-  }
-  // Reverse pass: lam (multiplier of u^{n+1}) and mu in the two working
-  // pools, the memory-variable multipliers in pools 0..5, scratch in 6..12.
-  CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
-  CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
-  CK(cudaMemsetAsync(ctx->cpml.p, 0, kPmlPoolsGradient * pool, ctx->stream));
-  CpmlAdjArgs b{};
-  b.vols = (const VolDesc*)ctx->vols.p;
-  b.pr = T.pr;
-  b.A = (const float*)ctx->coefA.p;
-  b.M = P.dens ? (const float*)ctx->coefM.p : nullptr;
-  b.pitchG = P.pitchG;
-  b.NyG = P.Ny;
-  b.xb = cpml_pool(ctx, P, 6);
-  for (int k = 0; k < 3; ++k) {
-    b.psib[k] = cpml_pool(ctx, P, k);
-    b.zetab[k] = cpml_pool(ctx, P, 3 + k);
-    b.y[k] = cpml_pool(ctx, P, 7 + k);
-    b.z[k] = cpml_pool(ctx, P, 10 + k);
-  }
-  b.acc = (float*)ctx->acc.p;
-  float* lam = (float*)ctx->pool[0].p;
-  float* mu = (float*)ctx->pool[1].p;
-  const int nvol = (int)P.vols.size();
-  for (int n = P.nt - 1; n >= 0; --n) {
-    if (res)
-      CK(launch_cpml_inject(lam, (const long long*)ctx->cunode.p, (const int*)ctx->cuptr.p,
-                            (const int*)ctx->cucol.p, (const RecEntry*)ctx->crec.p,
-                            (const int*)ctx->colmap.p, res, P.nt, n, T.n_unode, ctx->stream));
-    b.lam = lam;
-    b.mu = mu;
-    b.tstore = tst + (size_t)n * P.term_elems;
-    CK(launch_cpml_adjoint(b, nvol, T.max_pts, ctx->stream));
-    ctx->launches += 4;
-    ++ctx->step_launches;
-    std::swap(lam, mu);
-  }
-  if (ctx->timing) CK(cudaEventRecord(ctx->ev1, ctx->stream));
-  const int ztop = opts ? std::max(0, std::min(opts->zero_top_planes, P.nz)) : 0;
-  FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(), vel,
-                  P.nx, P.ny, P.nz, P.b, P.dt, 2, smode ? 0 : ztop, grad, P.h};
-  CK(aux_count(ctx, launch_finalize(fa, ctx->stream)));
-  if (smode) {
-    TRY(do_smooth(ctx, P.nx, P.ny, P.nz, P.h, smode, opts->smooth_len, grad, grad));
-    if (ztop > 0) CK(cudaMemsetAsync(grad, 0, (size_t)ztop * P.nx * P.ny * 4, ctx->stream));
-  }
-  if (misfit) {
-    double J = 0.0;
-    CK(cudaMemcpyAsync(&J, ctx->misfit.p, sizeof J, cudaMemcpyDeviceToHost, ctx->stream));
-    TRY(finish(ctx));
-    *misfit = J;
-    return MAMUTE_OK;
-  }
-  return finish(ctx);
 }
 
 // host_seis (host, may be NULL): the seismograms also go to this host array,
@@ -1403,9 +1237,11 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   int ti = 0, ntd = P.nt;
   TRY(check_interp(ctx, g, opts, &ti, &ntd));
   TRY(check_cfl(ctx, P, vel));
-  if (P.pml) return run_model_pml(ctx, P, vel, rho, wavelet, opts, ti, ntd, seis, host_seis);
   const bool ph = opts && opts->phess;
+  if (P.pml && ph) return fail(ctx, MAMUTE_EINVAL, "phess is not available with pml");
   TRY(setup(ctx, P, vel, rho, false, ph));
+  PmlTables T;
+  if (P.pml) TRY(cpml_setup(ctx, P, vel, rho, kPmlPoolsModel, T));
   const size_t pool = (size_t)P.pool_elems * 4;
   CK(cudaMemsetAsync(ctx->pool[0].p, 0, pool, ctx->stream));
   CK(cudaMemsetAsync(ctx->pool[1].p, 0, pool, ctx->stream));
@@ -1413,7 +1249,7 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
   CK(ensure(ctx->dint, (size_t)P.nt * std::max(P.ncol, 1) * 4));
   const int mode = ph ? MODE_FWD_PH : MODE_FWD;
   // Two time levels per launch where the problem allows it.
-  const bool pairs = !ph && plan_pairs(ctx, P, opts);
+  const bool pairs = !ph && !P.pml && plan_pairs(ctx, P, opts);
   if (pairs) {
     TRY(setup_pairs(ctx, P, vel, rho));
     CK(cudaMemsetAsync(ctx->pflags.p, 0, P.pitems.size() * 4, ctx->stream));
@@ -1447,6 +1283,9 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
     for (const DevBuf* b : {&ctx->pitems, &ctx->pnbr, &ctx->precptr, &ctx->prec, &ctx->pmaps,
                             &ctx->pflags})
       push(pairs ? b->p : nullptr);
+    key.push_back(P.pml ? 1 : 0);
+    for (const DevBuf* b : {&ctx->cpml, &ctx->cprof, &ctx->cnode, &ctx->crec})
+      push(P.pml ? b->p : nullptr);
     key.push_back(stream_out ? 1 : 0);
     if (stream_out) {
       push(seis);
@@ -1488,6 +1327,14 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
         CK(launch_pair(a, (int)P.pitems.size(), P.Nz, P.ptx, P.pty, P.dens, ctx->stream, nullptr));
         if (ctx->timing) CK(cudaEventRecord(ctx->ev1, ctx->stream));
         n += 2;
+      } else if (P.pml) {
+        StepArgs a = fwd_args(ctx, P, n, wavelet, nullptr, mode);
+        TRY(cpml_fwd_step(ctx, P, T, (const float*)ctx->pool[n & 1].p, a.fout, nullptr,
+                          P.ncol > 0 ? drow : nullptr, [&]() -> int {
+                            CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+                            return MAMUTE_OK;
+                          }));
+        n += 1;
       } else {
         StepArgs a = fwd_args(ctx, P, n, wavelet, drow, mode);
         CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
@@ -1580,7 +1427,8 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
     }
     const int loop = pairs ? (P.nt / 2 + P.nt % 2) : P.nt;
     ctx->step_launches = loop;
-    ctx->launches += loop + (stream_out ? std::min(P.nt, 8) * (P.one_node ? 1 : 2) : 0);
+    ctx->launches += loop * (P.pml ? (P.ncol > 0 ? 4 : 3) : 1) +
+                     (stream_out ? std::min(P.nt, 8) * (P.one_node ? 1 : 2) : 0);
   }
 loop_done:
   if (!stream_out) {
@@ -1621,11 +1469,14 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   const int smode = opts ? opts->smooth_mode : 0;
   if (smode < 0 || smode > 2) return fail(ctx, MAMUTE_EINVAL, "smooth_mode must be 0, 1 or 2");
   TRY(check_cfl(ctx, P, vel));
-  if (P.pml)
-    return run_gradient_pml(ctx, P, vel, rho, wavelet, d_in, residual_mode, opts, ti, ntd, smode,
-                            misfit, grad);
   const bool ph = opts && opts->phess;
+  if (P.pml && ph) return fail(ctx, MAMUTE_EINVAL, "phess is not available with pml");
+  if (P.pml && opts && opts->n_snapshots > 0)
+    return fail(ctx, MAMUTE_EINVAL,
+                "a pml gradient keeps every step's imaging term: n_snapshots must be 0 or -1");
   TRY(setup(ctx, P, vel, rho, true, true));
+  PmlTables T;
+  if (P.pml) TRY(cpml_setup(ctx, P, vel, rho, kPmlPoolsGradient, T));
   const size_t pool = (size_t)P.pool_elems * 4;
   const size_t ncol = std::max(P.ncol, 1);
   CK(ensure(ctx->dint, (size_t)P.nt * ncol * 4));
@@ -1656,12 +1507,15 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
         cudaGetLastError();
     }
   }
+  if (P.pml && !all_mode)
+    return fail(ctx, MAMUTE_ENOMEM, "the imaging terms of %d steps (%.2f GB) do not fit", P.nt,
+                (double)P.nt * P.term_elems * 4e-9);
   if (!all_mode && ctx->tstore.p) release(ctx->tstore);  // room for the slots
   int slots = 0;
   if (all_mode) {
     CK(ensure(ctx->tstore, (size_t)P.nt * P.term_elems * 4));
     bool pads = false;
-    for (const VolDesc& V : P.vols) pads = pads || V.txoff != V.border || V.tpitch != V.nxi;
+    for (const VolDesc& V : P.vols) pads = pads || V.txoff != V.ix0 || V.tpitch != V.nxi;
     if (pads) CK(cudaMemsetAsync(ctx->tstore.p, 0, (size_t)P.nt * P.term_elems * 4, ctx->stream));
     for (size_t s = 0; s < P.vols.size(); ++s) {
       const VolDesc& V = P.vols[s];
@@ -1750,7 +1604,18 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     a.mU = a.mF;
     a.sU = a.sF;
     a.fout = (float*)buf_ptr(out);
-    CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+    if (P.pml) {
+      // the data sample is taken after the memory-variable correction
+      float* drow = a.dout;
+      a.dout = nullptr;
+      TRY(cpml_fwd_step(ctx, P, T, (const float*)buf_ptr(cur), a.fout, a.tstore, drow,
+                        [&]() -> int {
+                          CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+                          return MAMUTE_OK;
+                        }));
+    } else {
+      CK(step_launch(ctx, a, (int)P.items.size(), P.tx, P.ty, P.dens, mode));
+    }
     if (rec) recorded = n + 1;
     prev = cur;
     cur = out;
@@ -1829,12 +1694,29 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     a.rin = (const float*)ctx->rint.p + (size_t)i * P.ncol;
     a.status = ctx->status;
     a.zs = P.zs;
+    if (P.pml) {  // memory-variable multipliers from psi^{k+1}
+      CpmlArgs c = T.base;
+      c.u = (const float*)ctx->psi[(k + 1) & 1].p;
+      CK(aux_count(ctx, launch_cpml_pre(c, nvol, T.max_layer, ctx->stream)));
+      ++ctx->launches;
+    }
     CK(step_launch(ctx, a, (int)P.aitems.size(), P.atx, P.aty, P.dens,
                    all_mode ? MODE_ADJ_STORED : MODE_ADJ));
+    if (P.pml) {  // psi^k and the accumulator += the memory-variable part
+      CpmlArgs c = T.base;
+      c.u = (const float*)ctx->psi[(k + 1) & 1].p;
+      c.out = (float*)ctx->psi[k & 1].p;
+      c.tstore = (float*)ctx->tstore.p + (size_t)i * P.term_elems;
+      c.acc = (float*)ctx->acc.p;
+      CK(aux_count(ctx, launch_cpml_acorr(c, nvol, T.max_shell, ctx->stream)));
+      if (ctx->timing) CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    }
     return MAMUTE_OK;
   };
   auto begin_adjoint = [&]() -> int {
     TRY(make_residual());
+    if (P.pml)  // the memory variables' multipliers start at zero
+      CK(cudaMemsetAsync(ctx->cpml.p, 0, (size_t)kPmlPoolsGradient * pool, ctx->stream));
     if (ph) {
       FinalizeArgs fa{(const float*)ctx->acc.p, (const VolDesc*)ctx->vols.p, (int)P.vols.size(),
                       vel, P.nx, P.ny, P.nz, P.b, P.dt, 1, 0, opts->phess};
@@ -2207,8 +2089,7 @@ void mamute_ctx_destroy(mamute_ctx* ctx) {
                    &ctx->srcw, &ctx->smA, &ctx->smMat, &ctx->smLam, &ctx->rsPtr, &ctx->rsCol,
                    &ctx->rsW, &ctx->dmod, &ctx->ddat, &ctx->pitems, &ctx->pnbr, &ctx->precptr,
                    &ctx->prec, &ctx->pcells, &ctx->pgvals, &ctx->pmaps, &ctx->pflags,
-                   &ctx->cpml, &ctx->cprof, &ctx->cnode, &ctx->crec, &ctx->ccell, &ctx->cgval,
-                   &ctx->cunode, &ctx->cuptr, &ctx->cucol};
+                   &ctx->cpml, &ctx->cprof, &ctx->cnode, &ctx->crec, &ctx->ccell, &ctx->cgval};
   for (DevBuf* b : all) release(*b);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->maxbits) cudaFree(ctx->maxbits);

@@ -202,8 +202,7 @@ __global__ void sum_partials_kernel(const double* partial, int n, double* out) {
   }
 }
 
-// grad[z][y][x] = 2 / (c^3 dt^2) sum_s G_s (2 c dt^2 / h^2 sum_s G_s for the
-// PML scheme), or phess = sum_s P_s / (c dt)^4,
+// grad[z][y][x] = 2 / (c^3 dt^2) sum_s G_s, or phess = sum_s P_s / (c dt)^4,
 // summed over shots in ascending order (deterministic).
 __global__ void finalize_kernel(FinalizeArgs a) {
   const long long n = (long long)a.nx * a.ny * a.nz;
@@ -214,18 +213,15 @@ __global__ void finalize_kernel(FinalizeArgs a) {
     float acc = 0.0f;
     for (int s = 0; s < a.n_vol; ++s) {
       const VolDesc& V = a.vols[s];
+      // the window's imaging region (its cells inside the model)
       const int lx = X - V.cx0, ly = Y - V.cy0;
-      if (lx < 0 || ly < 0 || lx >= V.Nx || ly >= V.Ny) continue;
+      if (lx < V.ix0 || ly < V.iy0 || lx >= V.ix0 + V.nxi || ly >= V.iy0 + V.nyi) continue;
       acc += a.acc[V.off + ((long long)Z * V.Ny + ly) * V.pitch + lx];
     }
     const double cv = a.vel[p];
     double out;
     if (a.kind == 0) {
       out = 2.0 * (double)acc / (cv * cv * cv * a.dt * a.dt);
-      if (z < a.zero_top) out = 0.0;
-    } else if (a.kind == 2) {
-      // acc = h^2 sum_n lam (x - m2 u) = h^2 dJ/d(c^2 dt^2)
-      out = 2.0 * cv * a.dt * a.dt * (double)acc / (a.h * a.h);
       if (z < a.zero_top) out = 0.0;
     } else {
       const double A2 = cv * cv * a.dt * a.dt;

@@ -32,16 +32,15 @@ struct GeomArgs {
 };
 
 struct FinalizeArgs {
-  const float* acc;   // accumulator pool
+  const float* acc;   // accumulator pool (read on each window's imaging region)
   const VolDesc* vols;
   int n_vol;
   const float* vel;   // model [nz][ny][nx]
   int nx, ny, nz, border;
   double dt;
-  int kind;           // 0: gradient dJ/dc, 1: pseudo-Hessian, 2: dJ/dc of the PML scheme
+  int kind;           // 0: gradient dJ/dc, 1: pseudo-Hessian
   int zero_top;
   float* out;         // [nz][ny][nx]
-  double h;           // grid spacing (kind 2)
 };
 
 cudaError_t launch_prep_coef(const CoefPrepArgs& a, cudaStream_t s);

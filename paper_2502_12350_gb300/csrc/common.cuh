@@ -33,11 +33,17 @@ struct VolDesc {
   // source cell (nearest node: corner 0 only; trilinear: the 8 weights w_e)
   float src_sc[8];
   int border;            // sponge cells on each face
-  int nxi, nyi, nzi;     // interior (model) extent of the window
+  // Imaging region: the window's cells that lie in the model, local x in
+  // [ix0, ix0 + nxi), y in [iy0, iy0 + nyi), z in [border, border + nzi).  The
+  // stored imaging terms cover it (rows of tpitch floats from local x =
+  // txoff), and the gradient / pseudo-Hessian take the accumulator (pool
+  // layout) on it.
+  int ix0, iy0;
+  int nxi, nyi, nzi;
   int txoff, tpitch;     // term store rows: local x in [txoff, txoff + tpitch)
   long long off;         // element offset of the shot's arrays in each pool
   long long slab;        // elements per wavefield array (Nz * Ny * pitch, rounded)
-  long long toff;        // offset of the shot's interior in one step of the term store
+  long long toff;        // offset of the shot's region in one step of the term store
 };
 
 // One CTA's work: the w x h tile at (x0, y0) of one shot's padded window

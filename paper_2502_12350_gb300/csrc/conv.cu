@@ -352,9 +352,10 @@ void conv_gy_box(unsigned (&box)[4]) {
 
 // Blocking of the tensor-core convolution for a D x H x W volume: the
 // tallest row block (at most 8 chunks of 128 outputs) whose halo slots leave
-// room for a ring of 5 (lookahead of 2 planes), else the tallest with 4.
+// room for a ring of 4 (each halo plane is consumed by one step), else the
+// tallest with 3.
 constexpr int kTcSmemMax = 232448;                  // dynamic shared memory per CTA
-constexpr int kTcSlotBudget = kTcSmemMax - kTaps * 512 - 1024;
+constexpr int kTcSlotBudget = kTcSmemMax - kTcWBytes - 1024;
 
 static TcPlan tc_plan(int D, int H, int W) {
   TcPlan p{};
@@ -371,7 +372,7 @@ static TcPlan tc_plan(int D, int H, int W) {
   };
   const int ry_max = std::max(1, std::min(H, (kTcMaxChunks * 128) / p.P));
   int pick = 0;
-  for (int want = 5; want >= 3 && !pick; --want)
+  for (int want = 4; want >= 3 && !pick; --want)
     for (int ry = ry_max; ry >= 1; --ry) {
       shape(ry);
       if (p.rows <= 256 && p.ring >= want) {
@@ -398,7 +399,7 @@ static TcPlan tc_plan(int D, int H, int W) {
 }
 
 static size_t tc_smem_bytes(const TcPlan& p) {
-  return (size_t)p.ring * p.slot_bytes + (size_t)kTaps * 512 + 1024;
+  return (size_t)p.ring * p.slot_bytes + (size_t)kTcWBytes + 1024;
 }
 
 void conv_halo_box(int D, int H, int W, unsigned (&box)[4]) {
@@ -422,7 +423,7 @@ cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& xmap, int* status,
     attr = sm;
   }
   const int grid = (int)std::min<long long>(p.items, 152);
-  conv_tc_kernel<<<grid, 192, sm, s>>>(xmap, a, p, status);
+  conv_tc_kernel<<<grid, kTcThreads, sm, s>>>(xmap, a, p, status);
   return cudaGetLastError();
 }
 

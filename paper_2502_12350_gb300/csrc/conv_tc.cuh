@@ -16,22 +16,43 @@
 // stored), so the A rows of tap (dz, dy, dx) for the 128 outputs
 // f0 .. f0+127 are the 128 consecutive halo voxels starting at
 // f0 + dy P + dx of halo plane z + dz: one descriptor per tap and chunk, no
-// data movement.  Per output plane: NCH chunks x 27 taps of
-// tcgen05.mma.kind::f16 M=128 N=16 K=16 (bf16 in, f32 accumulate) into
-// NCH x 16 TMEM columns; the epilogue warps read one voxel's 16 output
+// data movement.
+//
+// Plane stacking.  Halo plane h feeds output planes h + 1, h and h - 1
+// through the kernel's dz = 0, 1, 2 taps with the same A operand, so each
+// halo plane is consumed once: per chunk, 9 (dy, dx) products of
+// tcgen05.mma.kind::f16 M=128 N=64 K=16 (bf16 in, f32 accumulate) whose 64
+// columns are the chunk's 4 accumulator slots of 16 output channels.  Plane
+// p lives in slot p mod 4; at step h the slots hold planes h + 1 (first
+// contribution: zeroed just before by an N=16 product with a zero B), h,
+// h - 1 (last contribution) and h - 2 (complete, read by the epilogue
+// meanwhile: its B columns are zero, so the products rewrite its values
+// unchanged).  The B operand is the window of 4 blocks at offset (1 - h)
+// mod 4 of the block sequence [dz2, dz1, dz0, 0, dz2, dz1, dz0] of the
+// (dy, dx) tap's weights.  The epilogue warps read one voxel's 16 output
 // channels per thread with tcgen05.ld and store 32 (bf16) or 64 (f32)
 // contiguous bytes.
 //
-// Warp roles (192 threads): warp 0 lane 0 issues the TMA loads of halo
+// Warp roles (320 threads): warp 0 lane 0 issues the TMA loads of halo
 // planes into a ring of slots; warp 1 allocates TMEM and lane 0 issues
-// the MMAs; warps 2-5 (TMEM lane quarters 2, 3, 0, 1) run the epilogue from
-// a double-buffered accumulator.  Every wait is bounded; a timeout sets the
-// status flag and a CTA-wide abort flag that ends every role's loop.
+// the MMAs; warps 2-9 run the epilogue, two per TMEM lane quarter (warp w
+// reads lanes 32 (w mod 4) ..), each taking every other chunk.  Every wait
+// is bounded; a timeout sets the status flag and a CTA-wide abort flag that
+// ends every role's loop.
 
 constexpr int kTcMaxRing = 6;        // halo plane slots (at most)
-constexpr int kTcCols = 256;         // TMEM columns: 2 buffers x 8 chunks x 16
+constexpr int kTcCols = 512;         // TMEM columns: 8 chunks x 4 plane slots x 16
 constexpr int kTcMaxChunks = 8;
 constexpr int kTcMaxP = 200;         // halo row width (x segment + 2)
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
+// B operand: per (dy, dx) tap, 7 blocks x 16 output channels (N rows) x 16
+// input channels (K), K-major core matrices: 8-row groups 128 bytes apart,
+// the two 8-channel K halves kTcWHalf bytes apart.
+constexpr int kTcWBlocks = 7;
+constexpr int kTcWHalf = kTcWBlocks * 16 * 16;   // bytes
+constexpr int kTcWTap = 2 * kTcWHalf;            // bytes per (dy, dx) tap
+constexpr int kTcWBytes = 9 * kTcWTap;
 
 struct TcPlan {
   int P, SW, RY, NCH, rows, ZC, ring;
@@ -121,6 +142,17 @@ __device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint3
 // bits 24-28.
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) |
                               ((128u >> 4) << 24);
+constexpr uint32_t kTcIdesc64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
+                                ((128u >> 4) << 24);
+
+// 16 consecutive f32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 
 // Bounded wait that also ends when another role has aborted.
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* status,
@@ -134,25 +166,28 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* sta
   return false;
 }
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, ConvArgs a, TcPlan pl, int* status) {
   extern __shared__ unsigned char tc_raw[];
   // the 32-byte swizzle acts on address bits 4 and 7: slots on 1024 bytes
   unsigned char* sm = tc_raw + ((1024 - (smem_u32(tc_raw) & 1023)) & 1023);
   unsigned char* slots = sm;                               // ring x slot_bytes
-  unsigned char* wts = sm + pl.ring * pl.slot_bytes;       // [27][k half][16 out][8 in] bf16
-  __shared__ uint64_t full[kTcMaxRing], empty[kTcMaxRing], tfull[2], tempty[2], done_bar;
+  unsigned char* wts = sm + pl.ring * pl.slot_bytes;       // kTcWBytes, see kTcWBlocks
+  __shared__ uint64_t full[kTcMaxRing], empty[kTcMaxRing], tfull[4], tempty[4], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   volatile int* ab = &abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // B operand: weights w[tap][o][i] in the K-major canonical layout (core
-  // matrix = 8 out channels x 8 in channels; out groups 128 B apart, in
-  // halves 256 B apart).
-  for (int e = threadIdx.x; e < kTaps * kC * kC; e += blockDim.x) {
-    const int tap = e / (kC * kC), o = (e / kC) % kC, i = e % kC;
-    reinterpret_cast<uint16_t*>(wts)[(tap * 2 + (i >> 3)) * 128 + o * 8 + (i & 7)] = a.w[e];
+  // B blocks: block j of tap (dy, dx) holds w[dz][dy][dx][o][i] for the dz of
+  // the sequence [2, 1, 0, -, 2, 1, 0] (block 3 zero).
+  for (int e = threadIdx.x; e < 9 * kTcWBlocks * kC * kC; e += blockDim.x) {
+    const int t9 = e / (kTcWBlocks * kC * kC), j = (e / (kC * kC)) % kTcWBlocks;
+    const int o = (e / kC) % kC, i = e % kC;
+    const int dz = j == 3 ? -1 : 2 - (j % 4);
+    const uint16_t v = dz < 0 ? (uint16_t)0 : a.w[((dz * 9 + t9) * kC + o) * kC + i];
+    reinterpret_cast<uint16_t*>(wts)[(t9 * kTcWTap + (i >> 3) * kTcWHalf) / 2 + (j * 16 + o) * 8 +
+                                     (i & 7)] = v;
   }
   fence_async_smem();  // visible to the tensor cores (async proxy)
   if (threadIdx.x == 0) {
@@ -160,9 +195,9 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 4);
+      mbar_init(&tempty[i], kTcEpiWarps);
     }
     mbar_init(&done_bar, 1);
     fence_barrier_init();
@@ -207,127 +242,124 @@ __global__ void __launch_bounds__(192, 1)
         }
     }
   } else if (warp == 1) {
-    // ---- MMA issuer
+    // ---- MMA issuer: one step per halo plane (global step counter t)
     if (lane == 0) {
       const uint32_t wbase = smem_u32(wts), sbase = smem_u32(slots);
-      uint32_t q0 = 0, p = 0;
-      for (long long it = blockIdx.x; it < pl.items && !*ab; it += gridDim.x) {
+      const uint64_t bw = tc_sdesc(wbase, (uint32_t)kTcWHalf, 128u);
+      const uint64_t bzero = bw + 3ull * 16u;  // block 3 (zeros), N = 16
+      const uint64_t rowoff[3] = {0ull, 2ull * (uint64_t)pl.P, 4ull * (uint64_t)pl.P};
+      uint32_t t = 0;
+      bool ok = true;
+      for (long long it = blockIdx.x; it < pl.items && ok && !*ab; it += gridDim.x) {
         int xs, y0, z0, nz;
         geom(it, xs, y0, z0, nz);
-        for (int j = 0; j < nz; ++j, ++p) {
-          const int buf = (int)(p & 1);
-          if (!tc_wait(&tempty[buf], ((p >> 1) & 1) ^ 1, status, ab)) break;
-          // Taps in dz order: the oldest halo plane (dz = 0) is released as soon
-          // as its products are done, so its slot refills while the newer
-          // planes' products run, and the newest plane is needed last.
-          const uint64_t b0 = tc_sdesc(wbase, 256u, 128u);
-          const uint64_t rowoff[3] = {0ull, 2ull * (uint64_t)pl.P, 4ull * (uint64_t)pl.P};
-          bool ok = true;
+        for (int k = 0; k < nz + 2; ++k, ++t) {
+          const uint32_t hs = t % (uint32_t)pl.ring;
+          if (!(ok = tc_wait(&full[hs], (t / pl.ring) & 1, status, ab))) break;
+          const uint32_t sn = (t + 1) & 3;  // slot of plane h + 1
+          if (t >= 2 && !(ok = tc_wait(&tempty[sn], ((t - 2) >> 2) & 1, status, ab))) break;
+          tc_fence_after();
+          // start-address field (address >> 4) advanced by chunk * 128 +
+          // dy * P + dx voxels of 32 bytes (2 units each)
+          const uint64_t a0 = tc_sdesc(sbase + hs * (uint32_t)pl.slot_bytes, 16u, 256u, 6u);
+          const uint64_t bwin = bw + (uint64_t)(((1u - t) & 3u) * 16u);
+          for (int c = 0; c < pl.NCH; ++c) {
+            const uint32_t d = tmem + (uint32_t)(c * 64);
+            const uint64_t ac = a0 + (uint64_t)c * 256u;
+            tc_mma(d + sn * 16u, ac, bzero, kTcIdesc, 0u);
 #pragma unroll
-          for (int dz = 0; dz < 3; ++dz) {
-            const uint32_t q = q0 + j + dz;
-            if (!(ok = tc_wait(&full[q % pl.ring], (q / pl.ring) & 1, status, ab))) break;
-            tc_fence_after();
-            // start-address field (address >> 4) advanced by
-            // chunk * 128 + dy * P + dx voxels of 32 bytes (2 units each)
-            const uint64_t a0 = tc_sdesc(sbase + (q % pl.ring) * (uint32_t)pl.slot_bytes, 16u,
-                                         256u, 6u);
-            for (int c = 0; c < pl.NCH; ++c) {
-              const uint32_t d = tmem + (uint32_t)(buf * 128 + c * 16);
-              const uint64_t ac = a0 + (uint64_t)c * 256u;
-#pragma unroll
-              for (int t9 = 0; t9 < 9; ++t9) {
-                const int dy = t9 / 3, dx = t9 % 3;
-                tc_mma(d, ac + rowoff[dy] + 2ull * (uint64_t)dx, b0 + (uint64_t)(dz * 9 + t9) * 32u,
-                       kTcIdesc, (dz | t9) != 0);
-              }
+            for (int t9 = 0; t9 < 9; ++t9) {
+              const int dy = t9 / 3, dx = t9 % 3;
+              tc_mma(d, ac + rowoff[dy] + 2ull * (uint64_t)dx,
+                     bwin + (uint64_t)t9 * (uint64_t)(kTcWTap >> 4), kTcIdesc64, 1u);
             }
-            if (dz == 0) tc_commit(&empty[(q0 + j) % pl.ring]);
           }
-          if (!ok) break;
-          tc_commit(&tfull[buf]);
-          if (j == nz - 1) {
-            tc_commit(&empty[(q0 + j + 1) % pl.ring]);
-            tc_commit(&empty[(q0 + j + 2) % pl.ring]);
-          }
+          tc_commit(&empty[hs]);
+          tc_commit(&tfull[(t + 3) & 3]);  // plane h - 1 complete
         }
-        q0 += nz + 2;
       }
       tc_commit(&done_bar);  // every MMA issued above has completed
       mbar_wait(&done_bar, 0, status);
     }
   } else {
     // ---- epilogue: one output voxel (16 channels) per thread and chunk
-    const int quarter = warp & 3;
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
     const int row = quarter * 32 + lane;
     float bias[kC];
 #pragma unroll
     for (int o = 0; o < kC; ++o) bias[o] = a.bias ? a.bias[o] : 0.f;
-    uint32_t p = 0;
     // Lane 0 waits and reads the abort flag for the warp, so the break and
     // the tcgen05.ld that follows (a .sync.aligned warp instruction) are
     // taken by the whole warp together.
     auto warp_stop = [&]() { return __shfl_sync(0xffffffffu, lane == 0 ? (int)(*ab != 0) : 0, 0) != 0; };
-    for (long long it = blockIdx.x; it < pl.items && !warp_stop(); it += gridDim.x) {
+    uint32_t t = 0;
+    bool ok = true;
+    for (long long it = blockIdx.x; it < pl.items && ok && !warp_stop(); it += gridDim.x) {
       int xs, y0, z0, nz;
       geom(it, xs, y0, z0, nz);
-      bool ok = true;
-      for (int j = 0; j < nz; ++j, ++p) {
-        const int buf = (int)(p & 1);
+      for (int k = 0; k < nz + 2; ++k, ++t) {
+        const uint32_t sd = (t + 3) & 3;  // slot of plane h - 1
         int got = 0;
-        if (lane == 0) got = tc_wait(&tfull[buf], (p >> 1) & 1, status, ab) ? 1 : 0;
+        if (lane == 0) got = tc_wait(&tfull[sd], (t >> 2) & 1, status, ab) ? 1 : 0;
         if (!(ok = __shfl_sync(0xffffffffu, got, 0) != 0)) break;
         tc_fence_after();
-        const int z = z0 + j;
-        for (int c0 = 0; c0 < pl.NCH; c0 += 4) {  // 4 chunks (64 columns) per TMEM load
-          uint32_t r[64];
-          tc_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 128 + c0 * 16), r);
-          tc_wait_ld();
+        if (k >= 2) {
+          const int z = z0 + k - 2;
+          for (int c0 = half; c0 < pl.NCH; c0 += 8) {  // up to 4 chunks per TMEM wait
+            uint32_t r[64];
 #pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const int f = (c0 + cc) * 128 + row;
-            const int ry = f / pl.P, xx = f % pl.P;
-            const int y = y0 + ry, x = xs + xx;
-            if (c0 + cc >= pl.NCH || ry >= pl.RY || xx >= pl.SW || y >= a.H || x >= a.W) continue;
-            const long long vox = ((long long)z * a.H + y) * a.W + x;
-            float v[kC];
+            for (int cc = 0; cc < 4; ++cc)
+              if (c0 + 2 * cc < pl.NCH)
+                tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) +
+                            (uint32_t)((c0 + 2 * cc) * 64) + sd * 16u,
+                        r + 16 * cc);
+            tc_wait_ld();
 #pragma unroll
-            for (int o = 0; o < kC; ++o) {
-              v[o] = __uint_as_float(r[cc * 16 + o]) + bias[o];
-              if (a.relu) v[o] = fmaxf(v[o], 0.f);
-            }
-            if (a.mask) {
-              const uint4* mp = reinterpret_cast<const uint4*>(a.mask + vox * kC);
-              const uint4 m0 = mp[0], m1 = mp[1];
-              const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+            for (int cc = 0; cc < 4; ++cc) {
+              const int f = (c0 + 2 * cc) * 128 + row;
+              const int ry = f / pl.P, xx = f % pl.P;
+              const int y = y0 + ry, x = xs + xx;
+              if (c0 + 2 * cc >= pl.NCH || ry >= pl.RY || xx >= pl.SW || y >= a.H || x >= a.W)
+                continue;
+              const long long vox = ((long long)z * a.H + y) * a.W + x;
+              float v[kC];
 #pragma unroll
               for (int o = 0; o < kC; ++o) {
-                const uint16_t mb = (uint16_t)(mw[o >> 1] >> (16 * (o & 1)));
-                if (!(bf2f(mb) > 0.f)) v[o] = 0.f;
+                v[o] = __uint_as_float(r[cc * 16 + o]) + bias[o];
+                if (a.relu) v[o] = fmaxf(v[o], 0.f);
               }
-            }
-            if (a.y32) {
-              float4* yp = reinterpret_cast<float4*>(a.y32 + vox * kC);
+              if (a.mask) {
+                const uint4* mp = reinterpret_cast<const uint4*>(a.mask + vox * kC);
+                const uint4 m0 = mp[0], m1 = mp[1];
+                const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
-              for (int k = 0; k < 4; ++k)
-                yp[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-            }
-            if (a.y16) {
-              uint32_t pk[8];
+                for (int o = 0; o < kC; ++o) {
+                  const uint16_t mb = (uint16_t)(mw[o >> 1] >> (16 * (o & 1)));
+                  if (!(bf2f(mb) > 0.f)) v[o] = 0.f;
+                }
+              }
+              if (a.y32) {
+                float4* yp = reinterpret_cast<float4*>(a.y32 + vox * kC);
 #pragma unroll
-              for (int k = 0; k < 8; ++k)
-                pk[k] = (uint32_t)f2bf(v[2 * k]) | ((uint32_t)f2bf(v[2 * k + 1]) << 16);
-              uint4* yp = reinterpret_cast<uint4*>(a.y16 + vox * kC);
-              yp[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-              yp[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                for (int q = 0; q < 4; ++q)
+                  yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+              }
+              if (a.y16) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                  pk[q] = (uint32_t)f2bf(v[2 * q]) | ((uint32_t)f2bf(v[2 * q + 1]) << 16);
+                uint4* yp = reinterpret_cast<uint4*>(a.y16 + vox * kC);
+                yp[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                yp[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+              }
             }
           }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if (lane == 0) mbar_arrive(&tempty[sd]);
       }
-      if (!ok) break;
     }
   }
   tc_fence_before();

@@ -7,25 +7,26 @@
 // eighth-order stencils D2_a (weights c0..c4) and D1_a (4/5, -1/5, 4/105,
 // -1/280) and the memory variables scaled by h and h^2 (so that the update
 // uses A = c^2 dt^2 / h^2 like the damping kernels):
-//   psi_a'  = b_a psi_a  + c_a D1_a u
-//   zeta_a' = b_a zeta_a + c_a (D2_a u + D1_a psi_a')
-//   x       = sum_a (D2_a u + D1_a psi_a' + zeta_a')
-//   u'      = (2 - M) u - v + A x + source,        M = A m2 h^2
+//   Psi_a'  = b_a Psi_a  + c_a D1_a u
+//   Zeta_a' = b_a Zeta_a + c_a (D2_a u + D1_a Psi_a')
+//   u'      = (2 - M) u - v + A (lap u + sum_a (D1_a Psi_a' + Zeta_a')) + source
 // with b_a = exp(-(d_a + alpha_a) dt), c_a = d_a (b_a - 1) / (d_a + alpha_a)
-// (profiles built on the host).  No sponge factor applies.  The gradient is
-// the exact transpose of this recursion in the Lagrange multiplier lam of
-// u', run backwards over stored imaging terms t = x - (M / A) u:
-//   acc += lam t;  xb = A lam
-//   per axis: y_a = c_a (zetab_a + xb),  zetab_a <- b_a (zetab_a + xb)
-//             p_a = psib_a - D1_a (xb + y_a), psib_a <- b_a p_a,  z_a = c_a p_a
-//   lam_new = (2 - M) lam + mu + sum_a (D2_a (xb + y_a) - D1_a z_a),  mu_new = -lam
-// (D2 is symmetric, D1 antisymmetric, the field is zero outside the padded
-// grid).  Outside the layer along an axis the memory variables and their
-// multipliers stay zero.
+// (profiles built on the host; b = 1, c = 0 outside the layer).  The main
+// step kernel forms (2 - M) u - v + A lap u + source everywhere (damping
+// factor 1); the kernels here add the memory-variable part on the shell
+// where it is non-zero, and the same amount A sum_a (...) to the stored
+// imaging term A lap u - M u.
 //
-// These kernels read neighbours straight from global memory (one point per
-// thread, L1/L2 serve the reuse); the memory-variable terms are evaluated
-// only within 4 cells of the layer along their axis.
+// The gradient is the exact transpose of this recursion.  In the adjoint
+// level psi (the multiplier of u scaled by A, which the main kernel
+// propagates with the forward operator itself), one reverse step is
+//   per axis, in the layer:  y_a = c_a (Zb_a + psi),  Zb_a <- b_a (Zb_a + psi)
+//                            p_a = Pb_a - D1_a (psi + y_a),  Pb_a <- b_a p_a,  z_a = c_a p_a
+//   main adjoint step:       psi' = (2 - M) psi - psi_prev + A lap psi + injection
+//   shell correction:        psi' += A sum_a (D2_a y_a - D1_a z_a)
+// (Zb, Pb the multipliers of Zeta and Psi; D2 is symmetric, D1 antisymmetric,
+// the fields are zero outside the padded window), and the imaging
+// accumulator takes the corrected psi' against the stored term.
 #include "cpml.h"
 
 #include <algorithm>
@@ -85,74 +86,104 @@ __device__ __forceinline__ void prof(const CpmlProf& c, const VolDesc& V, Pt p, 
 
 __device__ __forceinline__ bool in_layer(float b, float cc) { return cc != 0.0f || b != 1.0f; }
 
-// Within 4 cells of the layer along axis a: elsewhere D1_a and D2_a of a
-// field that is zero outside the layer vanish, and are skipped.
-__device__ __forceinline__ bool near_layer(const VolDesc& V, Pt p, int a) {
+// Within w cells of a face of the window along axis a.
+__device__ __forceinline__ bool near_face(const VolDesc& V, Pt p, int a, int w) {
   const int q = a == 0 ? p.x : (a == 1 ? p.y : p.z);
   const int N = a == 0 ? V.Nx : (a == 1 ? V.Ny : V.Nz);
-  return q < V.border + 4 || q >= N - V.border - 4;
+  return q < w || q >= N - w;
 }
 
+// Calls f(p) for every point of the shell of width w of window V, one point
+// per thread of the blockIdx.x range: the z slabs (all y, x), then the y
+// slabs of the middle planes, then the x slabs of the middle rows.
 template <typename F>
-__device__ __forceinline__ void for_points(const VolDesc& V, F f) {
-  const long long n = (long long)V.Nx * V.Ny * V.Nz;
+__device__ __forceinline__ void for_shell(const VolDesc& V, int w, F f) {
+  const int lz = min(w, V.Nz), hz = max(V.Nz - w, lz);
+  const int ly = min(w, V.Ny), hy = max(V.Ny - w, ly);
+  const int lx = min(w, V.Nx), hx = max(V.Nx - w, lx);
+  const long long nxy = (long long)V.Nx * V.Ny;
+  const long long n1 = (long long)(lz + V.Nz - hz) * nxy;
+  const int ny2 = ly + V.Ny - hy, midz = hz - lz, midy = hy - ly, nx3 = lx + V.Nx - hx;
+  const long long n2 = (long long)midz * ny2 * V.Nx;
+  const long long n3 = (long long)midz * midy * nx3;
+  const long long n = n1 + n2 + n3;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     Pt p;
-    p.x = (int)(q % V.Nx);
-    p.y = (int)((q / V.Nx) % V.Ny);
-    p.z = (int)(q / ((long long)V.Nx * V.Ny));
+    if (q < n1) {
+      p.x = (int)(q % V.Nx);
+      const long long r = q / V.Nx;
+      p.y = (int)(r % V.Ny);
+      const int zz = (int)(r / V.Ny);
+      p.z = zz < lz ? zz : hz + (zz - lz);
+    } else if (q < n1 + n2) {
+      const long long q2 = q - n1;
+      p.x = (int)(q2 % V.Nx);
+      const long long r = q2 / V.Nx;
+      const int yy = (int)(r % ny2);
+      p.y = yy < ly ? yy : hy + (yy - ly);
+      p.z = lz + (int)(r / ny2);
+    } else {
+      const long long q3 = q - n1 - n2;
+      const int xx = (int)(q3 % nx3);
+      p.x = xx < lx ? xx : hx + (xx - lx);
+      const long long r = q3 / nx3;
+      p.y = ly + (int)(r % midy);
+      p.z = lz + (int)(r / midy);
+    }
     f(p);
   }
 }
 
+// Index of p in the imaging-region layout, or -1 outside the region.
+__device__ __forceinline__ long long region_index(const VolDesc& V, Pt p) {
+  const int zi = p.z - V.border, yi = p.y - V.iy0, xi = p.x - V.ix0;
+  if (xi < 0 || xi >= V.nxi || yi < 0 || yi >= V.nyi || zi < 0 || zi >= V.nzi) return -1;
+  return V.toff + ((long long)zi * V.nyi + yi) * V.tpitch + (p.x - V.txoff);
+}
+
+__device__ __forceinline__ float coefA(const CpmlArgs& c, const VolDesc& V, Pt p) {
+  return c.A[((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0)];
+}
+
+// ---------------------------------------------------------------- forward
+
 __global__ void psi_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_points(V, [&](Pt p) {
+  for_shell(V, V.border, [&](Pt p) {
+    const long long i = idx(V, p.x, p.y, p.z);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       float b, cc;
       prof(c.pr, V, p, a, b, cc);
-      if (!in_layer(b, cc)) continue;
-      const long long i = idx(V, p.x, p.y, p.z);
-      c.psi[a][i] = fmaf(b, c.psi[a][i], cc * d1(c.u, V, p, a));
+      if (in_layer(b, cc)) c.m1[a][i] = fmaf(b, c.m1[a][i], cc * d1(c.u, V, p, a));
     }
   });
 }
 
-__global__ void step_kernel_pml(CpmlArgs c) {
+__global__ void fcorr_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_points(V, [&](Pt p) {
+  for_shell(V, V.border + 4, [&](Pt p) {
     const long long i = idx(V, p.x, p.y, p.z);
-    float x = 0.0f;
+    float corr = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float d2u = d2(c.u, V, p, a);
-      const float d1p = near_layer(V, p, a) ? d1(c.psi[a], V, p, a) : 0.0f;
+      if (!near_face(V, p, a, V.border + 4)) continue;
+      const float d1p = d1(c.m1[a], V, p, a);
       float b, cc;
       prof(c.pr, V, p, a, b, cc);
       float zt = 0.0f;
       if (in_layer(b, cc)) {
-        zt = fmaf(b, c.zeta[a][i], cc * (d2u + d1p));
-        c.zeta[a][i] = zt;
+        zt = fmaf(b, c.m2[a][i], cc * (d2(c.u, V, p, a) + d1p));
+        c.m2[a][i] = zt;
       }
-      x += d2u + d1p + zt;
+      corr += d1p + zt;
     }
-    const long long g = ((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0);
-    const float A = c.A[g];
-    const float M = c.M ? c.M[g] : 0.0f;
-    const float u = c.u[i];
-    float out = fmaf(A, x, fmaf(2.0f, u, -c.v[i]) - M * u);
-    // source: w_e dt^2 w[n] / (h^3 sqrt rho_e) at the corners of its cell
-    const int dx = p.x - V.src_x, dy = p.y - V.src_y, dz = p.z - V.src_z;
-    if ((unsigned)dx < 2u && (unsigned)dy < 2u && (unsigned)dz < 2u)
-      out = fmaf(c.vols[blockIdx.y].src_sc[dx + 2 * dy + 4 * dz], c.wn, out);
-    c.v[i] = out;
-    if (c.tstore) {  // imaging term x - m2 u (in units of the scaled A) on the interior
-      const int bb = V.border, zi = p.z - bb, yi = p.y - bb, xi = p.x - bb;
-      if (xi >= 0 && xi < V.nxi && yi >= 0 && yi < V.nyi && zi >= 0 && zi < V.nzi)
-        c.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.tpitch + (p.x - V.txoff)] =
-            x - (M / A) * u;
+    const float d = coefA(c, V, p) * corr;
+    c.out[i] += d;
+    if (c.tstore) {
+      const long long r = region_index(V, p);
+      if (r >= 0) c.tstore[r] += d;
     }
   });
 }
@@ -163,102 +194,93 @@ __global__ void record_kernel(const float* __restrict__ u, const long long* __re
   if (c < ncol) dout[c] = rec[c].fscale * u[node[c]];
 }
 
-// lam[node] += sum over the node's receiver entries of fscale * res[rec][n].
-__global__ void inject_kernel(float* __restrict__ lam, const long long* __restrict__ unode,
-                              const int* __restrict__ uptr, const int* __restrict__ ucol,
-                              const RecEntry* __restrict__ rec, const int* __restrict__ colmap,
-                              const float* __restrict__ res, int nt, int n, int n_nodes) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_nodes) return;
-  float s = 0.0f;
-  for (int e = uptr[k]; e < uptr[k + 1]; ++e) {
-    const int c = ucol[e];
-    s = fmaf(rec[c].fscale, res[(long long)colmap[c] * nt + n], s);
-  }
-  lam[unode[k]] += s;
-}
+// ---------------------------------------------------------------- reverse
 
-__global__ void adj1_kernel(CpmlAdjArgs c) {
+__global__ void y_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_points(V, [&](Pt p) {
+  for_shell(V, V.border, [&](Pt p) {
     const long long i = idx(V, p.x, p.y, p.z);
-    const float l = c.lam[i];
-    const int bb = V.border, zi = p.z - bb, yi = p.y - bb, xi = p.x - bb;
-    if (xi >= 0 && xi < V.nxi && yi >= 0 && yi < V.nyi && zi >= 0 && zi < V.nzi)
-      c.acc[i] = fmaf(l, c.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.tpitch + (p.x - V.txoff)],
-                      c.acc[i]);
-    const long long g = ((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0);
-    const float xb = c.A[g] * l;
-    c.xb[i] = xb;
+    const float psi = c.u[i];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       float b, cc;
       prof(c.pr, V, p, a, b, cc);
       if (in_layer(b, cc)) {
-        const float zt = c.zetab[a][i] + xb;
+        const float zt = c.m2[a][i] + psi;
         c.y[a][i] = cc * zt;
-        c.zetab[a][i] = b * zt;
-      } else {
-        c.y[a][i] = 0.0f;
+        c.m2[a][i] = b * zt;
       }
     }
   });
 }
 
-__global__ void adj2_kernel(CpmlAdjArgs c) {
+__global__ void z_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_points(V, [&](Pt p) {
+  for_shell(V, V.border, [&](Pt p) {
     const long long i = idx(V, p.x, p.y, p.z);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       float b, cc;
       prof(c.pr, V, p, a, b, cc);
       if (in_layer(b, cc)) {
-        const float pt = c.psib[a][i] - (d1(c.xb, V, p, a) + d1(c.y[a], V, p, a));
-        c.psib[a][i] = b * pt;
+        const float pt = c.m1[a][i] - (d1(c.u, V, p, a) + d1(c.y[a], V, p, a));
+        c.m1[a][i] = b * pt;
         c.z[a][i] = cc * pt;
-      } else {
-        c.z[a][i] = 0.0f;
       }
     }
   });
 }
 
-__global__ void adj3_kernel(CpmlAdjArgs c) {
+__global__ void acorr_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_points(V, [&](Pt p) {
+  for_shell(V, V.border + 4, [&](Pt p) {
     const long long i = idx(V, p.x, p.y, p.z);
-    const long long g = ((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0);
-    const float l = c.lam[i];
-    const float M = c.M ? c.M[g] : 0.0f;
-    float s = fmaf(2.0f, l, -M * l) + c.mu[i];
+    float corr = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (near_layer(V, p, a))
-        s += (d2(c.xb, V, p, a) + d2(c.y[a], V, p, a)) - d1(c.z[a], V, p, a);
-      else
-        s += d2(c.xb, V, p, a);
-    }
-    c.mu[i] = s;     // becomes lam of the previous step (the host swaps the roles)
-    c.lam[i] = -l;   // becomes mu
+    for (int a = 0; a < 3; ++a)
+      if (near_face(V, p, a, V.border + 4)) corr += d2(c.y[a], V, p, a) - d1(c.z[a], V, p, a);
+    const float d = coefA(c, V, p) * corr;
+    c.out[i] += d;
+    const long long r = region_index(V, p);
+    if (r >= 0) c.acc[i] = fmaf(d, c.tstore[r], c.acc[i]);
   });
 }
 
 dim3 grid_for(int n_vol, long long max_pts) {
   long long b = (max_pts + 255) / 256;
-  const long long cap = std::max(1LL, 152LL * 8 / n_vol);
+  const long long cap = std::max(1LL, 152LL * 16 / n_vol);
   if (b > cap) b = cap;
   return dim3((unsigned)(b < 1 ? 1 : b), (unsigned)n_vol);
 }
 
 }  // namespace
 
-cudaError_t launch_cpml_forward(const CpmlArgs& c, int n_vol, long long max_pts, cudaStream_t s) {
-  const dim3 g = grid_for(n_vol, max_pts);
-  psi_kernel<<<g, 256, 0, s>>>(c);
+long long cpml_shell_points(int Nx, int Ny, int Nz, int w) {
+  auto inner = [&](int N) { return (long long)std::max(0, N - 2 * w); };
+  return (long long)Nx * Ny * Nz - inner(Nx) * inner(Ny) * inner(Nz);
+}
+
+cudaError_t launch_cpml_psi(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s) {
+  psi_kernel<<<grid_for(n_vol, max_layer), 256, 0, s>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cpml_fcorr(const CpmlArgs& c, int n_vol, long long max_shell, cudaStream_t s) {
+  fcorr_kernel<<<grid_for(n_vol, max_shell), 256, 0, s>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cpml_pre(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s) {
+  const dim3 g = grid_for(n_vol, max_layer);
+  y_kernel<<<g, 256, 0, s>>>(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  step_kernel_pml<<<g, 256, 0, s>>>(c);
+  z_kernel<<<g, 256, 0, s>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cpml_acorr(const CpmlArgs& c, int n_vol, long long max_shell, cudaStream_t s) {
+  acorr_kernel<<<grid_for(n_vol, max_shell), 256, 0, s>>>(c);
   return cudaGetLastError();
 }
 
@@ -266,27 +288,6 @@ cudaError_t launch_cpml_record(const float* u, const long long* node, const RecE
                                float* dout, cudaStream_t s) {
   if (ncol <= 0) return cudaSuccess;
   record_kernel<<<(ncol + 127) / 128, 128, 0, s>>>(u, node, rec, ncol, dout);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cpml_inject(float* lam, const long long* unode, const int* uptr,
-                               const int* ucol, const RecEntry* rec, const int* colmap,
-                               const float* res, int nt, int n, int n_nodes, cudaStream_t s) {
-  if (n_nodes <= 0) return cudaSuccess;
-  inject_kernel<<<(n_nodes + 127) / 128, 128, 0, s>>>(lam, unode, uptr, ucol, rec, colmap, res, nt,
-                                                      n, n_nodes);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cpml_adjoint(const CpmlAdjArgs& c, int n_vol, long long max_pts, cudaStream_t s) {
-  const dim3 g = grid_for(n_vol, max_pts);
-  adj1_kernel<<<g, 256, 0, s>>>(c);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  adj2_kernel<<<g, 256, 0, s>>>(c);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  adj3_kernel<<<g, 256, 0, s>>>(c);
   return cudaGetLastError();
 }
 

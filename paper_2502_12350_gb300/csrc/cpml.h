@@ -1,4 +1,11 @@
 // Launch interface of the convolutional-PML kernels (internal to libmamute).
+//
+// The CPML scheme is run as the damping-free main step (the TMA stencil
+// kernels with g = 1, which form the whole update away from the layer) plus
+// these kernels, which touch only the shell of each shot window where the
+// memory variables live or are read: the `border` layer cells of each face,
+// and 4 more cells inward where the eighth-order derivatives of the memory
+// variables reach.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,48 +25,40 @@ struct CpmlProf {
   const float* cz;
 };
 
-// One forward step of one shot window (pools in the VolDesc layout).
+// Fields of one CPML launch, all in the pool layout of the shot windows
+// (blockIdx.y selects the window) except A (global padded grid) and the
+// term store / accumulator (imaging-region layout).
 struct CpmlArgs {
-  const VolDesc* vols; // one shot window per blockIdx.y
+  const VolDesc* vols;
   CpmlProf pr;
   const float* A;      // c^2 dt^2 / h^2 on the global padded grid
-  const float* M;      // A m2 h^2 or null
-  int pitchG, NyG;     // layout of A and M
-  const float* u;      // u^n
-  float* v;            // u^{n-1}, receives u^{n+1}
-  float* psi[3];       // memory variables (scaled by h), per axis x, y, z
-  float* zeta[3];      // (scaled by h^2)
-  float wn;            // wavelet sample of the step
-  float* tstore;       // imaging term x - m2 u of the step on the interior, or null
+  int pitchG, NyG;     // layout of A
+  const float* u;      // forward: u^n; reverse: the adjoint level being propagated (psi^{k+1})
+  float* out;          // the main kernel's new level, corrected in place
+  float* m1[3];        // forward: Psi_a (first memory variable, scaled by h); reverse: its multiplier
+  float* m2[3];        // forward: Zeta_a (scaled by h^2); reverse: its multiplier
+  float* y[3];         // reverse scratch: c_a (multiplier of Zeta_a + psi)
+  float* z[3];         // reverse scratch: c_a p_a
+  float* tstore;       // imaging term of this step (corrected in place, forward) or read (reverse); may be null
+  float* acc;          // reverse: imaging accumulator (pool layout, corrected in place)
 };
 
-// One reverse step of one shot window.
-struct CpmlAdjArgs {
-  const VolDesc* vols; // one shot window per blockIdx.y
-  CpmlProf pr;
-  const float* A;
-  const float* M;
-  int pitchG, NyG;
-  float* lam;          // multiplier of u^{n+1}; receives -lam (the next mu)
-  float* mu;           // multiplier of u^n through the previous-level slot; receives the next lam
-  float* xb;           // scratch: A lam
-  float* y[3];         // scratch: c_a (zetab_a + xb)
-  float* z[3];         // scratch: c_a p_a
-  float* psib[3];      // multipliers of the memory variables
-  float* zetab[3];
-  float* acc;          // sum over steps of lam (x - m2 u), padded layout
-  const float* tstore; // imaging term of the step
-};
-
-// psi update, then the step, of every window (max_pts: points of the largest).
-cudaError_t launch_cpml_forward(const CpmlArgs& c, int n_vol, long long max_pts, cudaStream_t s);
+// Forward, before the main step: Psi_a <- b_a Psi_a + c_a D1_a u^n in the layer.
+cudaError_t launch_cpml_psi(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s);
+// Forward, after the main step: Zeta_a <- b_a Zeta_a + c_a (D2_a u^n + D1_a Psi_a) in the layer,
+// u^{n+1} += A sum_a (D1_a Psi_a + Zeta_a) and the stored term likewise.
+cudaError_t launch_cpml_fcorr(const CpmlArgs& c, int n_vol, long long max_shell, cudaStream_t s);
+// Reverse, before the main adjoint step: y_a, the Zeta multipliers, then p_a,
+// the Psi multipliers and z_a, from the level psi^{k+1} (two launches).
+cudaError_t launch_cpml_pre(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s);
+// Reverse, after the main adjoint step: psi^k += A sum_a (D2_a y_a - D1_a z_a)
+// and the imaging accumulator likewise.
+cudaError_t launch_cpml_acorr(const CpmlArgs& c, int n_vol, long long max_shell, cudaStream_t s);
 // dout[c] = rec[c].fscale * u[node[c]] for the ncol internal data columns.
 cudaError_t launch_cpml_record(const float* u, const long long* node, const RecEntry* rec, int ncol,
                                float* dout, cudaStream_t s);
-// lam[unode[k]] += sum_{e in [uptr[k], uptr[k+1])} rec[c].fscale res[colmap[c]][n], c = ucol[e].
-cudaError_t launch_cpml_inject(float* lam, const long long* unode, const int* uptr,
-                               const int* ucol, const RecEntry* rec, const int* colmap,
-                               const float* res, int nt, int n, int n_nodes, cudaStream_t s);
-cudaError_t launch_cpml_adjoint(const CpmlAdjArgs& c, int n_vol, long long max_pts, cudaStream_t s);
+
+// Points of the shell of width w (per face) of an Nx x Ny x Nz window.
+long long cpml_shell_points(int Nx, int Ny, int Nz, int w);
 
 }  // namespace mamute

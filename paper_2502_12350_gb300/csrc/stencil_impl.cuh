@@ -261,7 +261,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
           if (DENS) tma_load_3d(cd + CI_M * CS, mapM, cx, cy, q, &fullC[c]);
           if (ACC) tma_load_3d(cd + CI_ACC * CS, mapAcc, x0, y0, q, &fullC[c]);
           if (TERM)
-            tma_load_4d(cd + CI_T * CS, mapT, x0 - V.txoff, y0 - V.border, q - V.border, a.tstep,
+            tma_load_4d(cd + CI_T * CS, mapT, x0 - V.txoff, y0 - V.iy0, q - V.border, a.tstep,
                         &fullC[c]);
           ++nC;
         }
@@ -391,11 +391,11 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
     }
     // Interior store of the new adjoint level.
     if (MODE == MODE_ADJ_TERM) {
-      const int b = V.border, zi = z - b, yi = gyl - b;
+      const int zi = z - V.border, yi = gyl - V.iy0;
       if (row_ok && col_ok && yi >= 0 && yi < V.nyi && zi >= 0 && zi < V.nzi) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int xi = gxl + e - b;
+          const int xi = gxl + e - V.ix0;
           if (xi >= 0 && xi < V.nxi)
             a.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.tpitch + (gxl + e - V.txoff)] =
                 out.v[e];
@@ -418,11 +418,11 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
         for (int e = 0; e < 4; ++e) t.v[e] = img_term(q[4].v[e], Av.v[e], Mv.v[e], lap[e], DENS);
       }
       if (MODE == MODE_FWD_STORE || MODE == MODE_FWD_STORE_PH) {
-        const int b = V.border, zi = z - b, yi = gyl - b;
+        const int zi = z - V.border, yi = gyl - V.iy0;
         if (row_ok && col_ok && yi >= 0 && yi < V.nyi && zi >= 0 && zi < V.nzi) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int xi = gxl + e - b;
+            const int xi = gxl + e - V.ix0;
             if (xi >= 0 && xi < V.nxi)
               a.tstore[V.toff + ((long long)zi * V.nyi + yi) * V.tpitch + (gxl + e - V.txoff)] =
                   t.v[e];
@@ -442,6 +442,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (MinBlocks<TX, TY, MODE>::
             nacc.v[e] = __fmaf_rn(gt, gt, acc.v[e]);
           }
         }
+        // (whole window; the gradient and pseudo-Hessian read its imaging region)
         if (row_ok && col_ok) {
           float* ap = a.acc + V.off + ((long long)z * V.Ny + gyl) * V.pitch + gxl;
 #pragma unroll

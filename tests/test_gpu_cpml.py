@@ -114,7 +114,9 @@ def test_gradient_matches_oracle(ctx, oracle, density, xi):
         w = _offgrid(w, 34)
     og = ogrid(oracle, w, xi)
     rng = np.random.default_rng(35)
-    vtrue = w.vel * (1 + 0.05 * rng.standard_normal(w.vel.shape))
+    # a 10 % perturbation keeps the residual well above the FP32 rounding of
+    # the traces, so that J is compared at 1e-4
+    vtrue = w.vel * (1 + 0.1 * rng.standard_normal(w.vel.shape))
     dobs = cpml.model(oracle, og, vtrue, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
                       f0=w.fpeak, rho=w.rho).astype(np.float32)
     Jr, gr = cpml.gradient(oracle, og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs,
