@@ -40,8 +40,8 @@ KERNEL_SOURCES = ["paper_2502_12350_gb300/csrc/stencil_impl.cuh",
                   "paper_2502_12350_gb300/csrc/stencil_fwd.cu",
                   "paper_2502_12350_gb300/csrc/stencil_pair.cu",
                   "paper_2502_12350_gb300/csrc/common.cuh"]
-PML_SOURCES = ["paper_2502_12350_gb300/csrc/cpml.cu", "paper_2502_12350_gb300/csrc/cpml.h",
-               "paper_2502_12350_gb300/csrc/common.cuh"]
+PML_SOURCES = KERNEL_SOURCES + ["paper_2502_12350_gb300/csrc/cpml.cu",
+                                "paper_2502_12350_gb300/csrc/cpml.h"]
 
 
 def kernel_source_hash(sources=KERNEL_SOURCES) -> str:

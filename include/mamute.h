@@ -266,8 +266,8 @@ int mamute_gn_diagonal(mamute_ctx* ctx, const mamute_grid* grid, const float* ve
 /* y = act(conv(x, w) + bias) with zero padding; act = ReLU if relu != 0;
  * if mask is given, outputs where mask <= 0 are zeroed (ReLU derivative of
  * the layer input in the input-gradient pass).  w is a packed weight set
- * (mamute_conv3d_pack): the forward set computes the layer, the backward set
- * the gradient with respect to the layer input.  y32 [D][H][W][16] FP32
+ * (mamute_conv3d_pack; 16-byte aligned): the forward set computes the layer,
+ * the backward set the gradient with respect to the layer input.  y32 [D][H][W][16] FP32
  * and/or y16 [D][H][W][16] BF16 receive the result (either may be NULL). */
 int mamute_conv3d(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
                   const unsigned short* w, const float* bias, int relu,

@@ -2238,16 +2238,26 @@ int mamute_conv3d(mamute_ctx* ctx, int D, int H, int W, const unsigned short* x,
   TRY(nn_begin(ctx));
   if (D < 1 || H < 1 || W < 1 || !x || !w || (!y32 && !y16))
     return fail(ctx, MAMUTE_EINVAL, "conv3d: bad arguments");
-  if ((uintptr_t)x % 16)
-    return fail(ctx, MAMUTE_EINVAL, "conv3d: x must be 16-byte aligned");
+  if ((uintptr_t)x % 16 || (uintptr_t)w % 16)
+    return fail(ctx, MAMUTE_EINVAL, "conv3d: x and w must be 16-byte aligned");
   ConvArgs a{x, w, bias, relu, mask, y32, y16, D, H, W};
   if ((uintptr_t)mask % 16 || (uintptr_t)y32 % 16 || (uintptr_t)y16 % 16)
     return fail(ctx, MAMUTE_EINVAL, "conv3d: mask and outputs must be 16-byte aligned");
+  // halo rows as long boxes of 8-byte elements, no swizzle (the kernel
+  // applies the operand swizzle in shared memory)
   CUtensorMap xmap;
   unsigned box[4];
   conv_halo_box(D, H, W, box);
-  if (encode_act(ctx, &xmap, x, D, H, W, box))
-    return fail(ctx, MAMUTE_ECUDA, "conv3d: cuTensorMapEncodeTiled failed");
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)W * 4, (cuuint64_t)H, (cuuint64_t)D};
+    cuuint64_t strides[2] = {(cuuint64_t)W * 32, (cuuint64_t)W * H * 32};
+    cuuint32_t cbox[3] = {box[0], box[1], box[2]};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (ctx->encode(&xmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<unsigned short*>(x), dims,
+                    strides, cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE))
+      return fail(ctx, MAMUTE_ECUDA, "conv3d: cuTensorMapEncodeTiled failed");
+  }
   CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
   CK(launch_conv(a, xmap, ctx->status, ctx->stream));
   return nn_end_status(ctx);

@@ -359,9 +359,11 @@ constexpr int kTcSlotBudget = kTcSmemMax - kTcWBytes - 1024;
 
 static TcPlan tc_plan(int D, int H, int W) {
   TcPlan p{};
-  p.SW = std::min(W, kTcMaxP - 2);
+  // x segments of at most kTcMaxP - 2 voxels, as even as possible: a halo
+  // row of P voxels is one TMA box row of 4 P 8-byte elements (<= 256)
+  p.nxs = (W + kTcMaxP - 3) / (kTcMaxP - 2);
+  p.SW = (W + p.nxs - 1) / p.nxs;
   p.P = p.SW + 2;
-  p.nxs = (W + p.SW - 1) / p.SW;
   auto shape = [&](int ry) {
     p.RY = ry;
     p.NCH = (p.RY * p.P + 127) / 128;
@@ -404,9 +406,9 @@ static size_t tc_smem_bytes(const TcPlan& p) {
 
 void conv_halo_box(int D, int H, int W, unsigned (&box)[4]) {
   const TcPlan p = tc_plan(D, H, W);
-  box[0] = 16;  // one voxel (32 bytes, the swizzle span)
-  box[1] = (unsigned)p.P;
-  box[2] = (unsigned)p.rows;
+  box[0] = 4u * (unsigned)p.P;  // one halo row: P voxels of 4 8-byte elements
+  box[1] = (unsigned)p.rows;
+  box[2] = 1;
   box[3] = 1;
 }
 

@@ -32,6 +32,8 @@ int mse_blocks();
 // volume: one halo plane of a row block, the activation viewed as
 // [D][H][W][16] BF16 (innermost first: 16 channels, x, y, z), 32-byte
 // swizzle, zero fill outside.
+// Box of the forward convolution's halo-plane loads over the activation
+// viewed as [D][H][4 W] 8-byte elements (no swizzle): {4 P, rows, 1, -}.
 void conv_halo_box(int D, int H, int W, unsigned (&box)[4]);
 cudaError_t launch_conv(const ConvArgs& a, const CUtensorMap& xmap, int* status, cudaStream_t s);
 // Boxes of the weight-gradient kernel's maps over x (halo) and gy (tile),

@@ -5,13 +5,15 @@
 //
 // Formulation.  A CTA owns a block of RY output rows (y) of an x segment of
 // SW voxels and marches over a chunk of z planes.  Each halo plane of the
-// block (rows y0-1 .., x from xs-1, width P = SW + 2) arrives by one TMA
-// load with the 32-byte swizzle: 32 bytes (16 channels) per voxel, the two
-// 16-byte channel halves of a voxel swapped when bit 7 of its shared-memory
-// address is set.  That is the K-major SWIZZLE_32B operand layout of
-// tcgen05 (one 32-byte row per M row, 8-row groups 256 bytes apart), with
-// the swizzle taken on absolute shared-memory addresses by both the copy
-// and the tensor core.  Output voxels are numbered f = ry * P + xx over the
+// block (rows y0-1 .., x from xs-1, width P = SW + 2 <= 64) arrives by one
+// TMA load of long rows (the activation viewed as 8-byte elements, one box
+// row per halo row, no swizzle): 32 bytes (16 channels) per voxel.  Two
+// warps then swap the two 16-byte channel halves of every voxel whose
+// shared-memory address has bit 7 set, in place, which gives the K-major
+// SWIZZLE_32B operand layout of tcgen05 (one 32-byte row per M row, 8-row
+// groups 256 bytes apart, the swizzle taken on absolute shared-memory
+// addresses).  (A TMA load with the 32-byte swizzle itself is limited to
+// 32-byte box rows, which move a few bytes per clock per SM.)  Output voxels are numbered f = ry * P + xx over the
 // block (xx in [0, P): the last two columns of every row are junk and never
 // stored), so the A rows of tap (dz, dy, dx) for the 128 outputs
 // f0 .. f0+127 are the 128 consecutive halo voxels starting at
@@ -33,19 +35,20 @@
 // channels per thread with tcgen05.ld and store 32 (bf16) or 64 (f32)
 // contiguous bytes.
 //
-// Warp roles (320 threads): warp 0 lane 0 issues the TMA loads of halo
+// Warp roles (384 threads): warp 0 lane 0 issues the TMA loads of halo
 // planes into a ring of slots; warp 1 allocates TMEM and lane 0 issues
 // the MMAs; warps 2-9 run the epilogue, two per TMEM lane quarter (warp w
-// reads lanes 32 (w mod 4) ..), each taking every other chunk.  Every wait
-// is bounded; a timeout sets the status flag and a CTA-wide abort flag that
-// ends every role's loop.
+// reads lanes 32 (w mod 4) ..), each taking every other chunk; warps 10-11
+// swizzle each loaded halo plane.  Every wait is bounded; a timeout sets
+// the status flag and a CTA-wide abort flag that ends every role's loop.
 
 constexpr int kTcMaxRing = 6;        // halo plane slots (at most)
 constexpr int kTcCols = 512;         // TMEM columns: 8 chunks x 4 plane slots x 16
 constexpr int kTcMaxChunks = 8;
-constexpr int kTcMaxP = 200;         // halo row width (x segment + 2)
+constexpr int kTcMaxP = 64;          // halo row width (x segment + 2): one TMA box row
 constexpr int kTcEpiWarps = 8;
-constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
+constexpr int kTcSwzWarps = 2;
+constexpr int kTcThreads = 32 * (2 + kTcEpiWarps + kTcSwzWarps);
 // B operand: per (dy, dx) tap, 7 blocks x 16 output channels (N rows) x 16
 // input channels (K), K-major core matrices: 8-row groups 128 bytes apart,
 // the two 8-channel K halves kTcWHalf bytes apart.
@@ -173,26 +176,49 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* sm = tc_raw + ((1024 - (smem_u32(tc_raw) & 1023)) & 1023);
   unsigned char* slots = sm;                               // ring x slot_bytes
   unsigned char* wts = sm + pl.ring * pl.slot_bytes;       // kTcWBytes, see kTcWBlocks
-  __shared__ uint64_t full[kTcMaxRing], empty[kTcMaxRing], tfull[4], tempty[4], done_bar;
+  __shared__ uint64_t full[kTcMaxRing], ready[kTcMaxRing], empty[kTcMaxRing], tfull[4], tempty[4],
+      done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   volatile int* ab = &abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // B blocks: block j of tap (dy, dx) holds w[dz][dy][dx][o][i] for the dz of
-  // the sequence [2, 1, 0, -, 2, 1, 0] (block 3 zero).
-  for (int e = threadIdx.x; e < 9 * kTcWBlocks * kC * kC; e += blockDim.x) {
-    const int t9 = e / (kTcWBlocks * kC * kC), j = (e / (kC * kC)) % kTcWBlocks;
-    const int o = (e / kC) % kC, i = e % kC;
-    const int dz = j == 3 ? -1 : 2 - (j % 4);
-    const uint16_t v = dz < 0 ? (uint16_t)0 : a.w[((dz * 9 + t9) * kC + o) * kC + i];
-    reinterpret_cast<uint16_t*>(wts)[(t9 * kTcWTap + (i >> 3) * kTcWHalf) / 2 + (j * 16 + o) * 8 +
-                                     (i & 7)] = v;
+  // the sequence [2, 1, 0, -, 2, 1, 0] (block 3 zero).  Each 16-byte piece
+  // (8 input channels of one output channel) goes to the two blocks of its
+  // dz; the global loads are issued together before the stores.
+  {
+    constexpr int kPieces = kTaps * kC * 2;  // 864 pieces of 8 bf16
+    constexpr int kPer = (kPieces + kTcThreads - 1) / kTcThreads;
+    const uint4* wg = reinterpret_cast<const uint4*>(a.w);
+    uint4 pc[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int e = threadIdx.x + k * kTcThreads;
+      if (e < kPieces) pc[k] = wg[e];
+    }
+    uint4* ws = reinterpret_cast<uint4*>(wts);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int e = threadIdx.x + k * kTcThreads;
+      if (e >= kPieces) continue;
+      const int tap = e / (kC * 2), o = (e / 2) % kC, ih = e % 2;
+      const int dz = tap / 9, t9 = tap % 9;
+      const int j0 = 2 - dz;  // blocks j0 and j0 + 4
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+        ws[(t9 * kTcWTap + ih * kTcWHalf) / 16 + (j0 + 4 * r) * 16 + o] = pc[k];
+    }
+    for (int e = threadIdx.x; e < 9 * 2 * 16; e += kTcThreads) {  // block 3: zeros
+      const int t9 = e / 32, ih = (e / 16) % 2, o = e % 16;
+      ws[(t9 * kTcWTap + ih * kTcWHalf) / 16 + 3 * 16 + o] = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   fence_async_smem();  // visible to the tensor cores (async proxy)
   if (threadIdx.x == 0) {
     for (int i = 0; i < kTcMaxRing; ++i) {
       mbar_init(&full[i], 1);
+      mbar_init(&ready[i], kTcSwzWarps);
       mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 4; ++i) {
@@ -232,7 +258,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (!tc_wait(&empty[s], ((q / pl.ring) & 1) ^ 1, status, ab)) break;
           unsigned char* dst = slots + (size_t)s * pl.slot_bytes;
           mbar_arrive_expect_tx(&full[s], tx);
-          tma_load_4d(dst, &xmap, 0, xs - 1, y0 - 1, z0 - 1 + h, &full[s]);
+          tma_load_3d(dst, &xmap, 4 * (xs - 1), y0 - 1, z0 - 1 + h, &full[s]);
         }
       }
       if (*ab)  // let issued loads land before the CTA exits
@@ -255,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         geom(it, xs, y0, z0, nz);
         for (int k = 0; k < nz + 2; ++k, ++t) {
           const uint32_t hs = t % (uint32_t)pl.ring;
-          if (!(ok = tc_wait(&full[hs], (t / pl.ring) & 1, status, ab))) break;
+          if (!(ok = tc_wait(&ready[hs], (t / pl.ring) & 1, status, ab))) break;
           const uint32_t sn = (t + 1) & 3;  // slot of plane h + 1
           if (t >= 2 && !(ok = tc_wait(&tempty[sn], ((t - 2) >> 2) & 1, status, ab))) break;
           tc_fence_after();
@@ -280,6 +306,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc_commit(&done_bar);  // every MMA issued above has completed
       mbar_wait(&done_bar, 0, status);
+    }
+  } else if (warp >= 2 + kTcEpiWarps) {
+    // ---- swizzle: swap the channel halves of the voxels at addresses with
+    // bit 7 set (voxels 4..7 of every 8 from the 1024-byte-aligned slot)
+    const int sid = threadIdx.x - 32 * (2 + kTcEpiWarps);
+    const int nvox = pl.rows * pl.P;
+    uint32_t q = 0;
+    bool ok = true;
+    for (long long it = blockIdx.x; it < pl.items && ok && !*ab; it += gridDim.x) {
+      int xs, y0, z0, nz;
+      geom(it, xs, y0, z0, nz);
+      for (int h = 0; h < nz + 2; ++h, ++q) {
+        const int s = (int)(q % pl.ring);
+        int got = 0;
+        if (lane == 0) got = tc_wait(&full[s], (q / pl.ring) & 1, status, ab) ? 1 : 0;
+        if (!(ok = __shfl_sync(0xffffffffu, got, 0) != 0)) break;
+        uint4* vox = reinterpret_cast<uint4*>(slots + (size_t)s * pl.slot_bytes);
+        for (int j = sid; j < (nvox + 1) / 2; j += 32 * kTcSwzWarps) {
+          const int v = (j >> 2) * 8 + 4 + (j & 3);
+          if (v < nvox) {
+            const uint4 lo = vox[2 * v], hi = vox[2 * v + 1];
+            vox[2 * v] = hi;
+            vox[2 * v + 1] = lo;
+          }
+        }
+        fence_async_smem();  // visible to the tensor cores (async proxy)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[s]);
+      }
     }
   } else {
     // ---- epilogue: one output voxel (16 channels) per thread and chunk
