@@ -8,6 +8,8 @@
 // forward product, with a flipped, transposed copy for the input gradient.
 #include "conv.h"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "common.cuh"

@@ -340,6 +340,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- epilogue: one output voxel (16 channels) per thread and chunk
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     const int row = quarter * 32 + lane;
+    // block row and column of this thread's voxel in each of its chunks
+    int rdiv[4], rmod[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int f = (half + 2 * cc) * 128 + row;
+      rdiv[cc] = f / pl.P;
+      rmod[cc] = f % pl.P;
+    }
     float bias[kC];
 #pragma unroll
     for (int o = 0; o < kC; ++o) bias[o] = a.bias ? a.bias[o] : 0.f;
@@ -371,8 +379,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc_wait_ld();
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
-              const int f = (c0 + 2 * cc) * 128 + row;
-              const int ry = f / pl.P, xx = f % pl.P;
+              const int ry = rdiv[cc], xx = rmod[cc];
               const int y = y0 + ry, x = xs + xx;
               if (c0 + 2 * cc >= pl.NCH || ry >= pl.RY || xx >= pl.SW || y >= a.H || x >= a.W)
                 continue;
@@ -399,11 +406,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int q = 0; q < 4; ++q)
                   yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
               }
-              if (a.y16) {
+              if (a.y16) {  // round to nearest even, two values per conversion
                 uint32_t pk[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                  pk[q] = (uint32_t)f2bf(v[2 * q]) | ((uint32_t)f2bf(v[2 * q + 1]) << 16);
+                for (int q = 0; q < 8; ++q) {
+                  const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                  pk[q] = *reinterpret_cast<const uint32_t*>(&b2);
+                }
                 uint4* yp = reinterpret_cast<uint4*>(a.y16 + vox * kC);
                 yp[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 yp[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
