@@ -1137,6 +1137,8 @@ int cpml_setup(mamute_ctx* ctx, const Plan& P, const float* vel, const float* rh
                PmlTables& T) {
   std::vector<float> bx, cx, by, cy, bz, cz;
   for (const VolDesc& V : P.vols) {
+    if ((long long)V.Nx * V.Ny * V.Nz >= (1LL << 32))  // 32-bit shell indexing
+      return fail(ctx, MAMUTE_EINVAL, "pml: a shot window of 2^32 points or more");
     cpml_profile(V.Nx, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bx, cx);
     cpml_profile(V.Ny, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, by, cy);
     T.max_layer = std::max(T.max_layer, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b));

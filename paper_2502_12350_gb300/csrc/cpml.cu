@@ -46,27 +46,42 @@ __device__ __forceinline__ long long idx(const VolDesc& V, int x, int y, int z) 
   return V.off + ((long long)z * V.Ny + y) * V.pitch + x;
 }
 
-// f at p + m along axis a (zero outside the window).
-__device__ __forceinline__ float nb(const float* f, const VolDesc& V, Pt p, int a, int m) {
-  int x = p.x, y = p.y, z = p.z;
-  if (a == 0) x += m;
-  else if (a == 1) y += m;
-  else z += m;
-  if (x < 0 || x >= V.Nx || y < 0 || y >= V.Ny || z < 0 || z >= V.Nz) return 0.0f;
-  return f[idx(V, x, y, z)];
+// Element stride of axis a in a window's arrays.
+__device__ __forceinline__ long long axis_stride(const VolDesc& V, int a) {
+  return a == 0 ? 1LL : (a == 1 ? (long long)V.pitch : (long long)V.Ny * V.pitch);
 }
 
-__device__ __forceinline__ float d2(const float* f, const VolDesc& V, Pt p, int a) {
-  float s = kC2[0] * f[idx(V, p.x, p.y, p.z)];
+// Neighbours p - 4 .. p + 4 along axis a of the point at element i (zero
+// outside the window; the bounds are tested only near the window's faces).
+__device__ __forceinline__ void column(const float* f, const VolDesc& V, Pt p, int a, long long i,
+                                       float (&v)[9]) {
+  const int q = a == 0 ? p.x : (a == 1 ? p.y : p.z);
+  const int N = a == 0 ? V.Nx : (a == 1 ? V.Ny : V.Nz);
+  const long long st = axis_stride(V, a);
+  if (q >= 4 && q + 4 < N) {
 #pragma unroll
-  for (int m = 1; m <= 4; ++m) s = fmaf(kC2[m], nb(f, V, p, a, m) + nb(f, V, p, a, -m), s);
+    for (int m = -4; m <= 4; ++m) v[m + 4] = f[i + m * st];
+  } else {
+#pragma unroll
+    for (int m = -4; m <= 4; ++m) v[m + 4] = (q + m >= 0 && q + m < N) ? f[i + m * st] : 0.0f;
+  }
+}
+
+__device__ __forceinline__ float d2(const float* f, const VolDesc& V, Pt p, int a, long long i) {
+  float v[9];
+  column(f, V, p, a, i, v);
+  float s = kC2[0] * v[4];
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) s = fmaf(kC2[m], v[4 + m] + v[4 - m], s);
   return s;
 }
 
-__device__ __forceinline__ float d1(const float* f, const VolDesc& V, Pt p, int a) {
+__device__ __forceinline__ float d1(const float* f, const VolDesc& V, Pt p, int a, long long i) {
+  float v[9];
+  column(f, V, p, a, i, v);
   float s = 0.0f;
 #pragma unroll
-  for (int m = 1; m <= 4; ++m) s = fmaf(kD1[m - 1], nb(f, V, p, a, m) - nb(f, V, p, a, -m), s);
+  for (int m = 1; m <= 4; ++m) s = fmaf(kD1[m - 1], v[4 + m] - v[4 - m], s);
   return s;
 }
 
@@ -107,29 +122,34 @@ __device__ __forceinline__ void for_shell(const VolDesc& V, int w, F f) {
   const long long n2 = (long long)midz * ny2 * V.Nx;
   const long long n3 = (long long)midz * midy * nx3;
   const long long n = n1 + n2 + n3;
+  // each region has fewer than 2^32 points (windows are checked on the
+  // host), so the index arithmetic runs in 32 bits
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     Pt p;
     if (q < n1) {
-      p.x = (int)(q % V.Nx);
-      const long long r = q / V.Nx;
-      p.y = (int)(r % V.Ny);
-      const int zz = (int)(r / V.Ny);
-      p.z = zz < lz ? zz : hz + (zz - lz);
+      const unsigned r0 = (unsigned)q;
+      const unsigned r = r0 / (unsigned)V.Nx;
+      p.x = (int)(r0 - r * (unsigned)V.Nx);
+      const unsigned zz = r / (unsigned)V.Ny;
+      p.y = (int)(r - zz * (unsigned)V.Ny);
+      p.z = (int)zz < lz ? (int)zz : hz + ((int)zz - lz);
     } else if (q < n1 + n2) {
-      const long long q2 = q - n1;
-      p.x = (int)(q2 % V.Nx);
-      const long long r = q2 / V.Nx;
-      const int yy = (int)(r % ny2);
+      const unsigned r0 = (unsigned)(q - n1);
+      const unsigned r = r0 / (unsigned)V.Nx;
+      p.x = (int)(r0 - r * (unsigned)V.Nx);
+      const unsigned zm = r / (unsigned)ny2;
+      const int yy = (int)(r - zm * (unsigned)ny2);
       p.y = yy < ly ? yy : hy + (yy - ly);
-      p.z = lz + (int)(r / ny2);
+      p.z = lz + (int)zm;
     } else {
-      const long long q3 = q - n1 - n2;
-      const int xx = (int)(q3 % nx3);
+      const unsigned r0 = (unsigned)(q - n1 - n2);
+      const unsigned r = r0 / (unsigned)nx3;
+      const int xx = (int)(r0 - r * (unsigned)nx3);
       p.x = xx < lx ? xx : hx + (xx - lx);
-      const long long r = q3 / nx3;
-      p.y = ly + (int)(r % midy);
-      p.z = lz + (int)(r / midy);
+      const unsigned zm = r / (unsigned)midy;
+      p.y = ly + (int)(r - zm * (unsigned)midy);
+      p.z = lz + (int)zm;
     }
     f(p);
   }
@@ -156,7 +176,7 @@ __global__ void psi_kernel(CpmlArgs c) {
     for (int a = 0; a < 3; ++a) {
       float b, cc;
       prof(c.pr, V, p, a, b, cc);
-      if (in_layer(b, cc)) c.m1[a][i] = fmaf(b, c.m1[a][i], cc * d1(c.u, V, p, a));
+      if (in_layer(b, cc)) c.m1[a][i] = fmaf(b, c.m1[a][i], cc * d1(c.u, V, p, a, i));
     }
   });
 }
@@ -169,12 +189,12 @@ __global__ void fcorr_kernel(CpmlArgs c) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (!near_face(V, p, a, V.border + 4)) continue;
-      const float d1p = d1(c.m1[a], V, p, a);
+      const float d1p = d1(c.m1[a], V, p, a, i);
       float b, cc;
       prof(c.pr, V, p, a, b, cc);
       float zt = 0.0f;
       if (in_layer(b, cc)) {
-        zt = fmaf(b, c.m2[a][i], cc * (d2(c.u, V, p, a) + d1p));
+        zt = fmaf(b, c.m2[a][i], cc * (d2(c.u, V, p, a, i) + d1p));
         c.m2[a][i] = zt;
       }
       corr += d1p + zt;
@@ -223,7 +243,7 @@ __global__ void z_kernel(CpmlArgs c) {
       float b, cc;
       prof(c.pr, V, p, a, b, cc);
       if (in_layer(b, cc)) {
-        const float pt = c.m1[a][i] - (d1(c.u, V, p, a) + d1(c.y[a], V, p, a));
+        const float pt = c.m1[a][i] - (d1(c.u, V, p, a, i) + d1(c.y[a], V, p, a, i));
         c.m1[a][i] = b * pt;
         c.z[a][i] = cc * pt;
       }
@@ -238,7 +258,7 @@ __global__ void acorr_kernel(CpmlArgs c) {
     float corr = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (near_face(V, p, a, V.border + 4)) corr += d2(c.y[a], V, p, a) - d1(c.z[a], V, p, a);
+      if (near_face(V, p, a, V.border + 4)) corr += d2(c.y[a], V, p, a, i) - d1(c.z[a], V, p, a, i);
     const float d = coefA(c, V, p) * corr;
     c.out[i] += d;
     const long long r = region_index(V, p);
