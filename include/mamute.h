@@ -82,9 +82,11 @@ typedef struct mamute_ctx mamute_ctx;
  * d_a = -3 vmax ln(pml_r) r^2 / (2 border h) and alpha_a = pi pml_f0 (1 - r),
  * vmax = max(vel).  pml_f0 is the source's dominant frequency in Hz (>= 0)
  * and pml_r the nominal reflection coefficient in (0, 1) (0 selects 1e-3).
- * A pml gradient keeps the imaging term of every step (n_snapshots 0 or -1;
- * ENOMEM when that store does not fit) and takes no phess; pml with
- * free_surface, and mamute_gn_diagonal with pml, are EINVAL.  0: the sponge. */
+ * With free_surface the top face has no layer (the surface's image method
+ * holds there) and the other five faces have it.  A pml gradient keeps the
+ * imaging term of every step (n_snapshots 0 or -1; ENOMEM when that store
+ * does not fit) and takes no phess; mamute_gn_diagonal with pml is EINVAL.
+ * 0: the sponge. */
 typedef struct {
   int nx, ny, nz;
   int border;

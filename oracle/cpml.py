@@ -21,7 +21,10 @@ outside the padded grid.  The layer is the `border` cells on each face;
 at depth r = dist / border (dist = 1 .. border cells):
     d_a = d0 r^2,   d0 = -3 v_max ln(R) / (2 border h),   alpha_a = pi f0 (1 - r),
 R = 1e-3 the nominal reflection coefficient and f0 the source's peak
-frequency.  No sponge factor is applied (g = 1).  Density enters as in the
+frequency.  No sponge factor is applied (g = 1).  With a free surface
+(g.free_surface) the top face has no layer, D2_z reads the negated mirror
+planes above the surface (the main scheme's image method) and the field is
+held at zero on and above it.  Density enters as in the
 main scheme (A = c^2 dt^2, m2 = lap(sqrt rho) / sqrt rho, source / sqrt rho,
 receivers sqrt rho u); sources and receivers are at their nearest nodes, or
 (g.xyz_interp = 1) spread over the 8 nodes of their cell with trilinear
@@ -40,15 +43,19 @@ import scipy.sparse as sp
 D1W = np.array([4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0])
 
 
-def _d2(n, h, c):
+def _d2(n, h, c, zs=-1):
+    """Second difference; with a free surface at zs a neighbour j <= zs reads
+    the negated mirror plane 2 zs - j (the main scheme's image method)."""
     M = sp.lil_matrix((n, n))
     for i in range(n):
-        M[i, i] = c[0]
+        M[i, i] += c[0]
         for m in range(1, 5):
-            if i - m >= 0:
-                M[i, i - m] = c[m]
-            if i + m < n:
-                M[i, i + m] = c[m]
+            for j in (i - m, i + m):
+                sign = 1.0
+                if zs >= 0 and j <= zs:
+                    j, sign = 2 * zs - j, -1.0
+                if 0 <= j < n:
+                    M[i, j] += sign * c[m]
     return (M / (h * h)).tocsr()
 
 
@@ -63,14 +70,15 @@ def _d1(n, h):
     return (M / h).tocsr()
 
 
-def profiles(N, border, h, dt, vmax, f0, R=1e-3):
-    """(b, c) of one padded axis of length N."""
+def profiles(N, border, h, dt, vmax, f0, R=1e-3, low_face=True):
+    """(b, c) of one padded axis of length N (low_face=False: no layer at the
+    low end, the top face under a free surface)."""
     L = border * h
     d0 = -3.0 * vmax * np.log(R) / (2.0 * L) if border > 0 else 0.0
     dist = np.zeros(N)
     for i in range(N):
         if i < border:
-            dist[i] = border - i
+            dist[i] = border - i if low_face else 0
         elif i > N - 1 - border:
             dist[i] = i - (N - 1 - border)
     r = dist / max(border, 1)
@@ -91,8 +99,10 @@ class Operators:
         h, dt = g.dx, g.dt
         assert g.dx == g.dy == g.dz
         c = oracle.fd_coeffs()
+        # free surface: the top model plane (padded plane zs = border)
+        self.zs = g.border if getattr(g, "free_surface", 0) else -1
         I = [sp.identity(n, format="csr") for n in (Nz, Ny, Nx)]
-        d2 = [_d2(n, h, c) for n in (Nz, Ny, Nx)]
+        d2 = [_d2(Nz, h, c, self.zs), _d2(Ny, h, c), _d2(Nx, h, c)]
         d1 = [_d1(n, h) for n in (Nz, Ny, Nx)]
         # axis order a = 0: x, 1: y, 2: z (C order [z][y][x], x fastest)
         self.D2 = [sp.kron(sp.kron(I[0], I[1]), d2[2]).tocsr(),
@@ -101,8 +111,15 @@ class Operators:
         self.D1 = [sp.kron(sp.kron(I[0], I[1]), d1[2]).tocsr(),
                    sp.kron(sp.kron(I[0], d1[1]), I[2]).tocsr(),
                    sp.kron(sp.kron(d1[0], I[1]), I[2]).tocsr()]
+        self.D2T = [D.T.tocsr() for D in self.D2]
         vmax = float(np.max(vel))
-        bc = [profiles(n, g.border, h, dt, vmax, f0, R) for n in (Nx, Ny, Nz)]
+        bc = [profiles(Nx, g.border, h, dt, vmax, f0, R), profiles(Ny, g.border, h, dt, vmax, f0, R),
+              profiles(Nz, g.border, h, dt, vmax, f0, R, low_face=self.zs < 0)]
+        # the field is held at zero on and above a free surface
+        live = np.ones(self.shape)
+        if self.zs >= 0:
+            live[: self.zs + 1] = 0.0
+        self.live = live.ravel()
         ones = np.ones(self.shape)
         self.b = [(bc[0][0][None, None, :] * ones).ravel(),
                   (bc[1][0][None, :, None] * ones).ravel(),
@@ -178,7 +195,7 @@ def forward(op, wavelet, sn, scale, recs, keep=False):
             x += d2u + d1p + zeta[a]
         if keep:
             terms.append(x - op.m2 * u)
-        un = op.Bc * u - v + op.A * x
+        un = op.live * (op.Bc * u - v + op.A * x)
         np.add.at(un, sn, scale * wavelet[it])
         v, u = u, un
         tr[:, it] = recs @ u
@@ -221,15 +238,16 @@ def gradient(oracle, g, vel, src_xyz, wavelet, rec_offset, rec_xyz, dobs, f0, rh
         for it in range(nt - 1, -1, -1):
             lam += recs.T @ res[:, it]                       # d[n] = S u^{n+1}
             dwav[it] += np.sum(scale * lam[sn])
+            lam = op.live * lam                              # through the surface mask
             gA += lam * terms[it]                           # u^{n+1} = ... + A (x - m2 u)
             xb = op.A * lam                                  # adjoint of x^n
             ub = op.Bc * lam + mu                            # adjoint of u^n (so far)
-            ub += sum(op.D2[a] @ xb for a in range(3))
+            ub += sum(op.D2T[a] @ xb for a in range(3))
             for a in range(3):
                 zt = zetab[a] + xb                           # adjoint of zeta_a^n
                 y = op.c[a] * zt
                 zetab[a] = op.b[a] * zt                      # adjoint of zeta_a^{n-1}
-                ub += op.D2[a] @ y
+                ub += op.D2T[a] @ y
                 pt = psib[a] - op.D1[a] @ xb - op.D1[a] @ y  # adjoint of psi_a^n (D1^T = -D1)
                 psib[a] = op.b[a] * pt                       # adjoint of psi_a^{n-1}
                 ub -= op.D1[a] @ (op.c[a] * pt)

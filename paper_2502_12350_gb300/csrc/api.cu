@@ -396,7 +396,6 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   if (!(g->cerjan >= 0.f)) return fail(ctx, MAMUTE_EINVAL, "cerjan must be >= 0");
   if (g->pml != 0 && g->pml != 1) return fail(ctx, MAMUTE_EINVAL, "pml must be 0 or 1");
   if (g->pml) {
-    if (g->free_surface) return fail(ctx, MAMUTE_EINVAL, "pml with a free surface is not supported");
     if (!(g->pml_f0 >= 0.f)) return fail(ctx, MAMUTE_EINVAL, "pml_f0 must be >= 0");
     if (!(g->pml_r >= 0.f && g->pml_r < 1.f)) return fail(ctx, MAMUTE_EINVAL, "pml_r must be in [0, 1)");
     P.pml = true;
@@ -1101,13 +1100,15 @@ int data_to_user(mamute_ctx* ctx, const Plan& P, int n0, int n1, float* seis, cu
 // at each end, appended to bo / co: b = exp(-(d + alpha) dt) and
 // c = d (b - 1) / (d + alpha) with, at depth r = dist / border,
 // d = d0 r^2, d0 = -3 vmax ln(R) / (2 border h), alpha = pi f0 (1 - r);
-// b = 1, c = 0 outside the layer.
+// b = 1, c = 0 outside the layer.  low_face = false: no layer at the low
+// end (the top face under a free surface, whose image planes the main step
+// kernel forms).
 void cpml_profile(int N, int border, double h, double dt, double vmax, double f0, double R,
-                  std::vector<float>& bo, std::vector<float>& co) {
+                  std::vector<float>& bo, std::vector<float>& co, bool low_face = true) {
   const double d0 = border > 0 ? -3.0 * vmax * std::log(R) / (2.0 * border * h) : 0.0;
   for (int i = 0; i < N; ++i) {
     int dist = 0;
-    if (i < border) dist = border - i;
+    if (i < border) dist = low_face ? border - i : 0;
     else if (i > N - 1 - border) dist = i - (N - 1 - border);
     double b = 1.0, c = 0.0;
     if (dist > 0) {
@@ -1144,7 +1145,7 @@ int cpml_setup(mamute_ctx* ctx, const Plan& P, const float* vel, const float* rh
     T.max_layer = std::max(T.max_layer, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b));
     T.max_shell = std::max(T.max_shell, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b + 4));
   }
-  cpml_profile(P.Nz, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bz, cz);
+  cpml_profile(P.Nz, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bz, cz, P.zs < 0);
   std::vector<float> all;
   size_t off[6];
   const std::vector<float>* parts[6] = {&bx, &cx, &by, &cy, &bz, &cz};

@@ -58,19 +58,19 @@ def _offgrid(w, seed):
     return w
 
 
-def gpu_model(ctx, w, xi=0, **opts):
+def gpu_model(ctx, w, xi=0, fs=0, **opts):
     from paper_2502_12350_gb300 import mamute
     nt_out = opts.get("nt_data", w.nt) if opts.get("time_interp", 0) else w.nt
     seis = torch.full((int(w.rec_offset[-1]), nt_out), float("nan"), device="cuda:0")
-    ctx.model(mamute.grid_of(w, cerjan=0.0, xyz_interp=xi, pml=1), _dev(w.vel), _dev(w.rho),
-              w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, seis, **opts)
+    ctx.model(mamute.grid_of(w, cerjan=0.0, xyz_interp=xi, pml=1, free_surface=fs), _dev(w.vel),
+              _dev(w.rho), w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, seis, **opts)
     return seis.cpu().numpy()
 
 
-def gpu_gradient(ctx, w, dobs, xi=0, adjoint=False, **opts):
+def gpu_gradient(ctx, w, dobs, xi=0, adjoint=False, fs=0, **opts):
     from paper_2502_12350_gb300 import mamute
     grad = torch.full((w.nz, w.ny, w.nx), float("nan"), device="cuda:0")
-    g = mamute.grid_of(w, cerjan=0.0, xyz_interp=xi, pml=1)
+    g = mamute.grid_of(w, cerjan=0.0, xyz_interp=xi, pml=1, free_surface=fs)
     args = (g, _dev(w.vel), _dev(w.rho), w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, _dev(dobs),
             grad)
     if adjoint:
@@ -80,8 +80,18 @@ def gpu_gradient(ctx, w, dobs, xi=0, adjoint=False, **opts):
     return J, grad.cpu().numpy()
 
 
-def ogrid(oracle, w, xi=0):
-    return oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, xyz_interp=xi)
+def ogrid(oracle, w, xi=0, fs=0):
+    return oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt, xyz_interp=xi,
+                            free_surface=fs)
+
+
+def _below_surface(w):
+    """Sources and receivers below the top model plane (the free surface)."""
+    w.src_xyz = w.src_xyz.copy()
+    w.rec_xyz = w.rec_xyz.copy()
+    w.src_xyz[:, 2] = np.maximum(w.src_xyz[:, 2], 2 * w.h)
+    w.rec_xyz[:, 2] = np.maximum(w.rec_xyz[:, 2], 1 * w.h)
+    return w
 
 
 CASES = [
@@ -92,27 +102,32 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("xi", [0, 1])
-def test_model_matches_oracle(ctx, oracle, case, xi):
+@pytest.mark.parametrize("xi,fs", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_model_matches_oracle(ctx, oracle, case, xi, fs):
     from oracle import cpml
     w = synth.small_case(**case)
     if xi:
         w = _offgrid(w, case["seed"])
-    got = gpu_model(ctx, w, xi)
-    ref = cpml.model(oracle, ogrid(oracle, w, xi), w.vel, w.src_xyz, w.wavelet, w.rec_offset,
+    if fs:
+        w = _below_surface(w)
+    got = gpu_model(ctx, w, xi, fs)
+    ref = cpml.model(oracle, ogrid(oracle, w, xi, fs), w.vel, w.src_xyz, w.wavelet, w.rec_offset,
                      w.rec_xyz, f0=w.fpeak, rho=w.rho)
     assert np.isfinite(got).all()
     assert rel(got, ref) <= SEIS_TOL, rel(got, ref)
 
 
-@pytest.mark.parametrize("density,xi", [(True, 0), (False, 0), (True, 1)])
-def test_gradient_matches_oracle(ctx, oracle, density, xi):
+@pytest.mark.parametrize("density,xi,fs", [(True, 0, 0), (False, 0, 0), (True, 1, 0), (True, 0, 1),
+                                           (False, 1, 1)])
+def test_gradient_matches_oracle(ctx, oracle, density, xi, fs):
     from oracle import cpml
     w = synth.small_case(seed=33, nx=22, ny=19, nz=17, border=7, nt=55, density=density, n_src=2,
                          n_rec=8)
     if xi:
         w = _offgrid(w, 34)
-    og = ogrid(oracle, w, xi)
+    if fs:
+        w = _below_surface(w)
+    og = ogrid(oracle, w, xi, fs)
     rng = np.random.default_rng(35)
     # a 10 % perturbation keeps the residual well above the FP32 rounding of
     # the traces, so that J is compared at 1e-4
@@ -121,7 +136,7 @@ def test_gradient_matches_oracle(ctx, oracle, density, xi):
                       f0=w.fpeak, rho=w.rho).astype(np.float32)
     Jr, gr = cpml.gradient(oracle, og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, dobs,
                            f0=w.fpeak, rho=w.rho)
-    J, g = gpu_gradient(ctx, w, dobs, xi)
+    J, g = gpu_gradient(ctx, w, dobs, xi, fs=fs)
     assert np.isfinite(g).all()
     assert abs(J - Jr) <= 1e-4 * Jr, (J, Jr)
     assert cosine(g, gr) >= GRAD_COS
@@ -207,9 +222,6 @@ def test_invalid_combinations(ctx):
     grad = torch.zeros((w.nz, w.ny, w.nx), device="cuda:0")
     vel = _dev(w.vel)
     geo = (w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz)
-    with pytest.raises(mamute.MamuteError) as e:
-        ctx.model(mamute.grid_of(w, pml=1, free_surface=1), vel, None, *geo, seis)
-    assert e.value.code == mamute.EINVAL
     with pytest.raises(mamute.MamuteError) as e:
         ctx.gradient(mamute.grid_of(w, pml=1), vel, None, *geo, seis, grad, n_snapshots=3)
     assert e.value.code == mamute.EINVAL
