@@ -744,7 +744,23 @@ cudaError_t dft_launch(mamute_ctx* ctx, const float* V, long long N, int T, int 
     if (e != cudaSuccess) return e;
   }
   ctx->launches += 2;
-  e = launch_dft(V, N, T, n0, nf, bins, nb, W, re, im, ctx->status, ctx->stream);
+  if (dft_tc_supported(N, nb) && (uintptr_t)V % 16 == 0 && (uintptr_t)re % 16 == 0 &&
+      (uintptr_t)im % 16 == 0 && (uintptr_t)W % 16 == 0) {
+    // tensor cores: samples by TMA (V as {N, T, 1} FP32, boxes of 128 x 32)
+    CUtensorMap vmap;
+    cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)std::max(T, 1), 1};
+    cuuint64_t strides[2] = {(cuuint64_t)N * 4, (cuuint64_t)N * std::max(T, 1) * 4};
+    cuuint32_t box[3] = {128, 32, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (ctx->encode(&vmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(V), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE))
+      return cudaErrorInvalidValue;
+    e = launch_dft_tc(vmap, N, T, n0, nf, bins, nb, reinterpret_cast<float*>(W), re, im,
+                      ctx->status, ctx->stream);
+  } else {
+    e = launch_dft(V, N, T, n0, nf, bins, nb, W, re, im, ctx->status, ctx->stream);
+  }
   if (e == cudaSuccess && ctx->timing && T > 0) {
     e = cudaEventRecord(ctx->dft_ev[2 * ctx->dft_n + 1], ctx->stream);
     ++ctx->dft_n;
@@ -1865,8 +1881,11 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   // Shots are propagated together and receivers B at a time (one unit
   // impulse per shot window), so each batch is one launch per step; the DFT
   // accumulators hold every window of the batch.
-  const int kT = 64;
   const long long N = (long long)P.nx * P.ny * P.nz;
+  // Samples per DFT accumulation: 256 on the tensor cores (the accumulators
+  // are read and written once per block), 64 on the FP32 path (its twiddles
+  // and samples live in shared memory).
+  const int kT = dft_tc_supported(N, nb) ? 256 : 64;
   int B = n_src;
   {
     size_t fr = 0, tot = 0;
@@ -1882,7 +1901,7 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   CK(ensure(ctx->gnIm, (size_t)nb * B * N * 4));
   CK(ensure(ctx->gnS, (size_t)nb * N * 4));
   CK(ensure(ctx->gnR, (size_t)nb * N * 4));
-  CK(ensure(ctx->gnW, (size_t)kT * dft_max_bins() * 8));
+  CK(ensure(ctx->gnW, std::max((size_t)kT * dft_max_bins() * 8, dft_tc_image_bytes(kT, nb))));
   CK(upload(ctx->gnBins, bins, ctx->stream));
   CK(upload(ctx->gnWts, wts, ctx->stream));
   CK(ensure(ctx->gnRow, (size_t)2 * std::max(P.ncol, 1) * 4));

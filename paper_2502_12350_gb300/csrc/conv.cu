@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace mamute {
 

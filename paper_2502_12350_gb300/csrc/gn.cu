@@ -9,6 +9,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace mamute {
 
@@ -180,6 +181,275 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
   }
 }
 
+// ---- Tensor-core form of the same accumulation (kind::tf32, 3 products).
+//
+// The block sum acc[k][x] += sum_t V[t][x] W[t][k] is a product of a
+// (2 nb) x T twiddle matrix (rows: cos of bins 64 j .. 64 j + 63, then -sin
+// of the same bins, per M tile j) with the T x N sample matrix.  Each
+// operand x is split into tf32 parts hi = rna(x), lo = rna(x - hi) and the
+// product is taken as A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped term is
+// below FP32 rounding), with FP32 accumulation in tensor memory over all T
+// samples of the block: the accumulators are read and written once per
+// block instead of once per 64 samples.
+//
+// Operands in shared memory use the K-major canonical layout without
+// swizzle: core matrices of 8 rows x 16 bytes (4 tf32), the 8 K-cores of a
+// 32-sample chunk 128 bytes apart (LBO), 8-row groups 1024 bytes apart
+// (SBO).  A CTA takes tiles of 128 points; per 32-sample chunk the producer
+// brings the 32 x 128 samples by TMA and the chunk's twiddle images (built
+// in that layout by dft_image_kernel) by one bulk copy, four warps split the
+// samples into hi / lo rows, and one thread issues mt x 4 x 3 products
+// M=128 N=128 K=8 into a double-buffered accumulator; four epilogue warps
+// add the tile's accumulators to acc.
+
+constexpr int kTcNP = 128;                    // points per tile (MMA N)
+constexpr int kTcKC = 32;                     // samples per chunk
+constexpr int kTcImg = 128 * kTcKC * 4;       // bytes of one 128-row chunk image
+constexpr int kTcMaxMt = 2;                   // M tiles: up to 128 bins
+constexpr int kTcVBytes = kTcKC * kTcNP * 4;  // samples of one chunk
+constexpr int kTcABytes = kTcMaxMt * 2 * kTcImg;
+constexpr int kTcSBytes = 2 * kTcImg;         // hi and lo sample rows
+constexpr int kTcSmem = 2 * (kTcVBytes + kTcABytes) + 2 * kTcSBytes + 1024;
+constexpr int kTcDftThreads = 320;
+
+// D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9, 10-12 = 2), both K-major,
+// N = 128 (bits 17-22: N >> 3), M = 128 (bits 24-28: M >> 4).
+constexpr uint32_t kDftIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) |
+                               ((128u >> 4) << 24);
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of element (row, k) in a canonical K-major image of 8-row
+// groups with kTcKC / 4 K-cores each.
+__device__ __forceinline__ int img_off(int row, int k) {
+  return (row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+// Twiddle images: for chunk c, M tile j and part p (0 hi, 1 lo) a 128 x 32
+// image at W + ((c * mt + j) * 2 + p) * kTcImg bytes.
+__global__ void dft_image_kernel(int T, int n0, int nf, const int* __restrict__ bins, int nb,
+                                 int mt, int nchunks, float* __restrict__ W) {
+  const int n = nchunks * mt * 128 * kTcKC;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int k = e % kTcKC, row = (e / kTcKC) % 128, j = (e / (kTcKC * 128)) % mt;
+    const int c = e / (kTcKC * 128 * mt);
+    const int t = c * kTcKC + k, bin = 64 * j + (row & 63);
+    float v = 0.0f;
+    if (t < T && bin < nb) {
+      const long long m = ((long long)bins[bin] * (long long)(n0 + t)) % nf;
+      float sn, cs;
+      sincospif(2.0f * (float)m / (float)nf, &sn, &cs);
+      v = row < 64 ? cs : -sn;
+    }
+    const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
+    char* base = reinterpret_cast<char*>(W) + (size_t)((c * mt + j) * 2) * kTcImg;
+    *reinterpret_cast<float*>(base + img_off(row, k)) = hi;
+    *reinterpret_cast<float*>(base + kTcImg + img_off(row, k)) = lo;
+  }
+}
+
+struct DftTcArgs {
+  const float* W;   // twiddle images
+  float* re;
+  float* im;
+  long long N;
+  int nb, mt, nchunks;
+  int* status;
+};
+
+__global__ void __launch_bounds__(kTcDftThreads, 1)
+    dft_tc_kernel(const __grid_constant__ CUtensorMap vmap, DftTcArgs a) {
+  extern __shared__ unsigned char dft_raw[];
+  unsigned char* sm = dft_raw + ((1024 - (smem_u32(dft_raw) & 1023)) & 1023);
+  unsigned char* vraw = sm;                              // 2 stages of samples
+  unsigned char* aimg = sm + 2 * kTcVBytes;              // 2 stages of twiddle images
+  unsigned char* bspl = aimg + 2 * kTcABytes;            // 2 buffers of hi / lo rows
+  __shared__ uint64_t full[2], empty[2], sready[2], sfree[2], tfull[2], tempty[2], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  volatile int* ab = &abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long ntiles = (a.N + kTcNP - 1) / kTcNP;
+  const int nch = a.nchunks, mt = a.mt;
+  const uint32_t abytes = (uint32_t)(mt * 2 * kTcImg);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 5);   // 4 split warps + the MMA commit
+      mbar_init(&sready[i], 4);
+      mbar_init(&sfree[i], 1);
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_init(&done_bar, 1);
+    fence_barrier_init();
+    abort_flag = 0;
+  }
+  if (warp == 1) {
+    tc_alloc(&tmem_base, 512);
+    tc_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    // ---- producer: per chunk, the samples (TMA) and the twiddle images
+    if (lane == 0) {
+      tmap_acquire(&vmap);
+      uint32_t q = 0;
+      for (long long tile = blockIdx.x; tile < ntiles && !*ab; tile += gridDim.x)
+        for (int c = 0; c < nch; ++c, ++q) {
+          const int s = q & 1, r = (int)(q >> 1);
+          if (r > 0 && !tc_wait(&empty[s], (r & 1) ^ 1, a.status, ab)) break;
+          mbar_arrive_expect_tx(&full[s], (uint32_t)kTcVBytes + abytes);
+          tma_load_3d(vraw + s * kTcVBytes, &vmap, (int)(tile * kTcNP), c * kTcKC, 0, &full[s]);
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                  "r"(smem_u32(aimg + s * kTcABytes)),
+              "l"(reinterpret_cast<const char*>(a.W) + (size_t)c * abytes), "r"(abytes),
+              "r"(smem_u32(&full[s]))
+              : "memory");
+        }
+      if (*ab)  // let issued loads land before the CTA exits
+        for (uint32_t k = 0; k < 2 && k < q; ++k) {
+          const uint32_t qq = q - 1 - k;
+          mbar_wait(&full[qq & 1], (qq >> 1) & 1, a.status);
+        }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t abase = smem_u32(aimg), bbase = smem_u32(bspl);
+      uint32_t q = 0, p = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok && !*ab; tile += gridDim.x, ++p) {
+        const uint32_t tb = p & 1;
+        if (p >= 2 && !(ok = tc_wait(&tempty[tb], ((p >> 1) & 1) ^ 1, a.status, ab))) break;
+        for (int c = 0; c < nch && ok; ++c, ++q) {
+          const uint32_t s = q & 1;
+          if (!(ok = tc_wait(&full[s], (q >> 1) & 1, a.status, ab))) break;
+          if (!(ok = tc_wait(&sready[s], (q >> 1) & 1, a.status, ab))) break;
+          tc_fence_after();
+          const uint32_t bhi = bbase + s * kTcSBytes, blo = bhi + kTcImg;
+          for (int j = 0; j < mt; ++j) {
+            const uint32_t ahi = abase + s * kTcABytes + (uint32_t)(j * 2 * kTcImg);
+            const uint32_t alo = ahi + kTcImg;
+            const uint32_t d = tmem + tb * 256u + (uint32_t)(j * 128);
+#pragma unroll
+            for (int ks = 0; ks < kTcKC / 8; ++ks) {
+              const uint32_t ko = (uint32_t)ks * 256u;  // two K-cores per product
+              const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+              tc_mma_tf32(d, tc_sdesc(ahi + ko, 128u, 1024u), tc_sdesc(bhi + ko, 128u, 1024u), kDftIdesc,
+                     acc0);
+              tc_mma_tf32(d, tc_sdesc(ahi + ko, 128u, 1024u), tc_sdesc(blo + ko, 128u, 1024u), kDftIdesc, 1u);
+              tc_mma_tf32(d, tc_sdesc(alo + ko, 128u, 1024u), tc_sdesc(bhi + ko, 128u, 1024u), kDftIdesc, 1u);
+            }
+          }
+          tc_commit(&empty[s]);
+          tc_commit(&sfree[s]);
+        }
+        if (ok) tc_commit(&tfull[tb]);
+      }
+      tc_commit(&done_bar);
+      mbar_wait(&done_bar, 0, a.status);
+    }
+  } else if (warp < 6) {
+    // ---- split: samples of point n = 32 (warp - 2) + lane into hi / lo rows
+    const int n = 32 * (warp - 2) + lane;
+    uint32_t q = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok && !*ab; tile += gridDim.x)
+      for (int c = 0; c < nch; ++c, ++q) {
+        const int s = q & 1, r = (int)(q >> 1);
+        int got = 1;
+        if (lane == 0) {
+          got = tc_wait(&full[s], r & 1, a.status, ab) ? 1 : 0;
+          if (got && r > 0) got = tc_wait(&sfree[s], (r & 1) ^ 1, a.status, ab) ? 1 : 0;
+        }
+        if (!(ok = __shfl_sync(0xffffffffu, got, 0) != 0)) break;
+        const float* vr = reinterpret_cast<const float*>(vraw + s * kTcVBytes);
+        unsigned char* hi = bspl + s * kTcSBytes;
+        unsigned char* lo = hi + kTcImg;
+#pragma unroll
+        for (int k4 = 0; k4 < kTcKC / 4; ++k4) {
+          float4 h, l;
+          float* hp = &h.x;
+          float* lp = &l.x;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float x = vr[(k4 * 4 + e) * kTcNP + n];
+            hp[e] = tf32_rna(x);
+            lp[e] = tf32_rna(x - hp[e]);
+          }
+          *reinterpret_cast<float4*>(hi + img_off(n, k4 * 4)) = h;
+          *reinterpret_cast<float4*>(lo + img_off(n, k4 * 4)) = l;
+        }
+        fence_async_smem();  // visible to the tensor cores (async proxy)
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&sready[s]);
+          mbar_arrive(&empty[s]);  // the samples of this stage are read
+        }
+      }
+  } else {
+    // ---- epilogue: TMEM lane quarter q = warp & 3 (warps 6..9 -> 2, 3, 0, 1)
+    const int quarter = warp & 3, row = quarter * 32 + lane;
+    uint32_t p = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++p) {
+      const uint32_t tb = p & 1;
+      int got = 0;
+      if (lane == 0) got = tc_wait(&tfull[tb], (p >> 1) & 1, a.status, ab) ? 1 : 0;
+      if (!(ok = __shfl_sync(0xffffffffu, got, 0) != 0)) break;
+      tc_fence_after();
+      const long long x0 = tile * kTcNP;
+      for (int j = 0; j < mt; ++j) {
+        const int bin = 64 * j + (row & 63);
+        float* dst = (row < 64 ? a.re : a.im) + (long long)bin * a.N;
+#pragma unroll 1
+        for (int cb = 0; cb < kTcNP / 32; ++cb) {
+          uint32_t r[32];
+          tc_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * 256u + (uint32_t)(j * 128 + cb * 32),
+                  r);
+          tc_wait_ld();
+          const long long xb = x0 + cb * 32;
+          if (bin < a.nb) {
+            if (xb + 32 <= a.N) {
+              float4* dp = reinterpret_cast<float4*>(dst + xb);
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                float4 v = dp[k];
+                v.x += __uint_as_float(r[4 * k]);
+                v.y += __uint_as_float(r[4 * k + 1]);
+                v.z += __uint_as_float(r[4 * k + 2]);
+                v.w += __uint_as_float(r[4 * k + 3]);
+                dp[k] = v;
+              }
+            } else {
+              for (int k = 0; k < 32 && xb + k < a.N; ++k) dst[xb + k] += __uint_as_float(r[k]);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[tb]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tc_dealloc(tmem, 512);
+  }
+}
+
 // pw[k][x] += sum_v re[k][v N + x]^2 + im[k][v N + x]^2 over the nv windows
 // of a batch (accumulators laid out [k][nv N]); then re = im = 0.
 __global__ void power_kernel(int nb, long long N, int nv, float* __restrict__ re,
@@ -277,6 +547,36 @@ cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const
     dft_kernel<true><<<grid, threads, sm, s>>>(V, N, T, nb, W, re, im, status);
   else
     dft_kernel<false><<<grid, threads, sm, s>>>(V, N, T, nb, W, re, im, status);
+  return cudaGetLastError();
+}
+
+size_t dft_tc_image_bytes(int T, int nb) {
+  const int mt = (nb + 63) / 64, nch = (T + kTcKC - 1) / kTcKC;
+  return (size_t)nch * mt * 2 * kTcImg;
+}
+
+bool dft_tc_supported(long long N, int nb) { return N % 4 == 0 && nb >= 1 && nb <= 64 * kTcMaxMt; }
+
+cudaError_t launch_dft_tc(const CUtensorMap& vmap, long long N, int T, int n0, int nf,
+                          const int* bins, int nb, float* W, float* re, float* im, int* status,
+                          cudaStream_t s) {
+  if (T <= 0 || N <= 0) return cudaSuccess;
+  if (!dft_tc_supported(N, nb)) return cudaErrorInvalidValue;
+  const int mt = (nb + 63) / 64, nch = (T + kTcKC - 1) / kTcKC;
+  const int n = nch * mt * 128 * kTcKC;
+  dft_image_kernel<<<(n + 255) / 256, 256, 0, s>>>(T, n0, nf, bins, nb, mt, nch, W);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(dft_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  DftTcArgs a{W, re, im, N, nb, mt, nch, status};
+  const long long ntiles = (N + kTcNP - 1) / kTcNP;
+  const int grid = (int)std::min<long long>(ntiles, 152);
+  dft_tc_kernel<<<grid, kTcDftThreads, kTcSmem, s>>>(vmap, a);
   return cudaGetLastError();
 }
 

@@ -22,8 +22,8 @@ def ctx():
     c.close()
 
 
-def _common_receivers(density, seed, nt=120):
-    w = synth.small_case(seed=seed, nx=14, ny=12, nz=10, border=6, nt=nt, density=density,
+def _common_receivers(density, seed, nt=120, nx=14, ny=12):
+    w = synth.small_case(seed=seed, nx=nx, ny=ny, nz=10, border=6, nt=nt, density=density,
                          n_src=3, n_rec=5, fpeak=35.0)
     one = w.rec_xyz[:5]
     w.rec_xyz = np.concatenate([one] * w.n_src)
@@ -73,4 +73,24 @@ def test_gn_diagonal_full_band(ctx, oracle):
     ctx.gn_diagonal(mamute.grid_of(w), vel, None, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
                     H, band_rel=0.0)
     got = H.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
+
+
+@pytest.mark.parametrize("nt,nx,ny", [(300, 14, 12), (120, 13, 11)])
+def test_gn_diagonal_blocks_and_fp32_path(ctx, oracle, nt, nx, ny):
+    """nt = 300: two accumulation blocks on the tensor cores (256 samples and
+    a ragged 44); 13 x 11 x 10 points (not a multiple of 4): the FP32 path."""
+    from paper_2502_12350_gb300 import mamute
+    w = _common_receivers(True, 65, nt=nt, nx=nx, ny=ny)
+    og = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
+    ref = gn.separable(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho,
+                       band_rel=1e-4)
+    dev = torch.device("cuda:0")
+    vel = torch.from_numpy(w.vel).to(dev)
+    rho = torch.from_numpy(w.rho).to(dev)
+    H = torch.full_like(vel, float("nan"))
+    ctx.gn_diagonal(mamute.grid_of(w), vel, rho, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz,
+                    H, band_rel=1e-4)
+    got = H.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all() and got.min() > 0
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
