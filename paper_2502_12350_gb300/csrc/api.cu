@@ -746,17 +746,19 @@ cudaError_t dft_launch(mamute_ctx* ctx, const float* V, long long N, int T, int 
   ctx->launches += 2;
   if (dft_tc_supported(N, nb) && (uintptr_t)V % 16 == 0 && (uintptr_t)re % 16 == 0 &&
       (uintptr_t)im % 16 == 0 && (uintptr_t)W % 16 == 0) {
-    // tensor cores: samples by TMA (V as {N, T, 1} FP32, boxes of 128 x 32)
+    // tensor cores: samples by TMA (V as {N, T, 1} FP32, boxes of 128 points
+    // x one chunk of samples)
     CUtensorMap vmap;
     cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)std::max(T, 1), 1};
     cuuint64_t strides[2] = {(cuuint64_t)N * 4, (cuuint64_t)N * std::max(T, 1) * 4};
-    cuuint32_t box[3] = {128, 32, 1};
+    cuuint32_t box[3] = {128, (cuuint32_t)dft_tc_chunk(), 1};
     cuuint32_t es[3] = {1, 1, 1};
     if (ctx->encode(&vmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(V), dims, strides,
                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE))
       return cudaErrorInvalidValue;
-    e = launch_dft_tc(vmap, N, T, n0, nf, bins, nb, reinterpret_cast<float*>(W), re, im,
+    // every batch starts from zeroed accumulators: its first block stores
+    e = launch_dft_tc(vmap, N, T, n0, nf, bins, nb, reinterpret_cast<float*>(W), re, im, n0 == 0,
                       ctx->status, ctx->stream);
   } else {
     e = launch_dft(V, N, T, n0, nf, bins, nb, W, re, im, ctx->status, ctx->stream);
@@ -1882,19 +1884,42 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   // impulse per shot window), so each batch is one launch per step; the DFT
   // accumulators hold every window of the batch.
   const long long N = (long long)P.nx * P.ny * P.nz;
-  // Samples per DFT accumulation: 256 on the tensor cores (the accumulators
-  // are read and written once per block), 64 on the FP32 path (its twiddles
-  // and samples live in shared memory).
-  const int kT = dft_tc_supported(N, nb) ? 256 : 64;
-  int B = n_src;
+  // Samples per DFT accumulation: up to 1024 on the tensor cores (the
+  // accumulators are read and written once per block; the first block of a
+  // batch only writes them), 64 on the FP32 path (its twiddles and samples
+  // live in shared memory).  Batches of B windows share each launch.
+  // The longest block that still lets a batch hold every shot (fewer, fuller
+  // batches matter more for the propagations than block length does for the
+  // accumulation).
+  int kT = 64, B = n_src;
   {
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
-    const double per_vol = ((double)2 * nb + kT) * (double)N * 4.0;
+    // buffers this context already holds for the labels count as available
+    const double avail = (double)fr + (double)ctx->gnV.bytes + (double)ctx->gnRe.bytes +
+                         (double)ctx->gnIm.bytes;
     const double fixed = 2.0 * nb * (double)N * 4.0;  // S and R
-    B = (int)std::max(1.0, std::min((double)n_src, (0.6 * (double)fr - fixed) / per_vol));
+    auto batch = [&](int t) {
+      const double per_vol = ((double)2 * nb + t) * (double)N * 4.0;
+      return (int)std::max(1.0, std::min((double)n_src, (0.6 * avail - fixed) / per_vol));
+    };
+    if (dft_tc_supported(N, nb)) {
+      const int want = std::min(n_src, 16);
+      kT = 256;
+      for (int t : {1024, 512, 256}) {
+        const int tt = std::min(t, (nt + 31) / 32 * 32);
+        if (batch(tt) >= want) {
+          kT = tt;
+          break;
+        }
+      }
+    }
+    B = batch(kT);
     const int cap = env_int("MAMUTE_GN_BATCH", 0);  // smaller batches (profiling)
     if (cap > 0) B = std::min(B, cap);
+    if (env_int("MAMUTE_VERBOSE", 0))
+      fprintf(stderr, "mamute gn: %d bins, blocks of %d samples, batches of %d windows (%.1f GB available)\n",
+              nb, kT, B, avail * 1e-9);
   }
   CK(ensure(ctx->gnV, (size_t)kT * B * N * 4));
   CK(ensure(ctx->gnRe, (size_t)nb * B * N * 4));

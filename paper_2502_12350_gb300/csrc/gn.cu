@@ -193,23 +193,26 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1)
 // block instead of once per 64 samples.
 //
 // Operands in shared memory use the K-major canonical layout without
-// swizzle: core matrices of 8 rows x 16 bytes (4 tf32), the 8 K-cores of a
-// 32-sample chunk 128 bytes apart (LBO), 8-row groups 1024 bytes apart
-// (SBO).  A CTA takes tiles of 128 points; per 32-sample chunk the producer
-// brings the 32 x 128 samples by TMA and the chunk's twiddle images (built
-// in that layout by dft_image_kernel) by one bulk copy, four warps split the
-// samples into hi / lo rows, and one thread issues mt x 4 x 3 products
-// M=128 N=128 K=8 into a double-buffered accumulator; four epilogue warps
-// add the tile's accumulators to acc.
+// swizzle: core matrices of 8 rows x 16 bytes (4 tf32), the 4 K-cores of a
+// 16-sample chunk 128 bytes apart (LBO), 8-row groups 512 bytes apart
+// (SBO).  A CTA takes tiles of 128 points; per 16-sample chunk the producer
+// brings the 16 x 128 samples by TMA and the chunk's twiddle images (built
+// in that layout by dft_image_kernel) by one bulk copy into a 4-stage ring,
+// four warps split the samples into hi / lo rows, and one thread issues
+// mt x 2 x 3 products M=128 N=128 K=8 into a double-buffered accumulator;
+// four epilogue warps add (or, for the first block of a batch, store) the
+// tile's accumulators to acc.
 
 constexpr int kTcNP = 128;                    // points per tile (MMA N)
-constexpr int kTcKC = 32;                     // samples per chunk
+constexpr int kTcKC = 16;                     // samples per chunk
+constexpr int kTcStages = 4;                  // ring of sample / twiddle stages
+constexpr int kTcGroup = (kTcKC / 4) * 128;   // bytes per 8-row group (SBO)
 constexpr int kTcImg = 128 * kTcKC * 4;       // bytes of one 128-row chunk image
 constexpr int kTcMaxMt = 2;                   // M tiles: up to 128 bins
 constexpr int kTcVBytes = kTcKC * kTcNP * 4;  // samples of one chunk
 constexpr int kTcABytes = kTcMaxMt * 2 * kTcImg;
 constexpr int kTcSBytes = 2 * kTcImg;         // hi and lo sample rows
-constexpr int kTcSmem = 2 * (kTcVBytes + kTcABytes) + 2 * kTcSBytes + 1024;
+constexpr int kTcSmem = kTcStages * (kTcVBytes + kTcABytes) + 2 * kTcSBytes + 1024;
 constexpr int kTcDftThreads = 320;
 
 // D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9, 10-12 = 2), both K-major,
@@ -226,7 +229,7 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // Byte offset of element (row, k) in a canonical K-major image of 8-row
 // groups with kTcKC / 4 K-cores each.
 __device__ __forceinline__ int img_off(int row, int k) {
-  return (row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+  return (row >> 3) * kTcGroup + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
 }
 
 // Twiddle images: for chunk c, M tile j and part p (0 hi, 1 lo) a 128 x 32
@@ -258,6 +261,7 @@ struct DftTcArgs {
   float* im;
   long long N;
   int nb, mt, nchunks;
+  int overwrite;    // the accumulators are zero: store instead of add
   int* status;
 };
 
@@ -265,10 +269,11 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
     dft_tc_kernel(const __grid_constant__ CUtensorMap vmap, DftTcArgs a) {
   extern __shared__ unsigned char dft_raw[];
   unsigned char* sm = dft_raw + ((1024 - (smem_u32(dft_raw) & 1023)) & 1023);
-  unsigned char* vraw = sm;                              // 2 stages of samples
-  unsigned char* aimg = sm + 2 * kTcVBytes;              // 2 stages of twiddle images
-  unsigned char* bspl = aimg + 2 * kTcABytes;            // 2 buffers of hi / lo rows
-  __shared__ uint64_t full[2], empty[2], sready[2], sfree[2], tfull[2], tempty[2], done_bar;
+  unsigned char* vraw = sm;                                   // stages of samples
+  unsigned char* aimg = sm + kTcStages * kTcVBytes;           // stages of twiddle images
+  unsigned char* bspl = aimg + kTcStages * kTcABytes;         // 2 buffers of hi / lo rows
+  __shared__ uint64_t full[kTcStages], empty[kTcStages], sready[2], sfree[2], tfull[2], tempty[2],
+      done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   volatile int* ab = &abort_flag;
@@ -277,9 +282,11 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
   const int nch = a.nchunks, mt = a.mt;
   const uint32_t abytes = (uint32_t)(mt * 2 * kTcImg);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kTcStages; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 5);   // 4 split warps + the MMA commit
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&sready[i], 4);
       mbar_init(&sfree[i], 1);
       mbar_init(&tfull[i], 1);
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
       uint32_t q = 0;
       for (long long tile = blockIdx.x; tile < ntiles && !*ab; tile += gridDim.x)
         for (int c = 0; c < nch; ++c, ++q) {
-          const int s = q & 1, r = (int)(q >> 1);
+          const int s = (int)(q % kTcStages), r = (int)(q / kTcStages);
           if (r > 0 && !tc_wait(&empty[s], (r & 1) ^ 1, a.status, ab)) break;
           mbar_arrive_expect_tx(&full[s], (uint32_t)kTcVBytes + abytes);
           tma_load_3d(vraw + s * kTcVBytes, &vmap, (int)(tile * kTcNP), c * kTcKC, 0, &full[s]);
@@ -317,9 +324,9 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
               : "memory");
         }
       if (*ab)  // let issued loads land before the CTA exits
-        for (uint32_t k = 0; k < 2 && k < q; ++k) {
+        for (uint32_t k = 0; k < (uint32_t)kTcStages && k < q; ++k) {
           const uint32_t qq = q - 1 - k;
-          mbar_wait(&full[qq & 1], (qq >> 1) & 1, a.status);
+          mbar_wait(&full[qq % kTcStages], (qq / kTcStages) & 1, a.status);
         }
     }
   } else if (warp == 1) {
@@ -332,11 +339,11 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
         const uint32_t tb = p & 1;
         if (p >= 2 && !(ok = tc_wait(&tempty[tb], ((p >> 1) & 1) ^ 1, a.status, ab))) break;
         for (int c = 0; c < nch && ok; ++c, ++q) {
-          const uint32_t s = q & 1;
-          if (!(ok = tc_wait(&full[s], (q >> 1) & 1, a.status, ab))) break;
-          if (!(ok = tc_wait(&sready[s], (q >> 1) & 1, a.status, ab))) break;
+          const uint32_t s = q % kTcStages, b = q & 1;
+          if (!(ok = tc_wait(&full[s], (q / kTcStages) & 1, a.status, ab))) break;
+          if (!(ok = tc_wait(&sready[b], (q >> 1) & 1, a.status, ab))) break;
           tc_fence_after();
-          const uint32_t bhi = bbase + s * kTcSBytes, blo = bhi + kTcImg;
+          const uint32_t bhi = bbase + b * kTcSBytes, blo = bhi + kTcImg;
           for (int j = 0; j < mt; ++j) {
             const uint32_t ahi = abase + s * kTcABytes + (uint32_t)(j * 2 * kTcImg);
             const uint32_t alo = ahi + kTcImg;
@@ -345,14 +352,14 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
             for (int ks = 0; ks < kTcKC / 8; ++ks) {
               const uint32_t ko = (uint32_t)ks * 256u;  // two K-cores per product
               const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-              tc_mma_tf32(d, tc_sdesc(ahi + ko, 128u, 1024u), tc_sdesc(bhi + ko, 128u, 1024u), kDftIdesc,
-                     acc0);
-              tc_mma_tf32(d, tc_sdesc(ahi + ko, 128u, 1024u), tc_sdesc(blo + ko, 128u, 1024u), kDftIdesc, 1u);
-              tc_mma_tf32(d, tc_sdesc(alo + ko, 128u, 1024u), tc_sdesc(bhi + ko, 128u, 1024u), kDftIdesc, 1u);
+              constexpr uint32_t G = kTcGroup;
+              tc_mma_tf32(d, tc_sdesc(ahi + ko, 128u, G), tc_sdesc(bhi + ko, 128u, G), kDftIdesc, acc0);
+              tc_mma_tf32(d, tc_sdesc(ahi + ko, 128u, G), tc_sdesc(blo + ko, 128u, G), kDftIdesc, 1u);
+              tc_mma_tf32(d, tc_sdesc(alo + ko, 128u, G), tc_sdesc(bhi + ko, 128u, G), kDftIdesc, 1u);
             }
           }
           tc_commit(&empty[s]);
-          tc_commit(&sfree[s]);
+          tc_commit(&sfree[b]);
         }
         if (ok) tc_commit(&tfull[tb]);
       }
@@ -366,15 +373,15 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
     bool ok = true;
     for (long long tile = blockIdx.x; tile < ntiles && ok && !*ab; tile += gridDim.x)
       for (int c = 0; c < nch; ++c, ++q) {
-        const int s = q & 1, r = (int)(q >> 1);
+        const int s = (int)(q % kTcStages), b = (int)(q & 1), rb = (int)(q >> 1);
         int got = 1;
         if (lane == 0) {
-          got = tc_wait(&full[s], r & 1, a.status, ab) ? 1 : 0;
-          if (got && r > 0) got = tc_wait(&sfree[s], (r & 1) ^ 1, a.status, ab) ? 1 : 0;
+          got = tc_wait(&full[s], (q / kTcStages) & 1, a.status, ab) ? 1 : 0;
+          if (got && rb > 0) got = tc_wait(&sfree[b], (rb & 1) ^ 1, a.status, ab) ? 1 : 0;
         }
         if (!(ok = __shfl_sync(0xffffffffu, got, 0) != 0)) break;
         const float* vr = reinterpret_cast<const float*>(vraw + s * kTcVBytes);
-        unsigned char* hi = bspl + s * kTcSBytes;
+        unsigned char* hi = bspl + b * kTcSBytes;
         unsigned char* lo = hi + kTcImg;
 #pragma unroll
         for (int k4 = 0; k4 < kTcKC / 4; ++k4) {
@@ -393,7 +400,7 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
         fence_async_smem();  // visible to the tensor cores (async proxy)
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&sready[s]);
+          mbar_arrive(&sready[b]);
           mbar_arrive(&empty[s]);  // the samples of this stage are read
         }
       }
@@ -422,17 +429,27 @@ __global__ void __launch_bounds__(kTcDftThreads, 1)
           if (bin < a.nb) {
             if (xb + 32 <= a.N) {
               float4* dp = reinterpret_cast<float4*>(dst + xb);
+              if (a.overwrite) {
 #pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                float4 v = dp[k];
-                v.x += __uint_as_float(r[4 * k]);
-                v.y += __uint_as_float(r[4 * k + 1]);
-                v.z += __uint_as_float(r[4 * k + 2]);
-                v.w += __uint_as_float(r[4 * k + 3]);
-                dp[k] = v;
+                for (int k = 0; k < 8; ++k)
+                  dp[k] = make_float4(__uint_as_float(r[4 * k]), __uint_as_float(r[4 * k + 1]),
+                                      __uint_as_float(r[4 * k + 2]), __uint_as_float(r[4 * k + 3]));
+              } else {
+                float4 v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = dp[k];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                  v[k].x += __uint_as_float(r[4 * k]);
+                  v[k].y += __uint_as_float(r[4 * k + 1]);
+                  v[k].z += __uint_as_float(r[4 * k + 2]);
+                  v[k].w += __uint_as_float(r[4 * k + 3]);
+                  dp[k] = v[k];
+                }
               }
             } else {
-              for (int k = 0; k < 32 && xb + k < a.N; ++k) dst[xb + k] += __uint_as_float(r[k]);
+              for (int k = 0; k < 32 && xb + k < a.N; ++k)
+                dst[xb + k] = (a.overwrite ? 0.0f : dst[xb + k]) + __uint_as_float(r[k]);
             }
           }
         }
@@ -550,6 +567,8 @@ cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const
   return cudaGetLastError();
 }
 
+int dft_tc_chunk() { return kTcKC; }
+
 size_t dft_tc_image_bytes(int T, int nb) {
   const int mt = (nb + 63) / 64, nch = (T + kTcKC - 1) / kTcKC;
   return (size_t)nch * mt * 2 * kTcImg;
@@ -558,8 +577,8 @@ size_t dft_tc_image_bytes(int T, int nb) {
 bool dft_tc_supported(long long N, int nb) { return N % 4 == 0 && nb >= 1 && nb <= 64 * kTcMaxMt; }
 
 cudaError_t launch_dft_tc(const CUtensorMap& vmap, long long N, int T, int n0, int nf,
-                          const int* bins, int nb, float* W, float* re, float* im, int* status,
-                          cudaStream_t s) {
+                          const int* bins, int nb, float* W, float* re, float* im, bool overwrite,
+                          int* status, cudaStream_t s) {
   if (T <= 0 || N <= 0) return cudaSuccess;
   if (!dft_tc_supported(N, nb)) return cudaErrorInvalidValue;
   const int mt = (nb + 63) / 64, nch = (T + kTcKC - 1) / kTcKC;
@@ -573,7 +592,7 @@ cudaError_t launch_dft_tc(const CUtensorMap& vmap, long long N, int T, int n0, i
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  DftTcArgs a{W, re, im, N, nb, mt, nch, status};
+  DftTcArgs a{W, re, im, N, nb, mt, nch, overwrite ? 1 : 0, status};
   const long long ntiles = (N + kTcNP - 1) / kTcNP;
   const int grid = (int)std::min<long long>(ntiles, 152);
   dft_tc_kernel<<<grid, kTcDftThreads, kTcSmem, s>>>(vmap, a);

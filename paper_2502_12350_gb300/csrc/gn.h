@@ -14,14 +14,16 @@ cudaError_t launch_dft(const float* V, long long N, int T, int n0, int nf, const
                        float2* W, float* re, float* im, int* status, cudaStream_t s);
 // The same accumulation on the tensor cores (kind::tf32, hi / lo split, one
 // accumulator pass per call).  vmap: V viewed as 3-D {N, T, 1} FP32, box
-// {128, 32, 1}, no swizzle; W: dft_tc_image_bytes(T, nb) bytes of scratch
+// {128, dft_tc_chunk(), 1}, no swizzle; W: dft_tc_image_bytes(T, nb) bytes of scratch
 // (16-byte aligned); needs dft_tc_supported(N, nb) (N a multiple of 4, at
-// most 128 bins) and 16-byte aligned re / im.
+// most 128 bins) and 16-byte aligned re / im.  overwrite: re / im hold zeros
+// (the first block of a batch), so the sums are stored without reading them.
+int dft_tc_chunk();
 size_t dft_tc_image_bytes(int T, int nb);
 bool dft_tc_supported(long long N, int nb);
 cudaError_t launch_dft_tc(const CUtensorMap& vmap, long long N, int T, int n0, int nf,
-                          const int* bins, int nb, float* W, float* re, float* im, int* status,
-                          cudaStream_t s);
+                          const int* bins, int nb, float* W, float* re, float* im, bool overwrite,
+                          int* status, cudaStream_t s);
 // pw[k][x] += sum over the nv windows of |acc[k][v N + x]|^2, then acc = 0.
 cudaError_t launch_power(int nb, long long N, int nv, float* re, float* im, float* pw,
                          cudaStream_t s);
