@@ -253,8 +253,8 @@ int mamute_gn_diagonal(mamute_ctx* ctx, const mamute_grid* grid, const float* ve
                        const float* rho, int n_src, const float* src_xyz, const float* wavelet,
                        const int* rec_offset, const float* rec_xyz, float band_rel, float* hdiag);
 
-/* ---- Learned preconditioner network (not in the paper: the benchmark spec's
- * third training-system pattern).  A 4-layer 3x3x3 'same' CNN predicts the
+/* ---- Learned preconditioner network (not in the paper: a preconditioner
+ * learned from exact Gauss-Newton diagonals).  A 4-layer 3x3x3 'same' CNN predicts the
  * log of the Gauss-Newton diagonal from the velocity and the pseudo-Hessian.
  * All pointers are device pointers.  Activations are channels-last
  * [D][H][W][16] BF16 (unsigned short bit patterns, fewer channels zero-
