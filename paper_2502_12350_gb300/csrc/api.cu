@@ -380,9 +380,12 @@ TileChoice choose_tiles(const std::vector<VolDesc>& vols, bool dens, int mode, i
   return best;
 }
 
+// adj_mode: the adjoint kernel mode the tiles are chosen for (MODE_ADJ when
+// the forward states are recomputed, MODE_ADJ_STORED when every imaging term
+// is kept: their shared-memory footprints, hence occupancies, differ).
 int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, const float* src_xyz,
                const int* rec_offset, const float* rec_xyz, const int* aperture, Plan& P,
-               const int* tiles = nullptr) {
+               const int* tiles = nullptr, int adj_mode = MODE_ADJ) {
   if (!g) return fail(ctx, MAMUTE_EINVAL, "grid is NULL");
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->border < 0 || g->nt < 1)
     return fail(ctx, MAMUTE_EINVAL, "bad grid dimensions");
@@ -539,7 +542,7 @@ int build_plan(mamute_ctx* ctx, const mamute_grid* g, bool dens, int n_src, cons
   auto pick = [&](int i, const char* env) { return (tiles && tiles[i] > 0) ? tiles[i] : env_int(env, 0); };
   TileChoice fc = choose_tiles(P.vols, dens, fmode, n_sm, pick(0, "MAMUTE_TX"), pick(1, "MAMUTE_TY"),
                                pick(2, "MAMUTE_ZSPLIT"));
-  TileChoice ac = choose_tiles(P.vols, dens, MODE_ADJ, n_sm, pick(3, "MAMUTE_ADJ_TX"),
+  TileChoice ac = choose_tiles(P.vols, dens, adj_mode, n_sm, pick(3, "MAMUTE_ADJ_TX"),
                                pick(4, "MAMUTE_ADJ_TY"), pick(5, "MAMUTE_ADJ_ZSPLIT"));
   if (fc.tilings.empty() || ac.tilings.empty())
     return fail(ctx, MAMUTE_EINVAL, "unsupported tile shape");
@@ -1490,6 +1493,29 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
   const int smode = opts ? opts->smooth_mode : 0;
   if (smode < 0 || smode > 2) return fail(ctx, MAMUTE_EINVAL, "smooth_mode must be 0, 1 or 2");
   TRY(check_cfl(ctx, P, vel));
+  {
+    // When every step's imaging term will be kept (the storage decision
+    // below, made here ahead of it on the same figures), choose the adjoint
+    // tiles for the stored-term kernel.
+    const int ns = opts ? opts->n_snapshots : 0;
+    bool keep_all = ns < 0 || P.pml;
+    if (ns == 0 && !keep_all) {
+      size_t fr = 0, tot = 0;
+      CK(cudaMemGetInfo(&fr, &tot));
+      const double fr_ = (opts && opts->check_mem > 0.f) ? opts->check_mem : 0.8;
+      const double need = (double)P.nt * P.term_elems * 4;
+      keep_all = need <= fr_ * ((double)fr + (double)ctx->tstore.bytes + (double)ctx->slots.bytes);
+    }
+    if (keep_all) {
+      Plan Q;
+      TRY(build_plan(ctx, g, rho != nullptr, n_src, src_xyz, rec_offset, rec_xyz,
+                     opts ? opts->aperture : nullptr, Q, opts ? opts->tiles : nullptr,
+                     MODE_ADJ_STORED));
+      Q.vmax = P.vmax;
+      P = std::move(Q);
+      ctx->max_planes = P.Nz;
+    }
+  }
   const bool ph = opts && opts->phess;
   if (P.pml && ph) return fail(ctx, MAMUTE_EINVAL, "phess is not available with pml");
   if (P.pml && opts && opts->n_snapshots > 0)
