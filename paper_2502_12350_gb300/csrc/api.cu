@@ -367,6 +367,9 @@ TileChoice choose_tiles(const std::vector<VolDesc>& vols, bool dens, int mode, i
         // z-block priming reads 8 extra halo planes of one of ~4 arrays
         const double planes = (double)((Nz + zs - 1) / zs) + (zs > 1 ? 2.0 : 0.0);
         const double cost = (double)per * maxpts * planes / occ;
+        if (env_int("MAMUTE_VERBOSE", 0) >= 2)
+          fprintf(stderr, "mamute tiles: mode %d %dx%d rows x%d z%d: %d per SM, cost %.0f\n", mode, TX,
+                  TY, r, zs, per_sm, cost);
         if (best_cost < 0 || cost < best_cost * (1.0 - 1e-3)) {
           best_cost = cost;
           best.tx = TX;
