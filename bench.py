@@ -519,7 +519,7 @@ def pml_line(args, w, world, total_ms, value, e2e, vel_h, rho_h, seis_h, launche
                      "frac": achieved / peak,
                      "traffic": kernel_traffic(w, "cpml_step", PML_SOURCES),
                      "peak_kind": peak_kind,
-                     "kernel": "CPML time step (psi_kernel + step_kernel_pml + record_kernel)",
+                     "kernel": "CPML time step (per-axis Psi launches + step_kernel + per-axis correction launches + record_kernel)",
                      "bytes_per_step": alg, "step_ms": step_ms},
         "clocks": clocks,
     }

@@ -1155,6 +1155,7 @@ struct PmlTables {
   CpmlArgs base{};          // buffers and profiles; u, out, tstore, acc set per launch
   long long max_layer = 0;  // shell points of width border (largest window)
   long long max_shell = 0;  // shell points of width border + 4
+  CpmlExtent ext{};         // extents of the forward kernels' grids
 };
 
 // Profiles, the data columns' nodes and scales, and the pools (after setup()).
@@ -1168,7 +1169,11 @@ int cpml_setup(mamute_ctx* ctx, const Plan& P, const float* vel, const float* rh
     cpml_profile(V.Ny, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, by, cy);
     T.max_layer = std::max(T.max_layer, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b));
     T.max_shell = std::max(T.max_shell, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b + 4));
+    T.ext.xy = std::max(T.ext.xy, (long long)V.Nx * V.Ny);
+    T.ext.xz = std::max(T.ext.xz, (long long)V.Nx * V.Nz);
+    T.ext.yz = std::max(T.ext.yz, (long long)V.Ny * V.Nz);
   }
+  T.ext.border = P.b;
   cpml_profile(P.Nz, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bz, cz, P.zs < 0);
   std::vector<float> all;
   size_t off[6];
@@ -1239,9 +1244,11 @@ int cpml_fwd_step(mamute_ctx* ctx, const Plan& P, const PmlTables& T, const floa
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     ctx->ev0_set = true;
   }
-  CK(aux_count(ctx, launch_cpml_psi(c, nvol, T.max_layer, ctx->stream)));
+  CK(launch_cpml_psi(c, nvol, T.ext, ctx->stream));
+  ctx->launches += kCpmlAxisLaunches;
   TRY(main());
-  CK(aux_count(ctx, launch_cpml_fcorr(c, nvol, T.max_shell, ctx->stream)));
+  CK(launch_cpml_fcorr(c, nvol, T.ext, ctx->stream));
+  ctx->launches += kCpmlAxisLaunches;
   if (drow)
     CK(aux_count(ctx, launch_cpml_record(out, (const long long*)ctx->cnode.p,
                                          (const RecEntry*)ctx->crec.p, P.ncol, drow, ctx->stream)));

@@ -38,6 +38,8 @@ namespace {
 __constant__ float kC2[5] = {MAMUTE_C0, MAMUTE_C1, MAMUTE_C2, MAMUTE_C3, MAMUTE_C4};
 __constant__ float kD1[4] = {4.0f / 5.0f, -1.0f / 5.0f, 4.0f / 105.0f, -1.0f / 280.0f};
 
+constexpr int kZG = 4;  // planes per load group of the z-marching kernels
+
 struct Pt {
   int x, y, z;
 };
@@ -53,6 +55,8 @@ __device__ __forceinline__ long long axis_stride(const VolDesc& V, int a) {
 
 // Neighbours p - 4 .. p + 4 along axis a of the point at element i (zero
 // outside the window; the bounds are tested only near the window's faces).
+// No kernel writes an array that it reads this way, so the loads take the
+// read-only path and may be issued ahead of the kernel's stores.
 __device__ __forceinline__ void column(const float* f, const VolDesc& V, Pt p, int a, long long i,
                                        float (&v)[9]) {
   const int q = a == 0 ? p.x : (a == 1 ? p.y : p.z);
@@ -60,10 +64,10 @@ __device__ __forceinline__ void column(const float* f, const VolDesc& V, Pt p, i
   const long long st = axis_stride(V, a);
   if (q >= 4 && q + 4 < N) {
 #pragma unroll
-    for (int m = -4; m <= 4; ++m) v[m + 4] = f[i + m * st];
+    for (int m = -4; m <= 4; ++m) v[m + 4] = __ldg(f + i + m * st);
   } else {
 #pragma unroll
-    for (int m = -4; m <= 4; ++m) v[m + 4] = (q + m >= 0 && q + m < N) ? f[i + m * st] : 0.0f;
+    for (int m = -4; m <= 4; ++m) v[m + 4] = (q + m >= 0 && q + m < N) ? __ldg(f + i + m * st) : 0.0f;
   }
 }
 
@@ -166,40 +170,216 @@ __device__ __forceinline__ float coefA(const CpmlArgs& c, const VolDesc& V, Pt p
   return c.A[((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0)];
 }
 
-// ---------------------------------------------------------------- forward
+// The slab pair of width w across axis A (2: z, 1: y) of window V, marched
+// along A: blockIdx.z = 0 takes [0, lo), 1 takes [hi, N) with lo = min(w, N),
+// hi = max(N - w, lo); one thread per column across the other two axes (x
+// fastest), at element i0 with the marched coordinate 0 and element stride st.
+template <int A>
+struct Slab {
+  int s0, s1;
+  unsigned ncol;
+  long long st, stA;  // strides along A in the window and in the coefficient grid
+  __device__ __forceinline__ bool init(const VolDesc& V, const CpmlArgs& c, int w) {
+    const int N = A == 2 ? V.Nz : V.Ny;
+    const int lo = min(w, N), hi = max(N - w, lo);
+    s0 = blockIdx.z == 0 ? 0 : hi;
+    s1 = blockIdx.z == 0 ? lo : N;
+    ncol = (unsigned)V.Nx * (unsigned)(A == 2 ? V.Ny : V.Nz);
+    st = A == 2 ? (long long)V.Ny * V.pitch : (long long)V.pitch;
+    stA = A == 2 ? (long long)c.NyG * c.pitchG : (long long)c.pitchG;
+    return s0 < s1;
+  }
+  __device__ __forceinline__ Pt column(const VolDesc& V, unsigned q) const {
+    const unsigned o = q / (unsigned)V.Nx;
+    Pt p;
+    p.x = (int)(q - o * (unsigned)V.Nx);
+    p.y = A == 2 ? (int)o : 0;
+    p.z = A == 2 ? 0 : (int)o;
+    return p;
+  }
+  __device__ __forceinline__ static void at(Pt& p, int s) {
+    if (A == 2)
+      p.z = s;
+    else
+      p.y = s;
+  }
+  __device__ __forceinline__ static void profile(const CpmlProf& pr, const VolDesc& V, int s, float& b,
+                                                 float& cc) {
+    b = A == 2 ? pr.bz[s] : pr.by[V.gy_off + s];
+    cc = A == 2 ? pr.cz[s] : pr.cy[V.gy_off + s];
+  }
+};
 
-__global__ void psi_kernel(CpmlArgs c) {
-  const VolDesc V = c.vols[blockIdx.y];
-  for_shell(V, V.border, [&](Pt p) {
-    const long long i = idx(V, p.x, p.y, p.z);
+// Calls f(p) for every point within w cells of an x face of window V, one
+// point per thread of the blockIdx.x range (x fastest, then y, then z).
+template <typename F>
+__device__ __forceinline__ void for_xslab(const VolDesc& V, int w, F f) {
+  const int lx = min(w, V.Nx), hx = max(V.Nx - w, lx);
+  const unsigned nx3 = (unsigned)(lx + V.Nx - hx);
+  // fewer than 2^32 points (windows are checked on the host): 32-bit indices
+  const long long n = (long long)nx3 * V.Ny * V.Nz;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const unsigned q32 = (unsigned)q;
+    const unsigned r = q32 / nx3, zz = r / (unsigned)V.Ny;
+    const int xx = (int)(q32 - r * nx3);
+    Pt p;
+    p.x = xx < lx ? xx : hx + (xx - lx);
+    p.y = (int)(r - zz * (unsigned)V.Ny);
+    p.z = (int)zz;
+    f(p);
+  }
+}
+
+// f at coordinate s of the column starting at element i0 (zero outside
+// [0, N)); f is not written by the kernel that reads it this way.
+__device__ __forceinline__ float sval(const float* f, long long i0, long long st, int s, int N) {
+  return (s >= 0 && s < N) ? __ldg(f + i0 + s * st) : 0.0f;
+}
+
+__device__ __forceinline__ float d1q(const float (&v)[9]) {
+  float s = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      float b, cc;
-      prof(c.pr, V, p, a, b, cc);
-      if (in_layer(b, cc)) c.m1[a][i] = fmaf(b, c.m1[a][i], cc * d1(c.u, V, p, a, i));
+  for (int m = 1; m <= 4; ++m) s = fmaf(kD1[m - 1], v[4 + m] - v[4 - m], s);
+  return s;
+}
+
+__device__ __forceinline__ float d2q(const float (&v)[9]) {
+  float s = kC2[0] * v[4];
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) s = fmaf(kC2[m], v[4 + m] + v[4 - m], s);
+  return s;
+}
+
+__device__ __forceinline__ void shift(float (&v)[9], float next) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = v[m + 1];
+  v[8] = next;
+}
+
+// ---------------------------------------------------------------- forward
+//
+// Each axis's terms live in its own pair of layer slabs, so each update
+// runs as one launch per axis: for z and y a kernel that marches the slab
+// along the axis with one thread per column (x fastest), the neighbours
+// along the axis in register queues and the loads of kZG cells issued
+// before their stores; for x one point per thread, the x neighbours coming
+// from the same cache lines as the neighbouring threads' points.  The
+// correction adds each axis's part to u^{n+1} (and to the stored term) in
+// turn.
+
+template <int A>
+__global__ void __launch_bounds__(256, 4) psi_march_kernel(CpmlArgs c) {
+  const VolDesc V = c.vols[blockIdx.y];
+  Slab<A> S;
+  if (!S.init(V, c, V.border)) return;
+  const int N = A == 2 ? V.Nz : V.Ny;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < S.ncol; q += gridDim.x * blockDim.x) {
+    const Pt p = S.column(V, q);
+    const long long i0 = idx(V, p.x, p.y, p.z);
+    float v[9];  // u at s - 4 .. s + 4
+#pragma unroll
+    for (int m = 0; m < 9; ++m) v[m] = sval(c.u, i0, S.st, S.s0 - 4 + m, N);
+    for (int sg = S.s0; sg < S.s1; sg += kZG) {
+      float mv[kZG], un[kZG], b[kZG], cc[kZG];
+#pragma unroll
+      for (int k = 0; k < kZG; ++k) {
+        const int s = sg + k;
+        b[k] = 1.0f;
+        cc[k] = 0.0f;
+        if (s < S.s1) Slab<A>::profile(c.pr, V, s, b[k], cc[k]);
+        mv[k] = in_layer(b[k], cc[k]) ? c.m1[A][i0 + s * S.st] : 0.0f;
+        un[k] = sval(c.u, i0, S.st, s + 5, N);
+      }
+#pragma unroll
+      for (int k = 0; k < kZG; ++k) {
+        if (in_layer(b[k], cc[k])) c.m1[A][i0 + (sg + k) * S.st] = fmaf(b[k], mv[k], cc[k] * d1q(v));
+        shift(v, un[k]);
+      }
     }
+  }
+}
+
+template <int A>
+__global__ void __launch_bounds__(256, 3) fcorr_march_kernel(CpmlArgs c) {
+  const VolDesc V = c.vols[blockIdx.y];
+  Slab<A> S;
+  if (!S.init(V, c, V.border + 4)) return;
+  const int N = A == 2 ? V.Nz : V.Ny;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < S.ncol; q += gridDim.x * blockDim.x) {
+    Pt p = S.column(V, q);
+    const long long i0 = idx(V, p.x, p.y, p.z);
+    const float* Acol = c.A + ((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0);
+    float um[9], pm[9];  // u and Psi_A at s - 4 .. s + 4
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      um[m] = sval(c.u, i0, S.st, S.s0 - 4 + m, N);
+      pm[m] = sval(c.m1[A], i0, S.st, S.s0 - 4 + m, N);
+    }
+    for (int sg = S.s0; sg < S.s1; sg += kZG) {
+      float zt[kZG], o[kZG], ag[kZG], un[kZG], pn[kZG], b[kZG], cc[kZG];
+#pragma unroll
+      for (int k = 0; k < kZG; ++k) {
+        const int s = sg + k;
+        const bool in = s < S.s1;
+        b[k] = 1.0f;
+        cc[k] = 0.0f;
+        if (in) Slab<A>::profile(c.pr, V, s, b[k], cc[k]);
+        zt[k] = in_layer(b[k], cc[k]) ? c.m2[A][i0 + s * S.st] : 0.0f;
+        o[k] = in ? c.out[i0 + s * S.st] : 0.0f;
+        ag[k] = in ? __ldg(Acol + s * S.stA) : 0.0f;
+        un[k] = sval(c.u, i0, S.st, s + 5, N);
+        pn[k] = sval(c.m1[A], i0, S.st, s + 5, N);
+      }
+#pragma unroll
+      for (int k = 0; k < kZG; ++k) {
+        const int s = sg + k;
+        if (s < S.s1) {  // every slab point is within border + 4 cells of a face across A
+          const long long i = i0 + s * S.st;
+          const float d1p = d1q(pm);
+          float zn = 0.0f;
+          if (in_layer(b[k], cc[k])) {
+            zn = fmaf(b[k], zt[k], cc[k] * (d2q(um) + d1p));
+            c.m2[A][i] = zn;
+          }
+          const float d = ag[k] * (d1p + zn);
+          c.out[i] = o[k] + d;
+          if (c.tstore) {
+            Slab<A>::at(p, s);
+            const long long r = region_index(V, p);
+            if (r >= 0) c.tstore[r] += d;
+          }
+        }
+        shift(um, un[k]);
+        shift(pm, pn[k]);
+      }
+    }
+  }
+}
+
+__global__ void psi_x_kernel(CpmlArgs c) {
+  const VolDesc V = c.vols[blockIdx.y];
+  for_xslab(V, V.border, [&](Pt p) {
+    const long long i = idx(V, p.x, p.y, p.z);
+    float b, cc;
+    prof(c.pr, V, p, 0, b, cc);
+    if (in_layer(b, cc)) c.m1[0][i] = fmaf(b, c.m1[0][i], cc * d1(c.u, V, p, 0, i));
   });
 }
 
-__global__ void fcorr_kernel(CpmlArgs c) {
+__global__ void fcorr_x_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_shell(V, V.border + 4, [&](Pt p) {
+  for_xslab(V, V.border + 4, [&](Pt p) {
     const long long i = idx(V, p.x, p.y, p.z);
-    float corr = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (!near_face(V, p, a, V.border + 4)) continue;
-      const float d1p = d1(c.m1[a], V, p, a, i);
-      float b, cc;
-      prof(c.pr, V, p, a, b, cc);
-      float zt = 0.0f;
-      if (in_layer(b, cc)) {
-        zt = fmaf(b, c.m2[a][i], cc * (d2(c.u, V, p, a, i) + d1p));
-        c.m2[a][i] = zt;
-      }
-      corr += d1p + zt;
+    const float d1p = d1(c.m1[0], V, p, 0, i);
+    float b, cc;
+    prof(c.pr, V, p, 0, b, cc);
+    float zt = 0.0f;
+    if (in_layer(b, cc)) {
+      zt = fmaf(b, c.m2[0][i], cc * (d2(c.u, V, p, 0, i) + d1p));
+      c.m2[0][i] = zt;
     }
-    const float d = coefA(c, V, p) * corr;
+    const float d = coefA(c, V, p) * (d1p + zt);
     c.out[i] += d;
     if (c.tstore) {
       const long long r = region_index(V, p);
@@ -280,13 +460,23 @@ long long cpml_shell_points(int Nx, int Ny, int Nz, int w) {
   return (long long)Nx * Ny * Nz - inner(Nx) * inner(Ny) * inner(Nz);
 }
 
-cudaError_t launch_cpml_psi(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s) {
-  psi_kernel<<<grid_for(n_vol, max_layer), 256, 0, s>>>(c);
+// Both slabs of a marched axis (blockIdx.z), one thread per column.
+dim3 march_grid(int n_vol, long long max_cols) {
+  const long long b = std::min((max_cols + 255) / 256, 65535LL);
+  return dim3((unsigned)std::max(1LL, b), (unsigned)n_vol, 2);
+}
+
+cudaError_t launch_cpml_psi(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s) {
+  psi_march_kernel<2><<<march_grid(n_vol, e.xy), 256, 0, s>>>(c);
+  psi_march_kernel<1><<<march_grid(n_vol, e.xz), 256, 0, s>>>(c);
+  psi_x_kernel<<<grid_for(n_vol, 2LL * e.border * e.yz), 256, 0, s>>>(c);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cpml_fcorr(const CpmlArgs& c, int n_vol, long long max_shell, cudaStream_t s) {
-  fcorr_kernel<<<grid_for(n_vol, max_shell), 256, 0, s>>>(c);
+cudaError_t launch_cpml_fcorr(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s) {
+  fcorr_march_kernel<2><<<march_grid(n_vol, e.xy), 256, 0, s>>>(c);
+  fcorr_march_kernel<1><<<march_grid(n_vol, e.xz), 256, 0, s>>>(c);
+  fcorr_x_kernel<<<grid_for(n_vol, 2LL * (e.border + 4) * e.yz), 256, 0, s>>>(c);
   return cudaGetLastError();
 }
 

@@ -43,11 +43,19 @@ struct CpmlArgs {
   float* acc;          // reverse: imaging accumulator (pool layout, corrected in place)
 };
 
-// Forward, before the main step: Psi_a <- b_a Psi_a + c_a D1_a u^n in the layer.
-cudaError_t launch_cpml_psi(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s);
+// Largest extents over the shot windows, for the grids of the forward kernels.
+struct CpmlExtent {
+  long long xy, xz, yz;  // Nx Ny, Nx Nz and Ny Nz of a window
+  int border;            // layer width in cells
+};
+
+// Forward, before the main step: Psi_a <- b_a Psi_a + c_a D1_a u^n in the layer
+// (one launch per axis: kCpmlAxisLaunches).
+cudaError_t launch_cpml_psi(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s);
 // Forward, after the main step: Zeta_a <- b_a Zeta_a + c_a (D2_a u^n + D1_a Psi_a) in the layer,
-// u^{n+1} += A sum_a (D1_a Psi_a + Zeta_a) and the stored term likewise.
-cudaError_t launch_cpml_fcorr(const CpmlArgs& c, int n_vol, long long max_shell, cudaStream_t s);
+// u^{n+1} += A sum_a (D1_a Psi_a + Zeta_a) and the stored term likewise (one launch per axis).
+cudaError_t launch_cpml_fcorr(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s);
+constexpr int kCpmlAxisLaunches = 3;
 // Reverse, before the main adjoint step: y_a, the Zeta multipliers, then p_a,
 // the Psi multipliers and z_a, from the level psi^{k+1} (two launches).
 cudaError_t launch_cpml_pre(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s);
