@@ -1461,7 +1461,7 @@ int run_model(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const flo
     }
     const int loop = pairs ? (P.nt / 2 + P.nt % 2) : P.nt;
     ctx->step_launches = loop;
-    ctx->launches += loop * (P.pml ? (P.ncol > 0 ? 4 : 3) : 1) +
+    ctx->launches += loop * (P.pml ? 2 * kCpmlAxisLaunches + (P.ncol > 0 ? 2 : 1) : 1) +
                      (stream_out ? std::min(P.nt, 8) * (P.one_node ? 1 : 2) : 0);
   }
 loop_done:

@@ -231,3 +231,32 @@ def test_invalid_combinations(ctx):
     with pytest.raises(mamute.MamuteError) as e:
         ctx.model(mamute.grid_of(w, pml=1, pml_r=1.5), vel, None, *geo, seis)
     assert e.value.code == mamute.EINVAL
+
+
+def _last_launches(lib, h):
+    ms, sl, tl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+    assert lib.mamute_ctx_last_timing(h, ctypes.byref(ms), ctypes.byref(sl), ctypes.byref(tl)) == 0
+    return sl.value, tl.value
+
+
+def test_graph_replay_matches_direct_launches(ctx, monkeypatch):
+    """The captured time loop and direct launches give the same seismograms
+    bit for bit and report the same kernel launch counts (eight per step:
+    three Psi launches, the main step, three correction launches, the
+    receiver samples)."""
+    from paper_2502_12350_gb300 import mamute
+    lib = mamute.load()
+    w = synth.small_case(**CASES[0])
+    lib.mamute_ctx_set_timing(ctx._h, 1)
+    try:
+        runs = {}
+        for graphs in ("1", "0"):
+            monkeypatch.setenv("MAMUTE_GRAPHS", graphs)
+            runs[graphs] = (gpu_model(ctx, w), _last_launches(lib, ctx._h))
+    finally:
+        lib.mamute_ctx_set_timing(ctx._h, 0)
+    np.testing.assert_array_equal(runs["1"][0], runs["0"][0])
+    assert runs["1"][1] == runs["0"][1]
+    steps, total = runs["0"][1]
+    assert steps == w.nt
+    assert total >= 8 * w.nt
