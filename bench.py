@@ -222,9 +222,13 @@ def run_reference(args):
 
 GRAD_FWD_BYTES = (16, 4)  # per padded point (u^n, u^{n-1}, A, new level), per interior point (term store)
 GRAD_ADJ_BYTES = (24, 4)  # per padded point (psi levels, A, accumulator read + write), per interior point (term read)
+# CPML gradient, per (point, axis) pair of a layer: forward Psi_a, Zeta_a read and
+# written; reverse their multipliers read and written and the scratch y_a, z_a
+# written and read
+PML_GRAD_PAIR_BYTES = (16, 32)
 
 
-def gradient_metrics(workload, steps, warmup, autotune=False, snapshots=0, nt=None):
+def gradient_metrics(workload, steps, warmup, autotune=False, snapshots=0, nt=None, pml=False):
     """FWI gradient throughput through mamute_gradient on one GPU: shots/s,
     Gpt-updates/s of forward + adjoint work, CUDA-event time on the library's
     stream, and the step loop's bandwidth against the algorithmic bytes of
@@ -232,7 +236,9 @@ def gradient_metrics(workload, steps, warmup, autotune=False, snapshots=0, nt=No
     the new level, 16 B per padded point, and stores the imaging term, 4 B
     per interior point; each adjoint step reads two psi levels and A, writes
     the new level, reads and writes the accumulator, 24 B per padded point,
-    and reads the stored term, 4 B per interior point)."""
+    and reads the stored term, 4 B per interior point).  With pml, the
+    convolutional PML instead of the sponge (every imaging term kept), plus
+    PML_GRAD_PAIR_BYTES per (point, axis) pair of the layers."""
     import ctypes
 
     import torch
@@ -244,7 +250,7 @@ def gradient_metrics(workload, steps, warmup, autotune=False, snapshots=0, nt=No
         w = synth.gradient_single() if nt is None else synth.gradient_single(nt=nt)
     else:
         w = synth.batched_shots() if nt is None else synth.batched_shots(nt=nt)
-    g = mamute.grid_of(w)
+    g = mamute.grid_of(w, cerjan=0.0, pml=1) if pml else mamute.grid_of(w)
     stream = torch.cuda.current_stream(dev)
     ctx = mamute.Context(0, stream.cuda_stream)
     lib = mamute.load()
@@ -312,11 +318,16 @@ def gradient_metrics(workload, steps, warmup, autotune=False, snapshots=0, nt=No
         byts = w.nt * sum(GRAD_FWD_BYTES[0] * p + GRAD_FWD_BYTES[1] * q +
                           GRAD_ADJ_BYTES[0] * p + GRAD_ADJ_BYTES[1] * q
                           for p, q in zip(pts_shot, int_shot))
+        if pml:
+            Nx, Ny, Nz = w.nx + 2 * w.border, w.ny + 2 * w.border, w.nz + 2 * w.border
+            pairs = 2 * w.border * (Ny * Nz + Nx * Nz + Nx * Ny) * w.n_src
+            byts += w.nt * sum(PML_GRAD_PAIR_BYTES) * pairs
         lms = statistics.median(loop_ms)
         ach = byts / (lms / 1e3) / 1e9
         out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                            "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
-                           "kernel": "step_kernel<forward+store> and step_kernel<adjoint, stored term>",
+                           "kernel": "step_kernel<forward+store> and step_kernel<adjoint, stored term>" +
+                                     (" with the per-axis CPML kernels" if pml else ""),
                            "algorithmic_bytes_per_gradient": byts, "loop_ms": lms,
                            "bytes_per_point": {"forward": list(GRAD_FWD_BYTES),
                                                "adjoint": list(GRAD_ADJ_BYTES)}}
@@ -328,14 +339,15 @@ def run_gradient_bench(args):
     """FWI gradient throughput (shots/s and Gpt-updates/s of forward + adjoint
     work) through mamute_gradient, on one GPU."""
     gm = gradient_metrics(args.workload, args.steps, args.warmup, args.autotune, args.snapshots,
-                          args.nt)
+                          args.nt, pml=args.boundary == "pml")
     line = {"metric": "FWI gradient shots/s", "value": gm["value"], "unit": "shots/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": gm["ms_per_gradient"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {k: gm[k] for k in ("workload", "shots", "nt", "points_per_step",
-                                          "snapshots", "storage", "tiles",
-                                          "step_launches_per_gradient")},
+            "config": dict({k: gm[k] for k in ("workload", "shots", "nt", "points_per_step",
+                                               "snapshots", "storage", "tiles",
+                                               "step_launches_per_gradient")},
+                           boundary="convolutional PML" if args.boundary == "pml" else "sponge"),
             "gpt_updates_per_s": gm["gpt_updates_per_s"], "misfit": gm["misfit"],
             "gpu_launches": gm["gpu_launches"], "clocks": gm["clocks"]}
     if "roofline" in gm:
@@ -559,7 +571,8 @@ def main():
     ap.add_argument("--time-blocking", type=int, default=0, choices=[0, 2],
                     help="model workloads: 2 = two time steps per launch (two-level kernel)")
     ap.add_argument("--boundary", default="sponge", choices=["sponge", "pml"],
-                    help="model workloads: absorbing boundary (pml: convolutional PML)")
+                    help="model and gradient_single workloads: absorbing boundary (pml: "
+                         "convolutional PML)")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the 256^3 FWI gradient object of the headline line")
     ap.add_argument("--workload", default="model",

@@ -1153,9 +1153,7 @@ constexpr int kPmlPoolsModel = 6, kPmlPoolsGradient = 12;
 
 struct PmlTables {
   CpmlArgs base{};          // buffers and profiles; u, out, tstore, acc set per launch
-  long long max_layer = 0;  // shell points of width border (largest window)
-  long long max_shell = 0;  // shell points of width border + 4
-  CpmlExtent ext{};         // extents of the forward kernels' grids
+  CpmlExtent ext{};         // extents of the kernels' grids
 };
 
 // Profiles, the data columns' nodes and scales, and the pools (after setup()).
@@ -1167,8 +1165,6 @@ int cpml_setup(mamute_ctx* ctx, const Plan& P, const float* vel, const float* rh
       return fail(ctx, MAMUTE_EINVAL, "pml: a shot window of 2^32 points or more");
     cpml_profile(V.Nx, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, bx, cx);
     cpml_profile(V.Ny, P.b, P.h, P.dt, P.vmax, P.pml_f0, P.pml_r, by, cy);
-    T.max_layer = std::max(T.max_layer, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b));
-    T.max_shell = std::max(T.max_shell, cpml_shell_points(V.Nx, V.Ny, V.Nz, P.b + 4));
     T.ext.xy = std::max(T.ext.xy, (long long)V.Nx * V.Ny);
     T.ext.xz = std::max(T.ext.xz, (long long)V.Nx * V.Nz);
     T.ext.yz = std::max(T.ext.yz, (long long)V.Ny * V.Nz);
@@ -1754,8 +1750,8 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
     if (P.pml) {  // memory-variable multipliers from psi^{k+1}
       CpmlArgs c = T.base;
       c.u = (const float*)ctx->psi[(k + 1) & 1].p;
-      CK(aux_count(ctx, launch_cpml_pre(c, nvol, T.max_layer, ctx->stream)));
-      ++ctx->launches;
+      CK(launch_cpml_pre(c, nvol, T.ext, ctx->stream));
+      ctx->launches += kCpmlPreLaunches;
     }
     CK(step_launch(ctx, a, (int)P.aitems.size(), P.atx, P.aty, P.dens,
                    all_mode ? MODE_ADJ_STORED : MODE_ADJ));
@@ -1765,7 +1761,8 @@ int run_gradient(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const 
       c.out = (float*)ctx->psi[k & 1].p;
       c.tstore = (float*)ctx->tstore.p + (size_t)i * P.term_elems;
       c.acc = (float*)ctx->acc.p;
-      CK(aux_count(ctx, launch_cpml_acorr(c, nvol, T.max_shell, ctx->stream)));
+      CK(launch_cpml_acorr(c, nvol, T.ext, ctx->stream));
+      ctx->launches += kCpmlAxisLaunches;
       if (ctx->timing) CK(cudaEventRecord(ctx->ev1, ctx->stream));
     }
     return MAMUTE_OK;

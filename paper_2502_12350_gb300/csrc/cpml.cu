@@ -38,7 +38,7 @@ namespace {
 __constant__ float kC2[5] = {MAMUTE_C0, MAMUTE_C1, MAMUTE_C2, MAMUTE_C3, MAMUTE_C4};
 __constant__ float kD1[4] = {4.0f / 5.0f, -1.0f / 5.0f, 4.0f / 105.0f, -1.0f / 280.0f};
 
-constexpr int kZG = 4;  // planes per load group of the z-marching kernels
+constexpr int kZG = 4;  // cells per load group of the marching kernels
 
 struct Pt {
   int x, y, z;
@@ -105,60 +105,6 @@ __device__ __forceinline__ void prof(const CpmlProf& c, const VolDesc& V, Pt p, 
 
 __device__ __forceinline__ bool in_layer(float b, float cc) { return cc != 0.0f || b != 1.0f; }
 
-// Within w cells of a face of the window along axis a.
-__device__ __forceinline__ bool near_face(const VolDesc& V, Pt p, int a, int w) {
-  const int q = a == 0 ? p.x : (a == 1 ? p.y : p.z);
-  const int N = a == 0 ? V.Nx : (a == 1 ? V.Ny : V.Nz);
-  return q < w || q >= N - w;
-}
-
-// Calls f(p) for every point of the shell of width w of window V, one point
-// per thread of the blockIdx.x range: the z slabs (all y, x), then the y
-// slabs of the middle planes, then the x slabs of the middle rows.
-template <typename F>
-__device__ __forceinline__ void for_shell(const VolDesc& V, int w, F f) {
-  const int lz = min(w, V.Nz), hz = max(V.Nz - w, lz);
-  const int ly = min(w, V.Ny), hy = max(V.Ny - w, ly);
-  const int lx = min(w, V.Nx), hx = max(V.Nx - w, lx);
-  const long long nxy = (long long)V.Nx * V.Ny;
-  const long long n1 = (long long)(lz + V.Nz - hz) * nxy;
-  const int ny2 = ly + V.Ny - hy, midz = hz - lz, midy = hy - ly, nx3 = lx + V.Nx - hx;
-  const long long n2 = (long long)midz * ny2 * V.Nx;
-  const long long n3 = (long long)midz * midy * nx3;
-  const long long n = n1 + n2 + n3;
-  // each region has fewer than 2^32 points (windows are checked on the
-  // host), so the index arithmetic runs in 32 bits
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    Pt p;
-    if (q < n1) {
-      const unsigned r0 = (unsigned)q;
-      const unsigned r = r0 / (unsigned)V.Nx;
-      p.x = (int)(r0 - r * (unsigned)V.Nx);
-      const unsigned zz = r / (unsigned)V.Ny;
-      p.y = (int)(r - zz * (unsigned)V.Ny);
-      p.z = (int)zz < lz ? (int)zz : hz + ((int)zz - lz);
-    } else if (q < n1 + n2) {
-      const unsigned r0 = (unsigned)(q - n1);
-      const unsigned r = r0 / (unsigned)V.Nx;
-      p.x = (int)(r0 - r * (unsigned)V.Nx);
-      const unsigned zm = r / (unsigned)ny2;
-      const int yy = (int)(r - zm * (unsigned)ny2);
-      p.y = yy < ly ? yy : hy + (yy - ly);
-      p.z = lz + (int)zm;
-    } else {
-      const unsigned r0 = (unsigned)(q - n1 - n2);
-      const unsigned r = r0 / (unsigned)nx3;
-      const int xx = (int)(r0 - r * (unsigned)nx3);
-      p.x = xx < lx ? xx : hx + (xx - lx);
-      const unsigned zm = r / (unsigned)midy;
-      p.y = ly + (int)(r - zm * (unsigned)midy);
-      p.z = lz + (int)zm;
-    }
-    f(p);
-  }
-}
-
 // Index of p in the imaging-region layout, or -1 outside the region.
 __device__ __forceinline__ long long region_index(const VolDesc& V, Pt p) {
   const int zi = p.z - V.border, yi = p.y - V.iy0, xi = p.x - V.ix0;
@@ -166,24 +112,28 @@ __device__ __forceinline__ long long region_index(const VolDesc& V, Pt p) {
   return V.toff + ((long long)zi * V.nyi + yi) * V.tpitch + (p.x - V.txoff);
 }
 
-__device__ __forceinline__ float coefA(const CpmlArgs& c, const VolDesc& V, Pt p) {
-  return c.A[((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0)];
-}
-
 // The slab pair of width w across axis A (2: z, 1: y) of window V, marched
 // along A: blockIdx.z = 0 takes [0, lo), 1 takes [hi, N) with lo = min(w, N),
 // hi = max(N - w, lo); one thread per column across the other two axes (x
 // fastest), at element i0 with the marched coordinate 0 and element stride st.
+// With merge, slabs less than 8 cells apart are marched as one range [0, N)
+// by the blockIdx.z = 0 threads (for kernels whose queues reach 4 cells past
+// their range into values that the range's own march writes).
 template <int A>
 struct Slab {
   int s0, s1;
   unsigned ncol;
   long long st, stA;  // strides along A in the window and in the coefficient grid
-  __device__ __forceinline__ bool init(const VolDesc& V, const CpmlArgs& c, int w) {
+  __device__ __forceinline__ bool init(const VolDesc& V, const CpmlArgs& c, int w,
+                                       bool merge = false) {
     const int N = A == 2 ? V.Nz : V.Ny;
     const int lo = min(w, N), hi = max(N - w, lo);
     s0 = blockIdx.z == 0 ? 0 : hi;
     s1 = blockIdx.z == 0 ? lo : N;
+    if (merge && hi - lo < 8) {
+      s0 = 0;
+      s1 = blockIdx.z == 0 ? N : 0;
+    }
     ncol = (unsigned)V.Nx * (unsigned)(A == 2 ? V.Ny : V.Nz);
     st = A == 2 ? (long long)V.Ny * V.pitch : (long long)V.pitch;
     stA = A == 2 ? (long long)c.NyG * c.pitchG : (long long)c.pitchG;
@@ -255,6 +205,10 @@ __device__ __forceinline__ void shift(float (&v)[9], float next) {
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = v[m + 1];
   v[8] = next;
+}
+
+__device__ __forceinline__ float coefA(const CpmlArgs& c, const VolDesc& V, Pt p) {
+  return c.A[((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0)];
 }
 
 // ---------------------------------------------------------------- forward
@@ -395,51 +349,165 @@ __global__ void record_kernel(const float* __restrict__ u, const long long* __re
 }
 
 // ---------------------------------------------------------------- reverse
+//
+// One launch per axis and update, as in the forward pass.  For z and y one
+// marched kernel forms both multipliers: y_a is pointwise, so it is made as
+// each cell enters the register queue (its Zeta multiplier updated in the
+// same place), and p_a once the cell's neighbours along a are in the queue.
+// Where the two layers along a are less than 8 cells apart, one thread
+// marches the whole column, so that no queue reads a y_a another thread is
+// making.  For x, y_x comes from a pointwise kernel and p_x from one point
+// per thread.  The correction adds each axis's part to psi^k and to the
+// imaging accumulator in turn.
 
-__global__ void y_kernel(CpmlArgs c) {
+// Profile of cell s along A (b = 1, c = 0 outside the window).
+template <int A>
+__device__ __forceinline__ void prof_at(const CpmlProf& pr, const VolDesc& V, int N, int s, float& b,
+                                        float& cc) {
+  b = 1.0f;
+  cc = 0.0f;
+  if (s >= 0 && s < N) Slab<A>::profile(pr, V, s, b, cc);
+}
+
+template <int A>
+__global__ void __launch_bounds__(256, 2) pre_march_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_shell(V, V.border, [&](Pt p) {
-    const long long i = idx(V, p.x, p.y, p.z);
-    const float psi = c.u[i];
+  Slab<A> S;
+  if (!S.init(V, c, V.border, true)) return;
+  const int N = A == 2 ? V.Nz : V.Ny;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < S.ncol; q += gridDim.x * blockDim.x) {
+    const Pt p = S.column(V, q);
+    const long long i0 = idx(V, p.x, p.y, p.z);
+    // y_A of a cell entering the queue, c (Zb + psi) with Zb <- b (Zb + psi)
+    // in the layer, zero elsewhere (zb: the cell's Zeta multiplier)
+    auto enter = [&](int s, float psi, float zb, float b, float cc) -> float {
+      if (!in_layer(b, cc)) return 0.0f;
+      const long long i = i0 + s * S.st;
+      const float zt = zb + psi;
+      const float y = cc * zt;
+      c.y[A][i] = y;
+      c.m2[A][i] = b * zt;
+      return y;
+    };
+    float ps[9], yq[9];  // psi^{k+1} and y_A at s - 4 .. s + 4
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int m = 0; m < 9; ++m) {
+      const int s = S.s0 - 4 + m;
       float b, cc;
-      prof(c.pr, V, p, a, b, cc);
-      if (in_layer(b, cc)) {
-        const float zt = c.m2[a][i] + psi;
-        c.y[a][i] = cc * zt;
-        c.m2[a][i] = b * zt;
+      prof_at<A>(c.pr, V, N, s, b, cc);
+      ps[m] = sval(c.u, i0, S.st, s, N);
+      const float zb = in_layer(b, cc) ? c.m2[A][i0 + s * S.st] : 0.0f;
+      yq[m] = enter(s, ps[m], zb, b, cc);
+    }
+    for (int sg = S.s0; sg < S.s1; sg += kZG) {
+      // loads of the group: the cells entering (sg + 5 ..) and finishing (sg ..)
+      float pn[kZG], zb[kZG], be[kZG], ce[kZG], mv[kZG], bf[kZG], cf[kZG];
+#pragma unroll
+      for (int k = 0; k < kZG; ++k) {
+        const int e = sg + 5 + k, f = sg + k;
+        prof_at<A>(c.pr, V, N, e, be[k], ce[k]);
+        pn[k] = sval(c.u, i0, S.st, e, N);
+        zb[k] = in_layer(be[k], ce[k]) ? c.m2[A][i0 + e * S.st] : 0.0f;
+        prof_at<A>(c.pr, V, f < S.s1 ? N : 0, f, bf[k], cf[k]);
+        mv[k] = in_layer(bf[k], cf[k]) ? c.m1[A][i0 + f * S.st] : 0.0f;
       }
+#pragma unroll
+      for (int k = 0; k < kZG; ++k) {
+        if (in_layer(bf[k], cf[k])) {
+          const long long i = i0 + (sg + k) * S.st;
+          const float pt = mv[k] - (d1q(ps) + d1q(yq));
+          c.m1[A][i] = bf[k] * pt;
+          c.z[A][i] = cf[k] * pt;
+        }
+        const float ye = enter(sg + 5 + k, pn[k], zb[k], be[k], ce[k]);
+        shift(ps, pn[k]);
+        shift(yq, ye);
+      }
+    }
+  }
+}
+
+template <int A>
+__global__ void __launch_bounds__(256, 3) acorr_march_kernel(CpmlArgs c) {
+  const VolDesc V = c.vols[blockIdx.y];
+  Slab<A> S;
+  if (!S.init(V, c, V.border + 4)) return;
+  const int N = A == 2 ? V.Nz : V.Ny;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < S.ncol; q += gridDim.x * blockDim.x) {
+    Pt p = S.column(V, q);
+    const long long i0 = idx(V, p.x, p.y, p.z);
+    const float* Acol = c.A + ((long long)p.z * c.NyG + (p.y + V.cy0)) * c.pitchG + (p.x + V.cx0);
+    float yq[9], zq[9];  // y_A and z_A at s - 4 .. s + 4
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      yq[m] = sval(c.y[A], i0, S.st, S.s0 - 4 + m, N);
+      zq[m] = sval(c.z[A], i0, S.st, S.s0 - 4 + m, N);
+    }
+    for (int sg = S.s0; sg < S.s1; sg += kZG) {
+      float yn[kZG], zn[kZG], o[kZG], ac[kZG], ag[kZG], ts[kZG];
+      long long r[kZG];
+#pragma unroll
+      for (int k = 0; k < kZG; ++k) {
+        const int f = sg + k;
+        const bool in = f < S.s1;
+        const long long i = i0 + f * S.st;
+        yn[k] = sval(c.y[A], i0, S.st, f + 5, N);
+        zn[k] = sval(c.z[A], i0, S.st, f + 5, N);
+        o[k] = in ? c.out[i] : 0.0f;
+        ag[k] = in ? __ldg(Acol + f * S.stA) : 0.0f;
+        Slab<A>::at(p, f);
+        r[k] = in ? region_index(V, p) : -1;
+        ts[k] = r[k] >= 0 ? __ldg(c.tstore + r[k]) : 0.0f;
+        ac[k] = r[k] >= 0 ? c.acc[i] : 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < kZG; ++k) {
+        if (sg + k < S.s1) {  // every slab point is within border + 4 cells of a face across A
+          const long long i = i0 + (sg + k) * S.st;
+          const float d = ag[k] * (d2q(yq) - d1q(zq));
+          c.out[i] = o[k] + d;
+          if (r[k] >= 0) c.acc[i] = fmaf(d, ts[k], ac[k]);
+        }
+        shift(yq, yn[k]);
+        shift(zq, zn[k]);
+      }
+    }
+  }
+}
+
+__global__ void y_x_kernel(CpmlArgs c) {
+  const VolDesc V = c.vols[blockIdx.y];
+  for_xslab(V, V.border, [&](Pt p) {
+    const long long i = idx(V, p.x, p.y, p.z);
+    float b, cc;
+    prof(c.pr, V, p, 0, b, cc);
+    if (in_layer(b, cc)) {
+      const float zt = c.m2[0][i] + c.u[i];
+      c.y[0][i] = cc * zt;
+      c.m2[0][i] = b * zt;
     }
   });
 }
 
-__global__ void z_kernel(CpmlArgs c) {
+__global__ void z_x_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_shell(V, V.border, [&](Pt p) {
+  for_xslab(V, V.border, [&](Pt p) {
     const long long i = idx(V, p.x, p.y, p.z);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      float b, cc;
-      prof(c.pr, V, p, a, b, cc);
-      if (in_layer(b, cc)) {
-        const float pt = c.m1[a][i] - (d1(c.u, V, p, a, i) + d1(c.y[a], V, p, a, i));
-        c.m1[a][i] = b * pt;
-        c.z[a][i] = cc * pt;
-      }
+    float b, cc;
+    prof(c.pr, V, p, 0, b, cc);
+    if (in_layer(b, cc)) {
+      const float pt = c.m1[0][i] - (d1(c.u, V, p, 0, i) + d1(c.y[0], V, p, 0, i));
+      c.m1[0][i] = b * pt;
+      c.z[0][i] = cc * pt;
     }
   });
 }
 
-__global__ void acorr_kernel(CpmlArgs c) {
+__global__ void acorr_x_kernel(CpmlArgs c) {
   const VolDesc V = c.vols[blockIdx.y];
-  for_shell(V, V.border + 4, [&](Pt p) {
+  for_xslab(V, V.border + 4, [&](Pt p) {
     const long long i = idx(V, p.x, p.y, p.z);
-    float corr = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (near_face(V, p, a, V.border + 4)) corr += d2(c.y[a], V, p, a, i) - d1(c.z[a], V, p, a, i);
-    const float d = coefA(c, V, p) * corr;
+    const float d = coefA(c, V, p) * (d2(c.y[0], V, p, 0, i) - d1(c.z[0], V, p, 0, i));
     c.out[i] += d;
     const long long r = region_index(V, p);
     if (r >= 0) c.acc[i] = fmaf(d, c.tstore[r], c.acc[i]);
@@ -454,11 +522,6 @@ dim3 grid_for(int n_vol, long long max_pts) {
 }
 
 }  // namespace
-
-long long cpml_shell_points(int Nx, int Ny, int Nz, int w) {
-  auto inner = [&](int N) { return (long long)std::max(0, N - 2 * w); };
-  return (long long)Nx * Ny * Nz - inner(Nx) * inner(Ny) * inner(Nz);
-}
 
 // Both slabs of a marched axis (blockIdx.z), one thread per column.
 dim3 march_grid(int n_vol, long long max_cols) {
@@ -480,17 +543,19 @@ cudaError_t launch_cpml_fcorr(const CpmlArgs& c, int n_vol, const CpmlExtent& e,
   return cudaGetLastError();
 }
 
-cudaError_t launch_cpml_pre(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s) {
-  const dim3 g = grid_for(n_vol, max_layer);
-  y_kernel<<<g, 256, 0, s>>>(c);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  z_kernel<<<g, 256, 0, s>>>(c);
+cudaError_t launch_cpml_pre(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s) {
+  pre_march_kernel<2><<<march_grid(n_vol, e.xy), 256, 0, s>>>(c);
+  pre_march_kernel<1><<<march_grid(n_vol, e.xz), 256, 0, s>>>(c);
+  const dim3 g = grid_for(n_vol, 2LL * e.border * e.yz);
+  y_x_kernel<<<g, 256, 0, s>>>(c);
+  z_x_kernel<<<g, 256, 0, s>>>(c);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cpml_acorr(const CpmlArgs& c, int n_vol, long long max_shell, cudaStream_t s) {
-  acorr_kernel<<<grid_for(n_vol, max_shell), 256, 0, s>>>(c);
+cudaError_t launch_cpml_acorr(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s) {
+  acorr_march_kernel<2><<<march_grid(n_vol, e.xy), 256, 0, s>>>(c);
+  acorr_march_kernel<1><<<march_grid(n_vol, e.xz), 256, 0, s>>>(c);
+  acorr_x_kernel<<<grid_for(n_vol, 2LL * (e.border + 4) * e.yz), 256, 0, s>>>(c);
   return cudaGetLastError();
 }
 

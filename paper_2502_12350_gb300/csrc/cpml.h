@@ -2,10 +2,10 @@
 //
 // The CPML scheme is run as the damping-free main step (the TMA stencil
 // kernels with g = 1, which form the whole update away from the layer) plus
-// these kernels, which touch only the shell of each shot window where the
-// memory variables live or are read: the `border` layer cells of each face,
-// and 4 more cells inward where the eighth-order derivatives of the memory
-// variables reach.
+// these kernels, which touch only the layer slabs of each shot window where
+// the memory variables live or are read: per axis the `border` layer cells
+// of its two faces, and 4 more cells inward where the eighth-order
+// derivatives of the memory variables reach.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -57,16 +57,15 @@ cudaError_t launch_cpml_psi(const CpmlArgs& c, int n_vol, const CpmlExtent& e, c
 cudaError_t launch_cpml_fcorr(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s);
 constexpr int kCpmlAxisLaunches = 3;
 // Reverse, before the main adjoint step: y_a, the Zeta multipliers, then p_a,
-// the Psi multipliers and z_a, from the level psi^{k+1} (two launches).
-cudaError_t launch_cpml_pre(const CpmlArgs& c, int n_vol, long long max_layer, cudaStream_t s);
+// the Psi multipliers and z_a, from the level psi^{k+1} (kCpmlPreLaunches
+// launches: the marched z and y kernels, then y_x and p_x).
+cudaError_t launch_cpml_pre(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s);
+constexpr int kCpmlPreLaunches = 4;
 // Reverse, after the main adjoint step: psi^k += A sum_a (D2_a y_a - D1_a z_a)
-// and the imaging accumulator likewise.
-cudaError_t launch_cpml_acorr(const CpmlArgs& c, int n_vol, long long max_shell, cudaStream_t s);
+// and the imaging accumulator likewise (one launch per axis).
+cudaError_t launch_cpml_acorr(const CpmlArgs& c, int n_vol, const CpmlExtent& e, cudaStream_t s);
 // dout[c] = rec[c].fscale * u[node[c]] for the ncol internal data columns.
 cudaError_t launch_cpml_record(const float* u, const long long* node, const RecEntry* rec, int ncol,
                                float* dout, cudaStream_t s);
-
-// Points of the shell of width w (per face) of an Nx x Ny x Nz window.
-long long cpml_shell_points(int Nx, int Ny, int Nz, int w);
 
 }  // namespace mamute
