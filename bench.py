@@ -422,6 +422,73 @@ def run_cnn_bench(args):
     return 0
 
 
+def run_postproc_bench(args):
+    """Gradient smoothing and data time resampling (mamute_smooth,
+    mamute_resample) on one GPU: CUDA-event time per API call, inputs resident
+    on the device.  Smoothing: Bessel and Laplace filters of the 600x600x200
+    gradient of the 64-shot workload, a forward and an inverse dense DCT-II
+    pass per axis of 2 n_a flops per point (FP32 ALU bound: 152 SMs x 128
+    lanes x 2 flops x 2.07 GHz).  Resampling: sinc, 65,536 traces of 4000
+    samples to 1000 (the headline's receivers), every input sample read and
+    every output sample written once; the host builds the CSR matrix inside
+    each call."""
+    import torch
+
+    from paper_2502_12350_gb300 import build, mamute
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = mamute.Context(0, stream.cuda_stream)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+
+    def per_call_ms(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    nx, ny, nz, h = 600, 600, 200, 10.0
+    grad = torch.randn((nz, ny, nx), device=dev, generator=gen)  # 288 MB: larger than L2
+    out = torch.empty_like(grad)
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    flops = 2 * 2 * (nx + ny + nz) * nx * ny * nz
+    smooth = {}
+    for mode, name in ((mamute.SMOOTH_BESSEL, "bessel"), (mamute.SMOOTH_LAPLACE, "laplace")):
+        ms = per_call_ms(lambda: ctx.smooth(h, mode, grad, out, lengths=[4 * h] * 3))
+        tf = flops / (ms / 1e3) / 1e12
+        smooth[name] = {"ms": ms, "tflops": tf, "frac_fp32_alu": tf / alu_peak}
+    ntr, nt_in, nt_out, dt_in = 65536, 4000, 1000, 5e-4
+    x = torch.randn((ntr, nt_in), device=dev, generator=gen)
+    y = torch.empty((ntr, nt_out), device=dev)
+    ms_r = per_call_ms(lambda: ctx.resample(x, dt_in, nt_out, 4 * dt_in, mamute.INTERP_SINC, y))
+    ms_t = per_call_ms(lambda: ctx.resample(y, dt_in, nt_out, 4 * dt_in, mamute.INTERP_SINC, x,
+                                            adjoint=True))
+    peak, peak_kind = _peaks()
+    byts = 4 * ntr * (nt_in + nt_out)
+    line = {"metric": "gradient smoothing ms (Bessel, 600x600x200)", "value": smooth["bessel"]["ms"],
+            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "postproc", "gradient": [nx, ny, nz], "h": h,
+                       "lengths": [4 * h] * 3, "traces": ntr, "nt_in": nt_in, "nt_out": nt_out,
+                       "l2": "inputs larger than L2 (288 MB gradient, 1.3 GB of traces)"},
+            "smoothing": dict(smooth, bound="fp32 alu", peak_tflops=alu_peak,
+                              flops_per_call=flops),
+            "resampling": {"ms": ms_r, "ms_transpose": ms_t, "bytes_per_call": byts,
+                           "achieved_gbs": byts / (ms_r / 1e3) / 1e9,
+                           "frac": byts / (ms_r / 1e3) / 1e9 / peak, "peak": peak,
+                           "peak_kind": peak_kind}}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gn_bench(args):
     """Exact Gauss-Newton-diagonal labels of the 160x160x80 learned-
     preconditioner workload (12 shots, 64 receivers, 1500 steps)."""
@@ -577,7 +644,7 @@ def main():
                     help="skip the 256^3 FWI gradient object of the headline line")
     ap.add_argument("--workload", default="model",
                     choices=["model", "model_small", "model_mid", "gradient_single",
-                             "gradient_batched", "cnn", "gn_labels"],
+                             "gradient_batched", "cnn", "gn_labels", "postproc"],
                     help="model: the headline modelling benchmark; gradient_*: FWI gradient "
                          "shots/s on the 256^3 single-shot or the 64-shot aperture workload")
     ap.add_argument("--autotune", action="store_true",
@@ -593,6 +660,8 @@ def main():
         return run_cnn_bench(args)
     if args.workload == "gn_labels":
         return run_gn_bench(args)
+    if args.workload == "postproc":
+        return run_postproc_bench(args)
 
     import torch
     import torch.distributed as dist

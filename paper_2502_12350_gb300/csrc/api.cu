@@ -109,9 +109,10 @@ struct mamute_ctx {
   DevBuf coefA, coefM, srho, pool[2], psi[2], acc, slots, tstore, dint, rint, dtmp, partial, misfit;
   DevBuf ident, rcolptr, rcols, ecol, srcw;  // receiver-node combination (trilinear)
   DevBuf smA, smMat, smLam;                  // gradient smoothing scratch
+  std::vector<double> smKey, rsKey;          // what smMat / smLam and rsPtr / rsCol / rsW hold
   DevBuf pitems, pnbr, precptr, prec, pcells, pgvals, pmaps, pflags;  // two-level launches
   bool pair_graph_failed = false;  // cooperative launches could not be captured
-  DevBuf rsPtr, rsCol, rsW, dmod, ddat;      // time resampling: matrix, model- and data-axis traces
+  DevBuf rsPtr, rsCol, rsW, dmod, ddat;      // time resampling: band matrix (c0, len, weights), model- and data-axis traces
   DevBuf cpml, cprof, cnode, crec, ccell, cgval;  // convolutional PML
   DevBuf items, vols, maps, cmaps, recptr, rec, colmap, gx, gy, gz, cells, gvals, srccell,
       aitems, arecptr, arec, acolmap, acells, agvals;
@@ -967,29 +968,37 @@ int do_smooth(mamute_ctx* ctx, int nx, int ny, int nz, double h, int mode, const
     L[a] = l > 0.0 ? l : 2.0 * h;
   }
   // C_a (orthonormal DCT-II, rows = modes) and its transpose, per axis, and
-  // the eigenvalues of -l_a^2 D_aa.
-  std::vector<float> mats, lam;
+  // the eigenvalues of -l_a^2 D_aa; built and uploaded only when the sizes,
+  // the spacing or the lengths differ from the previous call's.
   size_t off[3][2];
+  size_t o = 0;
   for (int a = 0; a < 3; ++a) {
-    const int m = dims[a];
-    off[a][0] = mats.size();
-    mats.resize(mats.size() + (size_t)m * m);
-    off[a][1] = mats.size();
-    mats.resize(mats.size() + (size_t)m * m);
-    for (int k = 0; k < m; ++k)
-      for (int i = 0; i < m; ++i) {
-        const double sc = k == 0 ? std::sqrt(1.0 / m) : std::sqrt(2.0 / m);
-        const float c = (float)(sc * std::cos(M_PI * k * (i + 0.5) / m));
-        mats[off[a][0] + (size_t)k * m + i] = c;
-        mats[off[a][1] + (size_t)i * m + k] = c;
-      }
-    for (int k = 0; k < m; ++k) {
-      const double sn = std::sin(M_PI * k / (2.0 * m));
-      lam.push_back((float)(4.0 * (L[a] / h) * (L[a] / h) * sn * sn));
-    }
+    off[a][0] = o;
+    off[a][1] = o + (size_t)dims[a] * dims[a];
+    o += 2 * (size_t)dims[a] * dims[a];
   }
-  CK(upload(ctx->smMat, mats, ctx->stream));
-  CK(upload(ctx->smLam, lam, ctx->stream));
+  const std::vector<double> key = {(double)nx, (double)ny, (double)nz, h, L[0], L[1], L[2]};
+  if (key != ctx->smKey) {
+    ctx->smKey.clear();
+    std::vector<float> mats(o), lam;
+    for (int a = 0; a < 3; ++a) {
+      const int m = dims[a];
+      for (int k = 0; k < m; ++k)
+        for (int i = 0; i < m; ++i) {
+          const double sc = k == 0 ? std::sqrt(1.0 / m) : std::sqrt(2.0 / m);
+          const float c = (float)(sc * std::cos(M_PI * k * (i + 0.5) / m));
+          mats[off[a][0] + (size_t)k * m + i] = c;
+          mats[off[a][1] + (size_t)i * m + k] = c;
+        }
+      for (int k = 0; k < m; ++k) {
+        const double sn = std::sin(M_PI * k / (2.0 * m));
+        lam.push_back((float)(4.0 * (L[a] / h) * (L[a] / h) * sn * sn));
+      }
+    }
+    CK(upload(ctx->smMat, mats, ctx->stream));
+    CK(upload(ctx->smLam, lam, ctx->stream));
+    ctx->smKey = key;
+  }
   CK(ensure(ctx->smA, (size_t)n * 4));
   const float* M = (const float*)ctx->smMat.p;
   float* A = (float*)ctx->smA.p;
@@ -1013,7 +1022,8 @@ int do_smooth(mamute_ctx* ctx, int nx, int ny, int nz, double h, int mode, const
   return MAMUTE_OK;
 }
 
-// Rows of the resampling matrix (or of its transpose) as CSR, weights in
+// Rows of the resampling matrix (or of its transpose) as CSR (converted to a
+// band by do_resample), weights in
 // FP64 (see mamute_resample in the header for the definitions).
 void resample_csr(int nt_in, double dt_in, int nt_out, double dt_out, int mode, bool transpose,
                   std::vector<int>& ptr, std::vector<int>& col, std::vector<float>& w) {
@@ -1073,15 +1083,36 @@ int do_resample(mamute_ctx* ctx, int ntr, int nt_in, double dt_in, int nt_out, d
     return fail(ctx, MAMUTE_EINVAL, "resample: bad sizes, steps or mode");
   if (ntr == 0) return MAMUTE_OK;
   if (!x || !y) return fail(ctx, MAMUTE_EINVAL, "resample: NULL trace array");
-  std::vector<int> ptr, col;
-  std::vector<float> w;
-  resample_csr(nt_in, dt_in, nt_out, dt_out, mode, adjoint != 0, ptr, col, w);
-  CK(upload(ctx->rsPtr, ptr, ctx->stream));
-  CK(upload(ctx->rsCol, col, ctx->stream));
-  CK(upload(ctx->rsW, w, ctx->stream));
+  // the matrix is built and uploaded only when it differs from the previous call's
+  const std::vector<double> key = {(double)nt_in, dt_in, (double)nt_out, dt_out, (double)mode,
+                                   (double)(adjoint != 0)};
+  if (key != ctx->rsKey) {
+    ctx->rsKey.clear();
+    std::vector<int> ptr, col;
+    std::vector<float> w;
+    resample_csr(nt_in, dt_in, nt_out, dt_out, mode, adjoint != 0, ptr, col, w);
+    // as a band: row m covers columns c0[m] .. c0[m] + len[m] - 1 (a gap, if
+    // any, holds zero weights), weights tap-major
+    const int rows = (int)ptr.size() - 1;
+    std::vector<int> c0(rows, 0), len(rows, 0);
+    int K = 0;
+    for (int m = 0; m < rows; ++m)
+      if (ptr[m + 1] > ptr[m]) {
+        c0[m] = col[ptr[m]];
+        len[m] = col[ptr[m + 1] - 1] - c0[m] + 1;
+        K = std::max(K, len[m]);
+      }
+    std::vector<float> wb((size_t)K * rows, 0.0f);
+    for (int m = 0; m < rows; ++m)
+      for (int k = ptr[m]; k < ptr[m + 1]; ++k) wb[(size_t)(col[k] - c0[m]) * rows + m] = w[k];
+    CK(upload(ctx->rsPtr, c0, ctx->stream));
+    CK(upload(ctx->rsCol, len, ctx->stream));
+    CK(upload(ctx->rsW, wb, ctx->stream));
+    ctx->rsKey = key;
+  }
   ++ctx->launches;
   const int n_src = adjoint ? nt_out : nt_in, n_dst = adjoint ? nt_in : nt_out;
-  CK(launch_csr_rows(x, n_src, (const int*)ctx->rsPtr.p, (const int*)ctx->rsCol.p,
+  CK(launch_band_rows(x, n_src, (const int*)ctx->rsPtr.p, (const int*)ctx->rsCol.p,
                      (const float*)ctx->rsW.p, n_dst, ntr, y, ctx->stream));
   return MAMUTE_OK;
 }

@@ -15,8 +15,11 @@
 //
 // Resampling (Sec. 2: time interpolation by nearest neighbour or sinc;
 // Table 1 Interpolate).  The resampling of every trace is the same sparse
-// matrix, built on the host in FP64 (see api.cu) and applied as CSR rows to
-// each trace (csr_rows_kernel); its transpose is another CSR matrix.
+// matrix, built on the host in FP64 (see api.cu); each of its rows covers a
+// contiguous run of input samples, so it is stored as a band (first column,
+// length, tap-major weights) and applied to every trace by band_rows_kernel
+// (one thread per output sample and kBT traces, each weight loaded once for
+// them); its transpose is another banded matrix.
 #include "postproc.h"
 
 namespace mamute {
@@ -95,16 +98,32 @@ __global__ void scale_kernel(float* __restrict__ u, int nx, int ny, int nz,
   }
 }
 
-__global__ void csr_rows_kernel(const float* __restrict__ x, int n_in, const int* __restrict__ ptr,
-                                const int* __restrict__ col, const float* __restrict__ w,
-                                int n_out, int n_traces, float* __restrict__ y) {
-  const int r = blockIdx.x;  // trace
-  if (r >= n_traces) return;
-  const float* xr = x + (long long)r * n_in;
-  for (int m = blockIdx.y * blockDim.x + threadIdx.x; m < n_out; m += gridDim.y * blockDim.x) {
-    float v = 0.0f;
-    for (int k = ptr[m]; k < ptr[m + 1]; ++k) v = fmaf(w[k], xr[col[k]], v);
-    y[(long long)r * n_out + m] = v;
+constexpr int kBT = 8;  // traces per thread
+
+__global__ void band_rows_kernel(const float* __restrict__ x, int n_in, const int* __restrict__ c0,
+                                 const int* __restrict__ len, const float* __restrict__ w,
+                                 int n_out, int n_traces, float* __restrict__ y) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_out) return;
+  const int c = c0[m], L = len[m];
+  const int ngroup = (n_traces + kBT - 1) / kBT;
+  for (int tg = blockIdx.y; tg < ngroup; tg += gridDim.y) {
+    const int t0 = tg * kBT;
+    const float* xr[kBT];
+    float acc[kBT];
+#pragma unroll
+    for (int t = 0; t < kBT; ++t) {
+      xr[t] = x + (long long)min(t0 + t, n_traces - 1) * n_in + c;
+      acc[t] = 0.0f;
+    }
+    for (int j = 0; j < L; ++j) {
+      const float wj = __ldg(w + (long long)j * n_out + m);
+#pragma unroll
+      for (int t = 0; t < kBT; ++t) acc[t] = fmaf(wj, __ldg(xr[t] + j), acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kBT; ++t)
+      if (t0 + t < n_traces) y[(long long)(t0 + t) * n_out + m] = acc[t];
   }
 }
 
@@ -142,12 +161,12 @@ cudaError_t launch_spectral_scale(float* u, int nx, int ny, int nz, const float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_csr_rows(const float* x, int n_in, const int* ptr, const int* col,
-                            const float* w, int n_out, int n_traces, float* y, cudaStream_t s) {
+cudaError_t launch_band_rows(const float* x, int n_in, const int* c0, const int* len,
+                             const float* w, int n_out, int n_traces, float* y, cudaStream_t s) {
   if (n_traces <= 0 || n_out <= 0) return cudaSuccess;
-  const int by = (n_out + 127) / 128;
-  dim3 g((unsigned)n_traces, (unsigned)(by < 16 ? by : 16));
-  csr_rows_kernel<<<g, 128, 0, s>>>(x, n_in, ptr, col, w, n_out, n_traces, y);
+  const int groups = (n_traces + kBT - 1) / kBT;
+  dim3 g((unsigned)((n_out + 127) / 128), (unsigned)(groups < 65535 ? groups : 65535));
+  band_rows_kernel<<<g, 128, 0, s>>>(x, n_in, c0, len, w, n_out, n_traces, y);
   return cudaGetLastError();
 }
 

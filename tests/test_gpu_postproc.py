@@ -150,3 +150,38 @@ def test_model_and_gradient_on_a_data_time_axis(ctx, oracle, mode):
     ctx.model_host(g, np.ascontiguousarray(w.vel), np.ascontiguousarray(w.rho), w.src_xyz,
                    w.wavelet, w.rec_offset, w.rec_xyz, host, **ax)
     np.testing.assert_array_equal(host, seis.cpu().numpy())
+
+
+def test_cached_tables_follow_the_call(ctx):
+    """The transform tables and the resampling matrix are kept between calls
+    with the same sizes and parameters: alternating parameters must give,
+    call for call, what a fresh context gives."""
+    from paper_2502_12350_gb300 import mamute
+    rng = np.random.default_rng(61)
+    g = torch.from_numpy(rng.standard_normal((12, 14, 20)).astype(np.float32)).cuda()
+    x = torch.from_numpy(rng.standard_normal((7, 90)).astype(np.float32)).cuda()
+    calls = [("smooth", 1, (20.0, 30.0, 10.0)), ("smooth", 2, (20.0, 30.0, 10.0)),
+             ("smooth", 1, (40.0, 30.0, 10.0)), ("smooth", 1, (20.0, 30.0, 10.0)),
+             ("resample", mamute.INTERP_SINC, 0), ("resample", mamute.INTERP_NEAREST, 0),
+             ("resample", mamute.INTERP_SINC, 1), ("resample", mamute.INTERP_SINC, 0)]
+
+    def run(c, call):
+        if call[0] == "smooth":
+            out = torch.empty_like(g)
+            c.smooth(10.0, call[1], g, out, lengths=call[2])
+        elif call[2] == 0:
+            out = torch.empty((7, 40), device="cuda:0")
+            c.resample(x, 1e-3, 40, 2.2e-3, call[1], out)
+        else:
+            out = torch.empty((7, 90), device="cuda:0")
+            c.resample(x[:, :40].contiguous(), 1e-3, 40, 2.2e-3, call[1], out, adjoint=True)
+        return out.cpu().numpy()
+
+    for call in calls:
+        got = run(ctx, call)
+        fresh = mamute.Context(0)
+        try:
+            want = run(fresh, call)
+        finally:
+            fresh.close()
+        np.testing.assert_array_equal(got, want, err_msg=str(call))
