@@ -1022,9 +1022,9 @@ int do_smooth(mamute_ctx* ctx, int nx, int ny, int nz, double h, int mode, const
   return MAMUTE_OK;
 }
 
-// Rows of the resampling matrix (or of its transpose) as CSR (converted to a
-// band by do_resample), weights in
-// FP64 (see mamute_resample in the header for the definitions).
+// Rows of the resampling matrix (or of its transpose) as CSR, weights in FP64
+// (see mamute_resample in the header for the definitions); do_resample turns
+// them into a band.
 void resample_csr(int nt_in, double dt_in, int nt_out, double dt_out, int mode, bool transpose,
                   std::vector<int>& ptr, std::vector<int>& col, std::vector<float>& w) {
   std::vector<std::vector<std::pair<int, double>>> rows(nt_out);
