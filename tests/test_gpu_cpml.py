@@ -260,3 +260,66 @@ def test_graph_replay_matches_direct_launches(ctx, monkeypatch):
     steps, total = runs["0"][1]
     assert steps == w.nt
     assert total >= 8 * w.nt
+
+
+def _aperture_case(seed=42, nt=45):
+    """Three shots confined to apertures of different sizes of one model
+    (windows of different extents in one launch), x starting on multiples of 4."""
+    w = synth.small_case(seed=seed, nx=44, ny=36, nz=14, border=6, nt=nt, density=True, n_src=3,
+                         n_rec=5)
+    rng = np.random.default_rng(seed)
+    aps, srcs, recs = [], [], []
+    for _ in range(3):
+        x0 = 4 * int(rng.integers(0, 5))
+        x1 = min(w.nx, x0 + int(rng.integers(14, 27)))
+        y0 = int(rng.integers(0, 12))
+        y1 = min(w.ny, y0 + int(rng.integers(12, 24)))
+        aps.append((x0, x1, y0, y1))
+        srcs.append(((x0 + x1) // 2, (y0 + y1) // 2, int(rng.integers(2, w.nz - 2))))
+        for _ in range(5):
+            recs.append((int(rng.integers(x0, x1)), int(rng.integers(y0, y1)),
+                         int(rng.integers(0, w.nz))))
+    w.aperture = np.array(aps, np.int32)
+    w.src_xyz = (np.array(srcs) * w.h).astype(np.float32)
+    w.rec_xyz = (np.array(recs) * w.h).astype(np.float32)
+    w.rec_offset = np.arange(4, dtype=np.int32) * 5
+    return w
+
+
+def _one_shot(w, s, aperture):
+    import copy
+    ws = copy.copy(w)
+    ws.src_xyz = w.src_xyz[s:s + 1].copy()
+    ws.rec_xyz = w.rec_xyz[w.rec_offset[s]:w.rec_offset[s + 1]].copy()
+    ws.rec_offset = np.array([0, w.rec_offset[s + 1] - w.rec_offset[s]], np.int32)
+    ws.aperture = None if aperture is None else np.asarray(aperture, np.int32).reshape(1, 4)
+    return ws
+
+
+def test_apertures_batch_invariance(ctx):
+    """Shots in apertures of different sizes in one call (every per-axis
+    kernel running windows of different extents in one launch) give, bit for
+    bit, the seismograms each shot gives in a call of its own, and their
+    gradient is the sum of the single-shot gradients; an aperture covering
+    the whole model gives the run without apertures."""
+    w = _aperture_case()
+    full = gpu_model(ctx, w, aperture=w.aperture)
+    assert np.isfinite(full).all() and np.abs(full).max() > 0
+    for s in range(3):
+        ws = _one_shot(w, s, w.aperture[s])
+        np.testing.assert_array_equal(full[w.rec_offset[s]:w.rec_offset[s + 1]],
+                                      gpu_model(ctx, ws, aperture=ws.aperture))
+    dobs = np.random.default_rng(43).standard_normal(full.shape).astype(np.float32) * 1e-3
+    J, g = gpu_gradient(ctx, w, dobs, aperture=w.aperture)
+    Js, gs = 0.0, np.zeros_like(g, dtype=np.float64)
+    for s in range(3):
+        ws = _one_shot(w, s, w.aperture[s])
+        Ji, gi = gpu_gradient(ctx, ws, dobs[w.rec_offset[s]:w.rec_offset[s + 1]],
+                              aperture=ws.aperture)
+        Js += Ji
+        gs += gi
+    assert abs(J - Js) <= 1e-9 * Js
+    assert rel(g, gs) <= 1e-5, rel(g, gs)
+    ws = _one_shot(w, 1, (0, w.nx, 0, w.ny))
+    np.testing.assert_array_equal(gpu_model(ctx, ws, aperture=ws.aperture),
+                                  gpu_model(ctx, _one_shot(w, 1, None)))
