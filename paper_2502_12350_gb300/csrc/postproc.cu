@@ -40,15 +40,29 @@ __global__ void __launch_bounds__(256) axis_kernel(const float* __restrict__ in,
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const long long L0 = (long long)blockIdx.x * kTL;
   const int i0 = blockIdx.y * kTI;
+  // The kTL x kTK elements of a chunk are 4 per thread, at the same lines and
+  // chunk columns in every chunk, so the line offsets are computed once.
+  // Along x (astride 1) consecutive threads take consecutive j (the lines are
+  // a row apart); along y and z consecutive lines (inner-contiguous).
+  const bool xaxis = astride == 1;
+  long long abase[4];
+  int al[4], ajj[4];
+  bool aok[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    al[q] = xaxis ? e / kTK : e % kTL;
+    ajj[q] = xaxis ? e % kTK : e / kTL;
+    const long long L = L0 + al[q];
+    aok[q] = L < lines;
+    abase[q] = aok[q] ? (L / inner) * outer + (L % inner) : 0;
+  }
   float acc[4][4] = {};
   for (int j0 = 0; j0 < n; j0 += kTK) {
-    for (int e = threadIdx.x; e < kTL * kTK; e += 256) {
-      const int l = e % kTL, jj = e / kTL;
-      const long long L = L0 + l;
-      const int j = j0 + jj;
-      float v = 0.0f;
-      if (L < lines && j < n) v = in[(L / inner) * outer + (L % inner) + (long long)j * astride];
-      As[jj][l] = v;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + ajj[q];
+      As[ajj[q]][al[q]] = (aok[q] && j < n) ? in[abase[q] + (long long)j * astride] : 0.0f;
     }
     for (int e = threadIdx.x; e < kTI * kTK; e += 256) {
       const int jj = e % kTK, ii = e / kTK;
