@@ -1905,16 +1905,17 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   ctx->max_planes = P.Nz;
   TRY(check_cfl(ctx, P, vel));
   // Compact interior term layout: slot k of the ring is [nz][ny][nx].
-  {
+  auto compact_terms = [](Plan& Q) {
     long long toff = 0;
-    for (VolDesc& V : P.vols) {
+    for (VolDesc& V : Q.vols) {
       V.txoff = V.border;
       V.tpitch = V.nxi;
       V.toff = toff;
       toff += (long long)V.nxi * V.nyi * V.nzi;
     }
-    P.term_elems = toff;
-  }
+    Q.term_elems = toff;
+  };
+  compact_terms(P);
   TRY(setup(ctx, P, vel, rho, true, false));
   // Retained bins of the N_f = 2 nt DFT: where the wavelet spectrum is at
   // least band_rel of its peak (all bins for band_rel <= 0).
@@ -1955,7 +1956,9 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
   // The longest block that still lets a batch hold every shot (fewer, fuller
   // batches matter more for the propagations than block length does for the
   // accumulation).
-  int kT = 64, B = n_src;
+  // Receivers are batched independently of the shots, as many windows per
+  // launch as fit (larger launches propagate faster), in equal batches.
+  int kT = 64, B = n_src, Br = nr0;
   {
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
@@ -1963,39 +1966,44 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
     const double avail = (double)fr + (double)ctx->gnV.bytes + (double)ctx->gnRe.bytes +
                          (double)ctx->gnIm.bytes;
     const double fixed = 2.0 * nb * (double)N * 4.0;  // S and R
-    auto batch = [&](int t) {
+    // windows whose samples and accumulators fit in 0.6 of the memory
+    auto fit = [&](int t) {
       const double per_vol = ((double)2 * nb + t) * (double)N * 4.0;
-      return (int)std::max(1.0, std::min((double)n_src, (0.6 * avail - fixed) / per_vol));
+      return (int)std::max(1.0, std::min(1e6, std::floor((0.6 * avail - fixed) / per_vol)));
     };
     if (dft_tc_supported(N, nb)) {
       const int want = std::min(n_src, 16);
       kT = 256;
       for (int t : {1024, 512, 256}) {
         const int tt = std::min(t, (nt + 31) / 32 * 32);
-        if (batch(tt) >= want) {
+        if (fit(tt) >= want) {
           kT = tt;
           break;
         }
       }
     }
-    B = batch(kT);
-    const int cap = env_int("MAMUTE_GN_BATCH", 0);  // smaller batches (profiling)
-    if (cap > 0) B = std::min(B, cap);
+    int cap = fit(kT);
+    const int env_cap = env_int("MAMUTE_GN_BATCH", 0);  // smaller batches (profiling)
+    if (env_cap > 0) cap = std::min(cap, env_cap);
+    B = std::min(n_src, cap);
+    const int nbr = (nr0 + cap - 1) / cap;
+    Br = (nr0 + nbr - 1) / nbr;
     if (env_int("MAMUTE_VERBOSE", 0))
-      fprintf(stderr, "mamute gn: %d bins, blocks of %d samples, batches of %d windows (%.1f GB available)\n",
-              nb, kT, B, avail * 1e-9);
+      fprintf(stderr, "mamute gn: %d bins, blocks of %d samples, batches of %d shot and %d receiver "
+              "windows (%.1f GB available)\n", nb, kT, B, Br, avail * 1e-9);
   }
-  CK(ensure(ctx->gnV, (size_t)kT * B * N * 4));
-  CK(ensure(ctx->gnRe, (size_t)nb * B * N * 4));
-  CK(ensure(ctx->gnIm, (size_t)nb * B * N * 4));
+  const int Bmax = std::max(B, Br);
+  CK(ensure(ctx->gnV, (size_t)kT * Bmax * N * 4));
+  CK(ensure(ctx->gnRe, (size_t)nb * Bmax * N * 4));
+  CK(ensure(ctx->gnIm, (size_t)nb * Bmax * N * 4));
   CK(ensure(ctx->gnS, (size_t)nb * N * 4));
   CK(ensure(ctx->gnR, (size_t)nb * N * 4));
   CK(ensure(ctx->gnW, std::max((size_t)kT * dft_max_bins() * 8, dft_tc_image_bytes(kT, nb))));
   CK(upload(ctx->gnBins, bins, ctx->stream));
   CK(upload(ctx->gnWts, wts, ctx->stream));
   CK(ensure(ctx->gnRow, (size_t)2 * std::max(P.ncol, 1) * 4));
-  CK(cudaMemsetAsync(ctx->gnRe.p, 0, (size_t)nb * B * N * 4, ctx->stream));
-  CK(cudaMemsetAsync(ctx->gnIm.p, 0, (size_t)nb * B * N * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->gnRe.p, 0, (size_t)nb * Bmax * N * 4, ctx->stream));
+  CK(cudaMemsetAsync(ctx->gnIm.p, 0, (size_t)nb * Bmax * N * 4, ctx->stream));
   CK(cudaMemsetAsync(ctx->gnS.p, 0, (size_t)nb * N * 4, ctx->stream));
   CK(cudaMemsetAsync(ctx->gnR.p, 0, (size_t)nb * N * 4, ctx->stream));
   float* V = (float*)ctx->gnV.p;
@@ -2037,23 +2045,46 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
     CK(aux_count(ctx, launch_power(nb, N, nv, re, im, (float*)ctx->gnS.p, ctx->stream)));
   }
   // Receiver side: receiver r0 + b of the common set in window b, a unit data
-  // impulse at the last sample.
+  // impulse at the last sample.  Batches of Br windows: when Br exceeds the
+  // shot plan's windows, a plan of Br whole-grid windows that each record
+  // the common receiver set (their sources are never fired).
+  Plan Pr;
+  const Plan* R = &P;
+  std::vector<int> roff(rec_offset, rec_offset + n_src + 1);
+  if (Br > n_src) {
+    std::vector<float> sxyz(3 * (size_t)Br), rxyz(3 * (size_t)Br * nr0);
+    roff.assign(Br + 1, 0);
+    for (int b = 0; b < Br; ++b) {
+      for (int d = 0; d < 3; ++d) sxyz[3 * (size_t)b + d] = src_xyz[d];
+      std::copy(rec_xyz, rec_xyz + 3 * (size_t)nr0, rxyz.begin() + 3 * (size_t)b * nr0);
+      roff[b + 1] = (b + 1) * nr0;
+    }
+    TRY(build_plan(ctx, g, rho != nullptr, Br, sxyz.data(), roff.data(), rxyz.data(), nullptr, Pr));
+    if (!Pr.one_node || Pr.Nz != P.Nz)
+      return fail(ctx, MAMUTE_ECUDA, "receiver plan differs from the shot plan");
+    Pr.vmax = P.vmax;
+    compact_terms(Pr);
+    TRY(setup(ctx, Pr, vel, rho, true, false));
+    R = &Pr;
+  }
+  const size_t rpool = (size_t)R->pool_elems * 4;
+  CK(ensure(ctx->gnRow, (size_t)2 * std::max(R->ncol, 1) * 4));
   float* zero_row = (float*)ctx->gnRow.p;
-  float* imp_row = zero_row + std::max(P.ncol, 1);
-  CK(cudaMemsetAsync(ctx->gnRow.p, 0, (size_t)2 * std::max(P.ncol, 1) * 4, ctx->stream));
-  std::vector<int> col_of(P.ncol > 0 ? P.ncol : 1, -1);  // global receiver -> adjoint column
-  for (int c = 0; c < P.ncol; ++c) col_of[P.acolmap[c]] = c;
-  std::vector<float> row(std::max(P.ncol, 1));
-  for (int r0 = 0; r0 < nr0; r0 += B) {
-    const int nv = std::min(B, nr0 - r0);
+  float* imp_row = zero_row + std::max(R->ncol, 1);
+  CK(cudaMemsetAsync(ctx->gnRow.p, 0, (size_t)2 * std::max(R->ncol, 1) * 4, ctx->stream));
+  std::vector<int> col_of(R->ncol > 0 ? R->ncol : 1, -1);  // global receiver -> adjoint column
+  for (int c = 0; c < R->ncol; ++c) col_of[R->acolmap[c]] = c;
+  std::vector<float> row(std::max(R->ncol, 1));
+  for (int r0 = 0; r0 < nr0; r0 += Br) {
+    const int nv = std::min(Br, nr0 - r0);
     const long long Nb = (long long)nv * N;
     std::fill(row.begin(), row.end(), 0.0f);
-    for (int b = 0; b < nv; ++b) row[col_of[rec_offset[b] + r0 + b]] = 1.0f;
+    for (int b = 0; b < nv; ++b) row[col_of[roff[b] + r0 + b]] = 1.0f;
     CK(cudaMemcpyAsync(imp_row, row.data(), row.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemsetAsync(ctx->psi[0].p, 0, pool, ctx->stream));
-    CK(cudaMemsetAsync(ctx->psi[1].p, 0, pool, ctx->stream));
+    CK(cudaMemsetAsync(ctx->psi[0].p, 0, rpool, ctx->stream));
+    CK(cudaMemsetAsync(ctx->psi[1].p, 0, rpool, ctx->stream));
     int ib, ie;
-    range(P.aitems, 0, nv, ib, ie);
+    range(R->aitems, 0, nv, ib, ie);
     int done = 0;
     auto flush = [&](int upto) -> int {
       if (upto > done) {
@@ -2083,8 +2114,8 @@ int run_gn(mamute_ctx* ctx, const mamute_grid* g, const float* vel, const float*
       a.rec = (const RecEntry*)ctx->arec.p;
       a.rin = (j == 0) ? imp_row : zero_row;
       a.status = ctx->status;
-      a.zs = P.zs;
-      CK(step_launch(ctx, a, ie - ib, P.atx, P.aty, P.dens, MODE_ADJ_TERM));
+      a.zs = R->zs;
+      CK(step_launch(ctx, a, ie - ib, R->atx, R->aty, R->dens, MODE_ADJ_TERM));
       if ((j + 1) % kT == 0) TRY(flush(j + 1));
     }
     TRY(flush(nt));

@@ -94,3 +94,27 @@ def test_gn_diagonal_blocks_and_fp32_path(ctx, oracle, nt, nx, ny):
     got = H.cpu().numpy().astype(np.float64)
     assert np.isfinite(got).all() and got.min() > 0
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
+
+
+@pytest.mark.parametrize("cap", [0, 4, 3])
+def test_gn_receiver_batches_beyond_the_shots(ctx, oracle, monkeypatch, cap):
+    """Receivers are batched independently of the shots: more receivers per
+    launch than there are shot windows (a plan of their own), in one batch
+    (no cap) or in several (batches of 4 and 3, and of 3, 3 and 1)."""
+    from paper_2502_12350_gb300 import mamute
+    w = synth.small_case(seed=66, nx=14, ny=12, nz=10, border=6, nt=80, density=True, n_src=2,
+                         n_rec=7, fpeak=35.0)
+    w.rec_xyz = np.concatenate([w.rec_xyz[:7]] * 2)
+    w.rec_offset = np.array([0, 7, 14], np.int32)
+    og = oracle.make_grid(w.nx, w.ny, w.nz, w.border, w.h, w.dt, w.nt)
+    ref = gn.separable(og, w.vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=w.rho,
+                       band_rel=1e-4)
+    monkeypatch.setenv("MAMUTE_GN_BATCH", str(cap))
+    dev = torch.device("cuda:0")
+    vel = torch.from_numpy(w.vel).to(dev)
+    H = torch.full_like(vel, float("nan"))
+    ctx.gn_diagonal(mamute.grid_of(w), vel, torch.from_numpy(w.rho).to(dev), w.src_xyz,
+                    w.wavelet, w.rec_offset, w.rec_xyz, H, band_rel=1e-4)
+    got = H.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all() and got.min() > 0
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
