@@ -13,9 +13,9 @@
 // with b_a = exp(-(d_a + alpha_a) dt), c_a = d_a (b_a - 1) / (d_a + alpha_a)
 // (profiles built on the host; b = 1, c = 0 outside the layer).  The main
 // step kernel forms (2 - M) u - v + A lap u + source everywhere (damping
-// factor 1); the kernels here add the memory-variable part on the shell
-// where it is non-zero, and the same amount A sum_a (...) to the stored
-// imaging term A lap u - M u.
+// factor 1); the kernels here add the memory-variable part of each axis on
+// that axis's layer slabs, where it is non-zero, and the same amount to the
+// stored imaging term A lap u - M u.
 //
 // The gradient is the exact transpose of this recursion.  In the adjoint
 // level psi (the multiplier of u scaled by A, which the main kernel
@@ -23,7 +23,7 @@
 //   per axis, in the layer:  y_a = c_a (Zb_a + psi),  Zb_a <- b_a (Zb_a + psi)
 //                            p_a = Pb_a - D1_a (psi + y_a),  Pb_a <- b_a p_a,  z_a = c_a p_a
 //   main adjoint step:       psi' = (2 - M) psi - psi_prev + A lap psi + injection
-//   shell correction:        psi' += A sum_a (D2_a y_a - D1_a z_a)
+//   correction (per axis):   psi' += A sum_a (D2_a y_a - D1_a z_a)
 // (Zb, Pb the multipliers of Zeta and Psi; D2 is symmetric, D1 antisymmetric,
 // the fields are zero outside the padded window), and the imaging
 // accumulator takes the corrected psi' against the stored term.
