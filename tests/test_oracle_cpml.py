@@ -9,6 +9,11 @@
 * It absorbs: on a small grid, the error against a grid so large that no
   reflection reaches the receivers in the window is far below that of the
   Cerjan sponge of the same thickness.
+* The layer's coefficients mean what they are for: the damping profile gives
+  the continuous layer the nominal normal-incidence reflection R, and the
+  recursion's b and c are the step integrals of the kernel whose transform
+  is 1/s - 1 (quadrature).  A wrong factor or log base in the profile, a
+  sign of c, or b without the frequency shift fails one of them.
 """
 import numpy as np
 import pytest
@@ -151,3 +156,56 @@ def test_absorbs_with_a_free_surface(oracle):
     e_pml = np.linalg.norm(pml - ref) / np.linalg.norm(ref)
     assert e_pml < 0.01 * e_sponge, (e_pml, e_sponge)
     assert e_pml < 1e-4, e_pml
+
+
+def _d_alpha(b, c, dt):
+    """Damping d and frequency shift alpha recovered from the recursion's
+    coefficients b = exp(-(d + alpha) dt), c = d (b - 1) / (d + alpha)."""
+    s = -np.log(b) / dt
+    d = np.where(s > 0, c * s / np.where(s > 0, b - 1.0, 1.0), 0.0)
+    return d, s - d
+
+
+def test_layer_reaches_the_nominal_reflection():
+    """The damping profile is built for a nominal normal-incidence reflection
+    R of the continuous layer, exp(-(2 / vmax) * integral of d over the layer)
+    = R.  Integrating the oracle's d (recovered from its b and c) over a
+    finely sampled layer gives back R, for several R and velocities."""
+    from scipy.integrate import simpson
+    B, h, dt, f0 = 400, 10.0, 1e-4, 15.0
+    N = 2 * B + 10
+    for R, vmax in ((1e-3, 3000.0), (1e-2, 1800.0), (1e-5, 4500.0)):
+        b, cc = cpml.profiles(N, B, h, dt, vmax, f0, R)
+        d, _ = _d_alpha(b, cc, dt)
+        prof = np.concatenate([[0.0], d[N - B:]])  # inner edge (distance 0) to the outer face
+        x = np.arange(B + 1) * h
+        refl = np.exp(-2.0 / vmax * simpson(prof, x=x))
+        assert abs(np.log(refl) / np.log(R) - 1.0) < 1e-4, (R, vmax, refl)
+        # both faces carry the same layer
+        np.testing.assert_allclose(d[:B][::-1], d[N - B:], rtol=1e-12)
+
+
+def test_recursion_is_the_convolution_with_the_layer_kernel():
+    """In the layer the derivative is (1/s) d/dx with s = 1 + d / (alpha + i w),
+    and 1/s - 1 = -d / (d + alpha + i w) is the transform of the kernel
+    -d exp(-(d + alpha) t) for t > 0.  With the field held constant over each
+    step, the memory variable is the sum over past steps m of the kernel's
+    integral over [m dt, (m + 1) dt], which must equal c b^m."""
+    from scipy.integrate import quad
+    B, h, dt, vmax, f0, R = 10, 12.5, 1e-3, 3500.0, 12.0, 1e-3
+    N = 3 * B
+    b, cc = cpml.profiles(N, B, h, dt, vmax, f0, R)
+    d, alpha = _d_alpha(b, cc, dt)
+    for i in (N - B, N - B // 2, N - 1, 0, B // 2):
+        di, ai = d[i], alpha[i]
+        assert di > 0 and ai >= 0
+        kern = lambda t: -di * np.exp(-(di + ai) * t)
+        # the kernel's Fourier transform is 1/s - 1 at a few frequencies
+        for w in (0.0, 2 * np.pi * 7.0, 2 * np.pi * 30.0):
+            re = quad(lambda t: kern(t) * np.cos(w * t), 0, np.inf, limit=400)[0]
+            im = quad(lambda t: -kern(t) * np.sin(w * t), 0, np.inf, limit=400)[0]
+            inv_s = (ai + 1j * w) / (ai + 1j * w + di)  # 1 / (1 + d / (alpha + i w))
+            assert abs((re + 1j * im) - (inv_s - 1.0)) <= 1e-7 * abs(inv_s - 1.0)
+        for m in range(6):
+            want = quad(kern, m * dt, (m + 1) * dt)[0]
+            assert abs(cc[i] * b[i] ** m - want) <= 1e-10 * abs(want), (i, m)
