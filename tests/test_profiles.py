@@ -49,3 +49,21 @@ def test_bench_reads_the_traffic_figures():
             assert got == int(f["dram_bytes_per_launch"])
         else:  # the kernel changed after the capture: no figure
             assert got is None
+
+
+def test_algorithmic_bytes_agree_with_the_bench():
+    """The algorithmic bytes a profile quotes are the ones bench.py divides by
+    the step time: 20 B per padded point for the headline step with density,
+    and that plus 16 B per layer point and axis for the CPML step."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2502_12350_gb300 import synth
+
+    w = synth.forward_density(nt=1)
+    pts = (w.nx + 2 * w.border) * (w.ny + 2 * w.border) * (w.nz + 2 * w.border)
+    head = _fields(os.path.join(ROOT, "profiles",
+                                "step_kernel_forward_forward_512x512x256_density.md"))
+    assert int(head["algorithmic_bytes_per_launch"]) == 20 * pts
+    pml = _fields(os.path.join(ROOT, "profiles", "cpml_step_forward_512x512x256_density.md"))
+    assert int(pml["algorithmic_bytes_per_launch"]) == bench.pml_bytes_per_step(w)
