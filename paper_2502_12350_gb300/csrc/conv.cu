@@ -20,15 +20,9 @@ namespace mamute {
 namespace {
 
 constexpr int kTX = 16, kTY = 8;                       // output tile
-constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = 3;   // input halo tile
+constexpr int kHX = kTX + 2, kHY = kTY + 2;           // input halo tile (3 planes)
 constexpr int kC = 16;                                 // channels (padded)
 constexpr int kTaps = 27;
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
 
 __device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
