@@ -225,6 +225,16 @@ def test_gn_jacobian_column_matches_finite_differences(oracle, density):
     fd = (dp - dm) / (2 * eps)
     assert np.abs(col).max() > 0
     np.testing.assert_allclose(col, fd, rtol=0, atol=1e-6 * np.abs(fd).max())
+    # The label at that cell is the sum of squares of the whole column (the
+    # Born data over the full linear-convolution length 2 nt - 1, summed over
+    # the receivers), which ties the oracle's chain-rule factor to the one the
+    # finite differences just checked.
+    full = np.zeros((G.shape[0], 2 * nt - 1))
+    for n in range(nt):
+        full[:, n:n + nt] += G * a[n]
+    full *= 2.0 * vel[zyx] * w.dt**2
+    H = gn.separable(g, vel, w.src_xyz, w.wavelet, w.rec_offset, w.rec_xyz, rho=rho)
+    np.testing.assert_allclose(H[zyx], np.sum(full**2), rtol=1e-9)
 
 
 @pytest.mark.parametrize("density", [False, True])
